@@ -1,0 +1,78 @@
+"""L1 oracle: one QTT fractional step (Sec. III.C) from the L1 algebra, in FP64.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+The step (same sequence as the CUDA library, written independently):
+
+1. convective derivatives, each an MPO-MPS product rounded to chi (Sec. II.A.2):
+   dxu = round(D_x u), dzu = round(D_z u), dxv = round(D_x v), dzv = round(D_z v);
+2. explicit right-hand sides (eq:intermediate_vel_eq), one variational fit each
+   (Table I), warm-started from u (v):
+   rhs_u = u - dt [u (.) (dxu + bcx_u) + v (.) (dzu + bcz_u)],  rhs_v likewise;
+3. implicit momentum solves by ALS with the |J|-weighted SPD operator
+   H = |J| (I - dt/Re Lap_h):  H u* = |J| (.) rhs_u + dt/Re |J| bcLap_u  (warm start u);
+4. pressure Poisson by ALS (eq:Poisson with the Jacobian weighting of Sec. III.C):
+   (-|J| Lap_h^p) p = -|J| (.) (D_x u* + D_z v* + bc_div) / dt   (warm start p^m);
+5. projection, one fit each (warm start u*, v*):  u = u* - dt D_x^p p,  v = v* - dt D_z^p p.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import tt
+from .qtt_ops import Ops
+
+
+@dataclass
+class StepOpts:
+    chi: int
+    fit_sweeps: int = 1
+    mom_sweeps: int = 1
+    mom_cg: int = 8
+    poi_sweeps: int = 2
+    poi_cg: int = 20
+    cg_tol: float = 1e-12
+
+
+def _nz(terms):
+    return [t for t in terms if all(x is not None for x in t[2:])]
+
+
+def step(ops: Ops, u, v, p, o: StepOpts):
+    dt, Re = ops.dt, ops.Re
+    chi = o.chi
+    dxu = tt.round_tt(tt.mpo_mps(ops.Dx, u), chi)
+    dzu = tt.round_tt(tt.mpo_mps(ops.Dz, u), chi)
+    dxv = tt.round_tt(tt.mpo_mps(ops.Dx, v), chi)
+    dzv = tt.round_tt(tt.mpo_mps(ops.Dz, v), chi)
+    rhs_u = tt.fit(_nz([("vec", 1.0, u), ("had", -dt, u, dxu), ("had", -dt, u, ops.bcx_u),
+                        ("had", -dt, v, dzu), ("had", -dt, v, ops.bcz_u)]), u, o.fit_sweeps)
+    rhs_v = tt.fit(_nz([("vec", 1.0, v), ("had", -dt, u, dxv), ("had", -dt, u, ops.bcx_v),
+                        ("had", -dt, v, dzv), ("had", -dt, v, ops.bcz_v)]), v, o.fit_sweeps)
+    k = dt / Re
+    us, cg_u = tt.als(ops.H, _nz([("mpo", 1.0, ops.Jdiag, rhs_u), ("vec", k, ops.JbcLap_u)]), u,
+                      o.mom_sweeps, o.mom_cg, o.cg_tol)
+    vs, cg_v = tt.als(ops.H, _nz([("mpo", 1.0, ops.Jdiag, rhs_v), ("vec", k, ops.JbcLap_v)]), v,
+                      o.mom_sweeps, o.mom_cg, o.cg_tol)
+    pn, cg_p = tt.als(ops.Ap, _nz([("mpo", 1.0, ops.Px, us), ("mpo", 1.0, ops.Pz, vs),
+                                   ("vec", 1.0, ops.bcdiv_w)]), p, o.poi_sweeps, o.poi_cg, o.cg_tol)
+    un = tt.fit([("vec", 1.0, us), ("mpo", -dt, ops.Dxp, pn)], us, o.fit_sweeps)
+    vn = tt.fit([("vec", 1.0, vs), ("mpo", -dt, ops.Dzp, pn)], vs, o.fit_sweeps)
+    info = dict(cg_u=cg_u, cg_v=cg_v, cg_p=cg_p)
+    return un, vn, pn, info
+
+
+def padded(cores, chi: int, seed_cores):
+    """Embed an MPS into the bond profile min(2^k, 2^(n-k), chi): the missing rows and
+    columns of each core are filled from ``seed_cores`` (small seeded noise drawn by the
+    caller), the existing block is kept.  Used for warm starts of lower rank."""
+    out = []
+    for c, s in zip(cores, seed_cores):
+        r0, d, r1 = s.shape
+        x = s.copy()
+        a, b = min(r0, c.shape[0]), min(r1, c.shape[2])
+        x[:a, :, :b] = c[:a, :, :b]
+        out.append(x)
+    return out
