@@ -28,6 +28,11 @@ from __future__ import annotations
 
 import numpy as np
 
+# Multi-operand contractions go pairwise (greedy order, BLAS where possible); numpy's default
+# path search refuses intermediates larger than the inputs and would fall back to one nested
+# loop over all indices.  The order of a sum changes only the rounding, not the result.
+OPT = ("greedy", 1e12)
+
 # --------------------------------------------------------------------------------------
 # dense <-> TT
 # --------------------------------------------------------------------------------------
@@ -228,7 +233,7 @@ def dot(a, b) -> float:
     """<a, b> by left-to-right transfer matrices."""
     E = np.ones((1, 1))
     for A, B in zip(a, b):
-        E = np.einsum("ab,asc,bsd->cd", E, A, B)
+        E = np.einsum("ab,asc,bsd->cd", E, A, B, optimize=OPT)
     return float(E[0, 0])
 
 
@@ -259,24 +264,24 @@ def _left_update(term, L, C, k):
     kind = term[0]
     if kind == "vec":
         X = term[2][k]
-        return np.einsum("ca,csd,asb->db", L, C, X)
+        return np.einsum("ca,csd,asb->db", L, C, X, optimize=OPT)
     if kind == "had":
         A, B = term[2][k], term[3][k]
-        return np.einsum("cab,csd,ase,bsf->def", L, C, A, B)
+        return np.einsum("cab,csd,ase,bsf->def", L, C, A, B, optimize=OPT)
     W, X = term[2][k], term[3][k]
-    return np.einsum("cwa,csd,wstv,atb->dvb", L, C, W, X)
+    return np.einsum("cwa,csd,wstv,atb->dvb", L, C, W, X, optimize=OPT)
 
 
 def _right_update(term, R, C, k):
     kind = term[0]
     if kind == "vec":
         X = term[2][k]
-        return np.einsum("db,csd,asb->ca", R, C, X)
+        return np.einsum("db,csd,asb->ca", R, C, X, optimize=OPT)
     if kind == "had":
         A, B = term[2][k], term[3][k]
-        return np.einsum("def,csd,ase,bsf->cab", R, C, A, B)
+        return np.einsum("def,csd,ase,bsf->cab", R, C, A, B, optimize=OPT)
     W, X = term[2][k], term[3][k]
-    return np.einsum("dvb,csd,wstv,atb->cwa", R, C, W, X)
+    return np.einsum("dvb,csd,wstv,atb->cwa", R, C, W, X, optimize=OPT)
 
 
 def _local(term, L, R, k):
@@ -285,12 +290,12 @@ def _local(term, L, R, k):
     coef = term[1]
     if kind == "vec":
         X = term[2][k]
-        return coef * np.einsum("ca,asb,db->csd", L, X, R)
+        return coef * np.einsum("ca,asb,db->csd", L, X, R, optimize=OPT)
     if kind == "had":
         A, B = term[2][k], term[3][k]
-        return coef * np.einsum("cab,ase,bsf,def->csd", L, A, B, R)
+        return coef * np.einsum("cab,ase,bsf,def->csd", L, A, B, R, optimize=OPT)
     W, X = term[2][k], term[3][k]
-    return coef * np.einsum("cwa,wstv,atb,dvb->csd", L, W, X, R)
+    return coef * np.einsum("cwa,wstv,atb,dvb->csd", L, W, X, R, optimize=OPT)
 
 
 def fit(terms, init, sweeps: int = 1):
@@ -349,13 +354,13 @@ def zipup_hadamard(a, b, chi: int):
     cores = [None] * n
     C = np.ones((1, 1, 1))          # (c, a', b') carry
     for k in range(n - 1, 0, -1):
-        T = np.einsum("ase,bsf,cef->absc", a[k], b[k], C)
+        T = np.einsum("ase,bsf,cef->absc", a[k], b[k], C, optimize=OPT)
         ra, rb, _, rc = T.shape
         U, S, Vt = np.linalg.svd(T.reshape(ra * rb, d * rc), full_matrices=False)
         bk = kept_rank(S, chi, 0.0, min(m[k], d * rc))
         cores[k] = Vt[:bk].reshape(bk, d, rc)
         C = (U[:, :bk] * S[:bk]).T.reshape(bk, ra, rb)
-    T = np.einsum("ase,bsf,cef->absc", a[0], b[0], C)
+    T = np.einsum("ase,bsf,cef->absc", a[0], b[0], C, optimize=OPT)
     cores[0] = T.reshape(1, d, T.shape[3])
     return cores
 
@@ -371,16 +376,16 @@ def hadamard_round(a, b, chi: int, sweeps: int = 2, init=None):
 # --------------------------------------------------------------------------------------
 
 def _op_left(L, X, W):
-    return np.einsum("cwa,csd,wstv,atb->dvb", L, X, W, X)
+    return np.einsum("cwa,csd,wstv,atb->dvb", L, X, W, X, optimize=OPT)
 
 
 def _op_right(R, X, W):
-    return np.einsum("dvb,csd,wstv,atb->cwa", R, X, W, X)
+    return np.einsum("dvb,csd,wstv,atb->cwa", R, X, W, X, optimize=OPT)
 
 
 def _op_local(L, W, R, x):
     """Fast matvec (App. G): successive contractions L . x . W . R, never the assembled matrix."""
-    return np.einsum("cwa,wstv,atb,dvb->csd", L, W, x, R)
+    return np.einsum("cwa,wstv,atb,dvb->csd", L, W, x, R, optimize=OPT)
 
 
 def cg(matvec, b, x0, iters: int, tol: float):
