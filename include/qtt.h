@@ -1,0 +1,230 @@
+/*
+ * qtt.h -- C ABI of the GB300 library for the QTT (quantics tensor-train) fractional-step
+ * method for incompressible flow around a cylinder on a curvilinear O-grid
+ * (arXiv:2507.05222).
+ *
+ * Objects
+ *   qtt_ctx  -- one CUDA device, one stream, one device memory pool.  All calls on a
+ *               context are enqueued on its stream, in order; none blocks the host unless
+ *               its description says so.  A context must be used by one host thread at a time.
+ *   qtt_mps  -- a TT-vector (matrix product state, eq:simpleMPS): n cores A[k] of shape
+ *               (r_{k-1}, d, r_k), r_0 = r_n = 1, stored row-major with the left bond slowest.
+ *               Core 1 carries the most significant bit (App. D).
+ *   qtt_mpo  -- a TT-matrix (eq:simpleMatrix): n cores M[k] of shape (w_{k-1}, d, d, w_k),
+ *               index order (left bond, output bit, input bit, right bond).
+ *   qtt_case -- grid, analytic metric terms, curvilinear FD operators and boundary vectors of
+ *               one cylinder case, plus the flow state (u, v, p) (Sec. III, App. A, App. E).
+ *
+ * Ownership
+ *   Every qtt_mps / qtt_mpo / qtt_case returned through an out-pointer is owned by the caller
+ *   and released with the matching *_free.  Inputs are never modified unless the parameter is
+ *   named *_inout.  Device memory comes from the context's pool, which draws large blocks from
+ *   the allocator given to qtt_ctx_create (or cudaMalloc when none is given).
+ *
+ * Gauge
+ *   Every MPS produced by the library is right-canonical (cores 2..n right-orthonormal, the
+ *   norm in core 1; Sec. II).  Results are compared through reconstructed values, overlaps
+ *   and norms, never raw cores.
+ *
+ * Errors
+ *   Every int-returning call returns QTT_OK (0) or a negative QTT_ERR_* code; qtt_last_error()
+ *   gives a message for the calling thread.  Argument errors are detected on the host before
+ *   anything is enqueued.  Device-side outcomes (CG iterations, residuals, non-finite values)
+ *   land in the *_info structs and are valid after qtt_ctx_sync().  No C++ exception crosses
+ *   this interface.
+ */
+#ifndef QTT_H
+#define QTT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QTT_OK 0
+#define QTT_ERR_ARG (-1)          /* invalid argument (shape, size, null pointer, range) */
+#define QTT_ERR_ALLOC (-2)        /* device allocation failed */
+#define QTT_ERR_CUDA (-3)         /* a CUDA runtime call or kernel launch failed */
+#define QTT_ERR_NOT_CONVERGED (-4)/* a solver stopped at its sweep limit above tolerance */
+#define QTT_ERR_TIMEOUT (-5)      /* a bounded device wait ran out */
+#define QTT_ERR_NONFINITE (-6)    /* a NaN or Inf appeared in a result */
+#define QTT_ERR_UNSUPPORTED (-7)  /* size outside what the kernels support (e.g. bond > 160) */
+
+#define QTT_HOST 0                /* pointer is host memory */
+#define QTT_DEVICE 1              /* pointer is device memory of the context's device */
+
+#define QTT_ORDER_SEQUENTIAL 0    /* eta bits of i first, then xi bits of j (Sec. III.B.1) */
+#define QTT_ORDER_INTERLEAVED 1   /* eta and xi bits alternate, level by level */
+
+typedef struct qtt_ctx qtt_ctx;
+typedef struct qtt_mps qtt_mps;
+typedef struct qtt_mpo qtt_mpo;
+typedef struct qtt_case qtt_case;
+
+/* Device allocator hooks: alloc(bytes, user) returns a device pointer or NULL; free(ptr, user). */
+typedef void* (*qtt_alloc_fn)(size_t bytes, void* user);
+typedef void (*qtt_free_fn)(void* ptr, void* user);
+
+/* Truncation rule of every rounding (Sec. II: keep the first chi singular values, or those
+ * above a threshold): keep k = min(chi_max, structural rank, #{sigma_i > rel_tol sigma_1});
+ * rel_tol = 0 keeps the structural count (fixed bond profile min(2^k, 2^(n-k), chi_max)). */
+typedef struct {
+  int chi_max;
+  double rel_tol;
+} qtt_trunc;
+
+typedef struct {
+  int max_bond;            /* largest bond of the result */
+  double norm;             /* ||result||_2 (device-computed; valid after qtt_ctx_sync) */
+} qtt_round_info;
+
+/* Options of the single-site ALS solver (Sec. II.A.4). */
+typedef struct {
+  int sweeps;              /* full sweeps (left-to-right + right-to-left) */
+  int cg_iters;            /* CG iteration budget per site */
+  double cg_tol;           /* CG stops early when ||r|| <= cg_tol ||b_local|| */
+} qtt_solve_opts;
+
+typedef struct {
+  int cg_iters_total;      /* CG iterations spent (all sites, all sweeps) */
+  double rel_residual;     /* ||A x - b|| / ||b|| after the last sweep, or -1 if not computed */
+} qtt_solve_info;
+
+/* ------------------------------------------------------------------------------ context */
+
+/* Create a context on `device` that enqueues on `cuda_stream` (a cudaStream_t, may be NULL
+ * for the legacy default stream).  alloc/free may be NULL (cudaMalloc/cudaFree are used). */
+int qtt_ctx_create(qtt_ctx** out, int device, void* cuda_stream, qtt_alloc_fn alloc,
+                   qtt_free_fn free_fn, void* user);
+void qtt_ctx_destroy(qtt_ctx* ctx);
+/* Block the host until all work enqueued on the context's stream has finished. */
+int qtt_ctx_sync(qtt_ctx* ctx);
+/* Message of the last error on the calling thread ("" if none). */
+const char* qtt_last_error(void);
+/* Number of kernels this context has launched so far (all entry points). */
+int64_t qtt_ctx_kernel_launches(qtt_ctx* ctx);
+/* Bytes currently held by the context's device pool (in use + cached). */
+size_t qtt_ctx_pool_bytes(qtt_ctx* ctx);
+
+/* ------------------------------------------------------------------------ MPS and MPO */
+
+/* New MPS with n cores of physical size d and bonds[0..n] (bonds[0] = bonds[n] = 1), its
+ * cores copied from `cores` (all cores concatenated, each row-major; kind QTT_HOST or
+ * QTT_DEVICE).  `cores` may be NULL: the cores are then zero. */
+int qtt_mps_create(qtt_ctx* ctx, int n, int d, const int* bonds, const double* cores, int kind,
+                   qtt_mps** out);
+int qtt_mps_free(qtt_mps* x);
+int qtt_mps_n(const qtt_mps* x);
+int qtt_mps_d(const qtt_mps* x);
+/* Copy the n+1 bonds into bonds_out. */
+int qtt_mps_bonds(const qtt_mps* x, int* bonds_out);
+/* Total number of stored values (NVPS_TT, Sec. IV). */
+int64_t qtt_mps_size(const qtt_mps* x);
+/* Copy all cores (concatenated) to `dst` (kind QTT_HOST or QTT_DEVICE); synchronous for host. */
+int qtt_mps_get_cores(const qtt_mps* x, double* dst, int kind);
+/* Device pointer of the concatenated cores (valid while x lives). */
+const double* qtt_mps_device_ptr(const qtt_mps* x);
+int qtt_mps_copy(const qtt_mps* x, qtt_mps** out);
+
+int qtt_mpo_create(qtt_ctx* ctx, int n, int d, const int* bonds, const double* cores, int kind,
+                   qtt_mpo** out);
+int qtt_mpo_free(qtt_mpo* m);
+int qtt_mpo_bonds(const qtt_mpo* m, int* bonds_out);
+int qtt_mpo_get_cores(const qtt_mpo* m, double* dst, int kind);
+
+/* ------------------------------------------------------------------ TT operations (Sec. II) */
+
+/* TT-SVD of a dense vector of d^n values (Fig. 1), swept right to left, truncated by `tr`.
+ * `dense` (kind QTT_HOST or QTT_DEVICE) is indexed with core 1 as the most significant digit
+ * (for 2-D fields use qtt_field_to_vector first). */
+int qtt_encode(qtt_ctx* ctx, const double* dense, int kind, int n, int d, qtt_trunc tr,
+               qtt_mps** out, qtt_round_info* info);
+/* Dense reconstruction (d^n values) into `dense` (kind QTT_HOST or QTT_DEVICE).  Tests only;
+ * n <= 26. */
+int qtt_decode(qtt_ctx* ctx, const qtt_mps* x, double* dense, int kind);
+/* Reorder a 2^n_eta x 2^n_xi row-major field into the QTT vector index of `ordering`
+ * (Sec. III.B.1) or back (inverse = 1).  Device or host buffers of 2^(n_eta+n_xi) doubles. */
+int qtt_field_to_vector(qtt_ctx* ctx, const double* src, double* dst, int kind, int n_eta,
+                        int n_xi, int ordering, int inverse);
+
+/* TT-rounding of x (Sec. II.A): exact TT-SVD semantics, right-to-left. */
+int qtt_round(qtt_ctx* ctx, const qtt_mps* x, qtt_trunc tr, qtt_mps** out, qtt_round_info* info);
+/* z = round(alpha x + beta y): direct sum of the cores (Sec. II.A.1) then TT-rounding. */
+int mps_axpby_round(qtt_ctx* ctx, double alpha, const qtt_mps* x, double beta, const qtt_mps* y,
+                    qtt_trunc tr, qtt_mps** out, qtt_round_info* info);
+/* y = round(M x): core-wise contraction over the physical index (Sec. II.A.2) then
+ * TT-rounding, the rounding done on Gram environments so the bond chi*w product is never
+ * orthogonalised explicitly. */
+int mpo_apply_round(qtt_ctx* ctx, const qtt_mpo* M, const qtt_mps* x, qtt_trunc tr,
+                    qtt_mps** out, qtt_round_info* info);
+/* c ~ a (.) b (Sec. II.A.3) at the bond profile of `tr`, by the variational fit of Table I:
+ * start from `init` (right-canonical, may be NULL: a right-to-left zip-up of a (.) b is used),
+ * then `sweeps` fit sweeps. */
+int mps_hadamard_round(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, qtt_trunc tr,
+                       const qtt_mps* init, int sweeps, qtt_mps** out, qtt_round_info* info);
+/* Symmetric eigendecomposition of a small dense matrix (n <= 160), the building block of every
+ * Gram-based rounding: FP32 Jacobi sweeps refined to FP64 accuracy.  S (n x n row-major,
+ * symmetric), w (n, descending) and V (n x n row-major, eigenvectors as columns) are host
+ * buffers owned by the caller; synchronous. */
+int qtt_sym_eig(qtt_ctx* ctx, int n, const double* S, double* w, double* V);
+/* <a, b> into *out_host (synchronous). */
+int mps_dot(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, double* out_host);
+
+/* Solve A x = b for SPD A by single-site ALS (Sec. II.A.4, Sec. III.C): x_inout is the warm
+ * start and receives the solution (its bond profile is kept).  The residual is computed when
+ * info != NULL (costs one extra contraction sweep); QTT_ERR_NOT_CONVERGED is returned when
+ * tol > 0 and the relative residual stays above tol. */
+int poisson_solve(qtt_ctx* ctx, const qtt_mpo* A, const qtt_mps* b, qtt_mps* x_inout,
+                  const qtt_solve_opts* opts, double tol, qtt_solve_info* info);
+
+/* -------------------------------------------------------- cylinder case (Sec. III, IV) */
+
+typedef struct {
+  int n_eta, n_xi;         /* 2^n_eta radial x 2^n_xi angular interior nodes */
+  int ordering;            /* QTT_ORDER_* */
+  double D;                /* cylinder diameter (1) */
+  double R;                /* outer / inner diameter ratio D_outer / D (App. E) */
+  double Re, dt;           /* Reynolds number, fixed time step (Sec. III.C) */
+  double rot;              /* wall rotation rate: u_G = rot sin(theta), v_G = -rot cos(theta) */
+  double u_inf;            /* far-field velocity (u_inf, 0) */
+  int chi;                 /* bond cap of u, v, p and of every rounding in the step */
+  int fit_sweeps;          /* sweeps of each variational fit in the step */
+  qtt_solve_opts mom, poi; /* ALS options of the momentum and Poisson solves */
+} qtt_case_params;
+
+typedef struct {
+  int cg_u, cg_v, cg_p;    /* CG iterations of the three solves */
+  double cd, cl;           /* drag and lift coefficients after the step (eq:liftdrag) */
+} qtt_step_info;
+
+/* Build grid, analytic metric terms, operators (rounded at 1e-14) and boundary vectors
+ * (Sec. III.B.3, App. A, App. E).  Blocks the host (operator ranks are data dependent). */
+int qtt_case_create(qtt_ctx* ctx, const qtt_case_params* p, qtt_case** out);
+int qtt_case_free(qtt_case* c);
+/* Set the flow state (copies; p may be NULL: a zero pressure padded with tiny seeded noise
+ * from `p_pad`, which must then have the bond profile of chi). */
+int qtt_case_set_state(qtt_case* c, const qtt_mps* u, const qtt_mps* v, const qtt_mps* p);
+/* Copies of the current state. */
+int qtt_case_get_state(qtt_case* c, qtt_mps** u, qtt_mps** v, qtt_mps** p);
+/* Operator access for tests: which = 0 Dx, 1 Dz, 2 Dx^p, 3 Dz^p, 4 H, 5 A_p, 6 P_x, 7 P_z.
+ * Returns a copy. */
+int qtt_case_get_operator(qtt_case* c, int which, qtt_mpo** out);
+/* Boundary vectors for tests: which = 0 bcx_u, 1 bcz_u, 2 bcx_v, 3 bcz_v, 4 |J| bcLap_u,
+ * 5 |J| bcLap_v, 6 bc_div (weighted), 7 |J|.  *out = NULL when the vector is identically zero. */
+int qtt_case_get_vector(qtt_case* c, int which, qtt_mps** out);
+/* Advance nsteps fractional steps (Sec. III.C); per_step (may be NULL) receives nsteps
+ * records, valid after qtt_ctx_sync.  Forces are evaluated when with_forces != 0. */
+int fractional_step(qtt_ctx* ctx, qtt_case* c, int nsteps, int with_forces,
+                    qtt_step_info* per_step);
+/* Drag and lift of the current state (App. F; synchronous). */
+int qtt_case_forces(qtt_ctx* ctx, qtt_case* c, double* cd, double* cl);
+/* Strouhal number from upward zero crossings of C_L(t) (eq:st); host-only arithmetic on a
+ * scalar time series. */
+int qtt_strouhal(const double* t, const double* cl, int n, double* st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1046 @@
+// TT algebra of the QTT fractional-step method (arXiv:2507.05222, Sec. II) on the GPU:
+// rounding, sums, MPO-MPS products, Hadamard products (variational fit, Table I), the
+// single-site ALS solver (Sec. II.A.4), inner products, dense encode/decode (Fig. 1).
+//
+// Every operation is a host-side sequence of device kernels on the context stream; the host
+// never waits on the device inside an operation except where a data-dependent bond must be
+// known (rel_tol > 0 rounding, used at operator set-up).
+#include <algorithm>
+#include <cmath>
+#include <memory>
+
+#include "qtt_algebra.h"
+
+namespace qtt {
+
+// ------------------------------------------------------------------ handles
+
+qtt_mps* new_mps(Ctx* c, int n, int d, const std::vector<int>& bonds) {
+  QTT_CHECK_ARG(n >= 1 && d >= 1 && int(bonds.size()) == n + 1, "mps: bad shape");
+  std::unique_ptr<qtt_mps> x(new qtt_mps);
+  x->ctx = c;
+  x->n = n;
+  x->d = d;
+  x->bonds = bonds;
+  x->off.assign(n + 1, 0);
+  int64_t tot = 0;
+  for (int k = 0; k < n; ++k) {
+    QTT_CHECK_ARG(bonds[k] >= 1 && bonds[k + 1] >= 1, "mps: bonds must be >= 1");
+    x->off[k] = tot;
+    int64_t sz = int64_t(bonds[k]) * d * bonds[k + 1];
+    tot += (sz + 3) / 4 * 4;  // 32-byte aligned cores
+  }
+  x->off[n] = tot;
+  x->buf.reset(c, size_t(tot));
+  return x.release();
+}
+
+qtt_mpo* new_mpo(Ctx* c, int n, int d, const std::vector<int>& bonds) {
+  QTT_CHECK_ARG(n >= 1 && d >= 1 && int(bonds.size()) == n + 1, "mpo: bad shape");
+  std::unique_ptr<qtt_mpo> m(new qtt_mpo);
+  m->ctx = c;
+  m->n = n;
+  m->d = d;
+  m->bonds = bonds;
+  m->off.assign(n + 1, 0);
+  int64_t tot = 0;
+  for (int k = 0; k < n; ++k) {
+    m->off[k] = tot;
+    int64_t sz = int64_t(bonds[k]) * d * d * bonds[k + 1];
+    tot += (sz + 3) / 4 * 4;
+  }
+  m->off[n] = tot;
+  m->buf.reset(c, size_t(tot));
+  return m.release();
+}
+
+void free_mps(qtt_mps* x) { delete x; }
+void free_mpo(qtt_mpo* m) { delete m; }
+
+// ------------------------------------------------------------------ small kernels
+
+namespace {
+
+int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  return int(std::max<int64_t>(1, std::min<int64_t>(g, 65535 * 8)));
+}
+
+// Core k of alpha x (+) beta y (Sec. II.A.1): first core [ax | by], last [x ; y], middle
+// block diagonal; alpha/beta are applied on the first core only.
+__global__ void k_direct_sum(const double* __restrict__ X, int xr0, int xr1, const double* __restrict__ Y, int yr0,
+                             int yr1, int d, int first, int last, double alpha, double beta, double* __restrict__ Z) {
+  int zr0 = first ? 1 : xr0 + yr0;
+  int zr1 = last ? 1 : xr1 + yr1;
+  int64_t total = int64_t(zr0) * d * zr1;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    int a = int(e / (int64_t(d) * zr1));
+    int s = int((e / zr1) % d);
+    int b = int(e % zr1);
+    double v = 0.0;
+    if (first && last) {
+      v = alpha * X[s] + beta * Y[s];
+    } else if (first) {
+      v = (b < xr1) ? alpha * X[s * xr1 + b] : beta * Y[s * yr1 + (b - xr1)];
+    } else if (last) {
+      v = (a < xr0) ? X[a * d + s] : Y[(a - xr0) * d + s];
+    } else {
+      if (a < xr0 && b < xr1) v = X[(int64_t(a) * d + s) * xr1 + b];
+      else if (a >= xr0 && b >= xr1) v = Y[(int64_t(a - xr0) * d + s) * yr1 + (b - xr1)];
+    }
+    Z[e] = v;
+  }
+}
+
+// diag(a) as an MPO core: W(a, s', s, b) = delta_{s s'} A(a, s, b) (copy tensor, Sec. II.A.3).
+__global__ void k_diag_core(const double* __restrict__ A, int r0, int d, int r1, double* __restrict__ W) {
+  int64_t total = int64_t(r0) * d * d * r1;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    int b = int(e % r1);
+    int s = int((e / r1) % d);
+    int so = int((e / (int64_t(r1) * d)) % d);
+    int a = int(e / (int64_t(r1) * d * d));
+    W[e] = (s == so) ? A[(int64_t(a) * d + s) * r1 + b] : 0.0;
+  }
+}
+
+// Single-block fused CG update (Sec. II.A.4 local solve).  State: [0] rr, [1] bb, [2] tol^2,
+// [3] active flag (as int in a double slot), [4] iteration count.
+struct CGState {
+  double rr, bb, tol2;
+  int active;
+  int count;
+};
+
+__device__ double block_sum_d(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// r = b - Ax (Ax given), p = r, rr = r.r, bb = b.b, active = rr > tol^2 bb and rr > 0.
+__global__ void __launch_bounds__(1024) k_cg_init(int64_t n, const double* __restrict__ b, const double* __restrict__ Ax,
+                                                  double* __restrict__ r, double* __restrict__ p, CGState* st,
+                                                  double tol2) {
+  __shared__ double red[32];
+  double rr = 0, bb = 0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    double re = b[e] - Ax[e];
+    r[e] = re;
+    p[e] = re;
+    rr += re * re;
+    bb += b[e] * b[e];
+  }
+  rr = block_sum_d(rr, red);
+  bb = block_sum_d(bb, red);
+  if (threadIdx.x == 0) {
+    st->rr = rr;
+    st->bb = bb;
+    st->tol2 = tol2;
+    st->active = (rr > tol2 * bb && rr > 0.0) ? 1 : 0;
+    st->count = 0;
+  }
+}
+
+// One CG iteration after Ap = A p: alpha = rr / pAp, x += alpha p, r -= alpha Ap,
+// beta = rr'/rr, p = r + beta p; then the stopping test.
+__global__ void __launch_bounds__(1024) k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                    double* __restrict__ p, const double* __restrict__ Ap,
+                                                    CGState* st) {
+  __shared__ double red[32];
+  if (!st->active) return;
+  double pap = 0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) pap += p[e] * Ap[e];
+  pap = block_sum_d(pap, red);
+  const double rr = st->rr;
+  if (!(pap > 0.0)) {
+    __syncthreads();
+    if (threadIdx.x == 0) st->active = 0;
+    return;
+  }
+  const double alpha = rr / pap;
+  double rn = 0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    x[e] += alpha * p[e];
+    double re = r[e] - alpha * Ap[e];
+    r[e] = re;
+    rn += re * re;
+  }
+  rn = block_sum_d(rn, red);
+  const double beta = rn / rr;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) p[e] = r[e] + beta * p[e];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->rr = rn;
+    st->count += 1;
+    st->active = (rn > st->tol2 * st->bb && rn > 0.0) ? 1 : 0;
+  }
+}
+
+__global__ void k_cg_accumulate(const CGState* st, int* total) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *total += st->count;
+}
+
+__global__ void k_sqrt(const double* in, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = sqrt(fmax(*in, 0.0));
+}
+
+__global__ void k_set_int(int* p, int v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
+}  // namespace
+
+void sqrt_dev(Ctx& c, const double* in, double* out) {
+  k_sqrt<<<1, 1, 0, c.stream>>>(in, out);
+  after_launch(c, "sqrt");
+}
+
+void direct_sum_core(Ctx& c, const double* X, int xr0, int xr1, const double* Y, int yr0, int yr1, int d, bool first,
+                     bool last, double alpha, double beta, double* Z, int64_t zsize) {
+  k_direct_sum<<<grid_for(zsize, 256), 256, 0, c.stream>>>(X, xr0, xr1, Y, yr0, yr1, d, first ? 1 : 0, last ? 1 : 0,
+                                                           alpha, beta, Z);
+  after_launch(c, "direct_sum");
+}
+
+qtt_mps* direct_sum(Ctx& c, double alpha, const qtt_mps* x, double beta, const qtt_mps* y) {
+  QTT_CHECK_ARG(x->n == y->n && x->d == y->d, "direct sum: shape mismatch");
+  const int n = x->n, d = x->d;
+  std::vector<int> b(n + 1);
+  b[0] = 1;
+  b[n] = 1;
+  for (int k = 1; k < n; ++k) b[k] = x->bonds[k] + y->bonds[k];
+  qtt_mps* z = new_mps(&c, n, d, b);
+  for (int k = 0; k < n; ++k)
+    direct_sum_core(c, x->core(k), x->bonds[k], x->bonds[k + 1], y->core(k), y->bonds[k], y->bonds[k + 1], d, k == 0,
+                    k == n - 1, alpha, beta, z->core(k), int64_t(b[k]) * d * b[k + 1]);
+  return z;
+}
+
+qtt_mpo* diag_mpo(Ctx& c, const qtt_mps* a) {
+  qtt_mpo* m = new_mpo(&c, a->n, a->d, a->bonds);
+  for (int k = 0; k < a->n; ++k) {
+    int64_t tot = int64_t(a->bonds[k]) * a->d * a->d * a->bonds[k + 1];
+    k_diag_core<<<grid_for(tot, 256), 256, 0, c.stream>>>(a->core(k), a->bonds[k], a->d, a->bonds[k + 1], m->core(k));
+    after_launch(c, "diag_core");
+  }
+  return m;
+}
+
+// y = M x without rounding: B[k]((a w), s', (b v)) = sum_s M[k](w, s', s, v) A[k](a, s, b)
+// (Sec. II.A.2; fused bond index (x-bond slow, MPO-bond fast)).
+qtt_mps* mpo_mps_exact(Ctx& c, const qtt_mpo* M, const qtt_mps* x) {
+  QTT_CHECK_ARG(M->n == x->n && M->d == x->d, "mpo-mps: shape mismatch");
+  const int n = x->n, d = x->d;
+  std::vector<int> b(n + 1);
+  for (int k = 0; k <= n; ++k) b[k] = x->bonds[k] * M->bonds[k];
+  qtt_mps* y = new_mps(&c, n, d, b);
+  for (int k = 0; k < n; ++k) {
+    int a0 = x->bonds[k], a1 = x->bonds[k + 1], w0 = M->bonds[k], w1 = M->bonds[k + 1];
+    einsum(c, "wtsv,asb->awtbv", 1.0, tv(M->core(k), {w0, d, d, w1}), tv(x->core(k), {a0, d, a1}), 0.0,
+           tv(y->core(k), {a0, w0, d, a1, w1}));
+  }
+  return y;
+}
+
+qtt_mpo* mpo_mpo_exact(Ctx& c, const qtt_mpo* A, const qtt_mpo* B) {
+  QTT_CHECK_ARG(A->n == B->n && A->d == B->d, "mpo-mpo: shape mismatch");
+  const int n = A->n, d = A->d;
+  std::vector<int> b(n + 1);
+  for (int k = 0; k <= n; ++k) b[k] = A->bonds[k] * B->bonds[k];
+  qtt_mpo* m = new_mpo(&c, n, d, b);
+  for (int k = 0; k < n; ++k) {
+    int a0 = A->bonds[k], a1 = A->bonds[k + 1], b0 = B->bonds[k], b1 = B->bonds[k + 1];
+    einsum(c, "asrb,crtd->acstbd", 1.0, tv(A->core(k), {a0, d, d, a1}), tv(B->core(k), {b0, d, d, b1}), 0.0,
+           tv(m->core(k), {a0, b0, d, d, a1, b1}));
+  }
+  return m;
+}
+
+qtt_mps* mps_copy(Ctx& c, const qtt_mps* x) {
+  qtt_mps* y = new_mps(&c, x->n, x->d, x->bonds);
+  copy(c, y->buf.p, x->buf.p, x->off[x->n]);
+  return y;
+}
+
+void mps_scale(Ctx& c, qtt_mps* x, double s) { axpby(c, x->core_size(0), 0.0, x->core(0), s, x->core(0)); }
+
+// View an MPO as an MPS with physical dimension d^2 (no copy of values; a new handle).
+qtt_mps* mpo_as_mps(Ctx& c, const qtt_mpo* m) {
+  qtt_mps* x = new_mps(&c, m->n, m->d * m->d, m->bonds);
+  copy(c, x->buf.p, m->buf.p, m->off[m->n]);
+  return x;
+}
+
+qtt_mpo* mps_as_mpo(Ctx& c, const qtt_mps* x, int d) {
+  QTT_CHECK_ARG(x->d == d * d, "mps_as_mpo: physical size");
+  qtt_mpo* m = new_mpo(&c, x->n, d, x->bonds);
+  copy(c, m->buf.p, x->buf.p, x->off[x->n]);
+  return m;
+}
+
+// ------------------------------------------------------------------ structural ranks
+
+std::vector<int> left_struct(const std::vector<int>& pre, int d) {
+  std::vector<int> m(pre.size());
+  m[0] = 1;
+  for (size_t k = 1; k < pre.size(); ++k) {
+    int64_t v = std::min<int64_t>(pre[k], int64_t(d) * m[k - 1]);
+    m[k] = int(v);
+  }
+  return m;
+}
+
+static int kept(const std::vector<double>& sig, int chi, double eps, int strct) {
+  int b = std::min<int>(chi, strct);
+  b = std::min<int>(b, int(sig.size()));
+  if (eps > 0.0 && !sig.empty()) {
+    int cnt = 0;
+    for (double s : sig)
+      if (s > eps * sig[0]) ++cnt;
+    b = std::min(b, cnt);
+  }
+  return std::max(b, 1);
+}
+
+// ------------------------------------------------------------------ accurate rounding (QR + SVD)
+// TT-rounding (Sec. II.A): left-to-right Householder QR, right-to-left truncated SVD
+// (one-sided Jacobi, FP64).  Reads singular values on the host at every cut.
+
+qtt_mps* round_svd(Ctx& c, const qtt_mps* x_in, int chi, double eps) {
+  const int n = x_in->n, d = x_in->d;
+  std::vector<int> pre = x_in->bonds;
+  std::vector<int> m = left_struct(pre, d);
+  // working copy of the cores with the current bonds
+  std::vector<DBuf> core(n);
+  std::vector<int> b = pre;
+  for (int k = 0; k < n; ++k) {
+    core[k].reset(&c, size_t(x_in->core_size(k)) + 4);
+    copy(c, core[k].p, x_in->core(k), int64_t(b[k]) * d * b[k + 1]);
+  }
+  // left-to-right orthogonalisation
+  for (int k = 0; k + 1 < n; ++k) {
+    int rows = b[k] * d, cols = b[k + 1];
+    int kk = std::min(rows, cols);
+    DBuf Q(&c, size_t(rows) * kk), R(&c, size_t(kk) * cols);
+    qr(c, 1, rows, cols, 0, core[k].p, 0, Q.p, 0, R.p, 0);
+    core[k] = std::move(Q);
+    DBuf nxt(&c, size_t(kk) * d * b[k + 2]);
+    einsum(c, "ab,bsc->asc", 1.0, tv(R.p, {kk, cols}), tv(core[k + 1].p, {cols, d, b[k + 2]}), 0.0,
+           tv(nxt.p, {kk, d, b[k + 2]}));
+    core[k + 1] = std::move(nxt);
+    b[k + 1] = kk;
+  }
+  // right-to-left truncation
+  std::vector<int> out_b(n + 1);
+  out_b[0] = 1;
+  out_b[n] = 1;
+  for (int k = n - 1; k >= 1; --k) {
+    int r0 = b[k], r1 = out_b[k + 1];
+    int cols = d * r1;
+    // Y = core (r0 x cols).  SVD of the taller orientation.
+    int mm = std::max(r0, cols), nn = std::min(r0, cols);
+    DBuf U(&c, size_t(mm) * nn), S(&c, size_t(nn)), V(&c, size_t(nn) * nn), T(&c, size_t(r0) * cols);
+    bool tall = r0 >= cols;
+    if (tall) {
+      svd_small(c, r0, cols, core[k].p, U.p, S.p, V.p);  // Y = U S V^T, right vectors = V columns
+    } else {
+      int64_t dims[2] = {r0, cols};
+      int perm[2] = {1, 0};
+      permute(c, core[k].p, 2, dims, perm, T.p, 1.0, 0.0);  // Y^T (cols x r0)
+      svd_small(c, cols, r0, T.p, U.p, S.p, V.p);           // Y^T = U S V^T: right vectors of Y = U columns
+    }
+    std::vector<double> sig(nn);
+    QTT_CUDA(cudaMemcpyAsync(sig.data(), S.p, nn * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    QTT_CUDA(cudaStreamSynchronize(c.stream));
+    int nz = 0;
+    for (double s : sig)
+      if (s > 0.0) ++nz;
+    int bk = kept(sig, chi, eps, std::min(m[k], cols));
+    bk = std::max(1, std::min(bk, std::max(nz, 1)));
+    DBuf newcore(&c, size_t(bk) * cols), carry(&c, size_t(r0) * bk);
+    // right singular vectors (cols x bk) -> new core = their transpose (bk x cols);
+    // carry = left vectors * S (r0 x bk)
+    const double* Rv = tall ? V.p : U.p;        // (cols x nn) row-major, first bk columns
+    const double* Lv = tall ? U.p : V.p;        // (r0 x nn)
+    QTT_CUDA(cudaMemcpy2DAsync(T.p, bk * sizeof(double), Rv, nn * sizeof(double), bk * sizeof(double), cols,
+                               cudaMemcpyDeviceToDevice, c.stream));
+    {
+      int64_t dims[2] = {cols, bk};
+      int perm[2] = {1, 0};
+      permute(c, T.p, 2, dims, perm, newcore.p, 1.0, 0.0);
+    }
+    QTT_CUDA(cudaMemcpy2DAsync(carry.p, bk * sizeof(double), Lv, nn * sizeof(double), bk * sizeof(double), r0,
+                               cudaMemcpyDeviceToDevice, c.stream));
+    // scale columns by S: carry (r0 x bk) = carry * diag(S[:bk]) via einsum with a diag
+    {
+      DBuf Dg(&c, size_t(bk) * bk);
+      fill(c, Dg.p, int64_t(bk) * bk, 0.0);
+      QTT_CUDA(cudaMemcpy2DAsync(Dg.p, (bk + 1) * sizeof(double), S.p, sizeof(double), sizeof(double), bk,
+                                 cudaMemcpyDeviceToDevice, c.stream));
+      DBuf cs(&c, size_t(r0) * bk);
+      einsum(c, "ab,bc->ac", 1.0, tv(carry.p, {r0, bk}), tv(Dg.p, {bk, bk}), 0.0, tv(cs.p, {r0, bk}));
+      DBuf prev(&c, size_t(b[k - 1]) * d * bk);
+      einsum(c, "asb,bc->asc", 1.0, tv(core[k - 1].p, {b[k - 1], d, r0}), tv(cs.p, {r0, bk}), 0.0,
+             tv(prev.p, {b[k - 1], d, bk}));
+      core[k - 1] = std::move(prev);
+    }
+    core[k] = std::move(newcore);
+    out_b[k] = bk;
+  }
+  qtt_mps* y = new_mps(&c, n, d, out_b);
+  for (int k = 0; k < n; ++k) copy(c, y->core(k), core[k].p, int64_t(out_b[k]) * d * out_b[k + 1]);
+  return y;
+}
+
+// ------------------------------------------------------------------ Gram rounding
+// Right-to-left TT-SVD of an explicit TT through left Gram matrices G_k = Y_{<k}^T Y_{<k}
+// (density-matrix form): at core k, Z = Y[k] P_{k+1}, rho = Z^T G_k Z (d b x d b), the top
+// b_k eigenvectors of rho are the new core (right singular vectors of the unfolding), and
+// P_k = Z V.  Only (d chi)-sized eigenproblems appear, never the (pre-round) bond.
+
+static std::vector<double> host_copy(Ctx& c, const double* p, int n) {
+  std::vector<double> h(n);
+  QTT_CUDA(cudaMemcpyAsync(h.data(), p, n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  return h;
+}
+
+static int choose_rank(Ctx& c, const double* w_dev, int nw, int chi, double eps, int strct) {
+  int b = std::min(std::min(chi, strct), nw);
+  if (eps > 0.0) {
+    std::vector<double> w = host_copy(c, w_dev, nw);
+    std::vector<double> sig(nw);
+    for (int i = 0; i < nw; ++i) sig[i] = std::sqrt(std::max(w[i], 0.0));
+    b = kept(sig, chi, eps, strct);
+  }
+  return std::max(b, 1);
+}
+
+// Take the first b columns of V (nv x nv, row-major) as the rows of a (b x nv) core.
+static void top_vectors_as_core(Ctx& c, const double* V, int nv, int b, double* core_out) {
+  DBuf T(&c, size_t(nv) * b);
+  QTT_CUDA(cudaMemcpy2DAsync(T.p, b * sizeof(double), V, nv * sizeof(double), b * sizeof(double), nv,
+                             cudaMemcpyDeviceToDevice, c.stream));
+  int64_t dims[2] = {nv, b};
+  int perm[2] = {1, 0};
+  permute(c, T.p, 2, dims, perm, core_out, 1.0, 0.0);
+}
+
+qtt_mps* round_gram(Ctx& c, const qtt_mps* y, int chi, double eps) {
+  const int n = y->n, d = y->d;
+  const std::vector<int>& R = y->bonds;
+  std::vector<int> m = left_struct(R, d);
+  if (n == 1) return mps_copy(c, y);
+  // left Grams G_k (R_k x R_k), k = 0..n-1
+  std::vector<DBuf> G(n);
+  G[0].reset(&c, 1);
+  fill(c, G[0].p, 1, 1.0);
+  for (int k = 0; k + 1 < n; ++k) {
+    int a0 = R[k], a1 = R[k + 1];
+    DBuf T(&c, size_t(a0) * d * a1);
+    einsum(c, "aA,asb->Asb", 1.0, tv(G[k].p, {a0, a0}), tv(y->core(k), {a0, d, a1}), 0.0, tv(T.p, {a0, d, a1}));
+    G[k + 1].reset(&c, size_t(a1) * a1);
+    einsum(c, "Asb,AsB->bB", 1.0, tv(T.p, {a0, d, a1}), tv(y->core(k), {a0, d, a1}), 0.0, tv(G[k + 1].p, {a1, a1}));
+  }
+  std::vector<int> ob(n + 1);
+  ob[0] = 1;
+  ob[n] = 1;
+  std::vector<DBuf> out(n);
+  DBuf P(&c, 1);
+  fill(c, P.p, 1, 1.0);
+  for (int k = n - 1; k >= 0; --k) {
+    int a0 = R[k], a1 = R[k + 1], c1 = ob[k + 1];
+    DBuf Z(&c, size_t(a0) * d * c1);
+    einsum(c, "asb,bc->asc", 1.0, tv(y->core(k), {a0, d, a1}), tv(P.p, {a1, c1}), 0.0, tv(Z.p, {a0, d, c1}));
+    if (k == 0) {
+      out[0] = std::move(Z);
+      break;
+    }
+    const int nv = d * c1;
+    DBuf T(&c, size_t(a0) * nv), rho(&c, size_t(nv) * nv), w(&c, size_t(nv)), V(&c, size_t(nv) * nv);
+    einsum(c, "aA,asc->Asc", 1.0, tv(G[k].p, {a0, a0}), tv(Z.p, {a0, d, c1}), 0.0, tv(T.p, {a0, d, c1}));
+    einsum(c, "Asc,AtD->sctD", 1.0, tv(T.p, {a0, d, c1}), tv(Z.p, {a0, d, c1}), 0.0, tv(rho.p, {d, c1, d, c1}));
+    eigh(c, nv, rho.p, w.p, V.p);
+    int bk = choose_rank(c, w.p, nv, chi, eps, std::min(m[k], nv));
+    out[k].reset(&c, size_t(bk) * nv);
+    top_vectors_as_core(c, V.p, nv, bk, out[k].p);
+    // P_k = Z V[:, :bk]  (a0 x bk)
+    DBuf Pn(&c, size_t(a0) * bk);
+    gemm(c, 1, a0, bk, nv, 1.0, Z.p, 0, nv, 1, V.p, 0, nv, 1, 0.0, Pn.p, 0, bk, 1);
+    P = std::move(Pn);
+    ob[k] = bk;
+  }
+  qtt_mps* z = new_mps(&c, n, d, ob);
+  for (int k = 0; k < n; ++k) copy(c, z->core(k), out[k].p, int64_t(ob[k]) * d * ob[k + 1]);
+  return z;
+}
+
+// Gram rounding of y = M x without forming y: the left Gram of y at bond k is kept in the
+// factored index (w, a, w', a'), and Z = (M x)[k] P is contracted from M[k], X[k] directly.
+qtt_mps* apply_round_gram(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, double eps) {
+  const int n = x->n, d = x->d;
+  QTT_CHECK_ARG(M->n == n && M->d == d, "apply: shape mismatch");
+  std::vector<int> R(n + 1);
+  for (int k = 0; k <= n; ++k) R[k] = M->bonds[k] * x->bonds[k];
+  std::vector<int> mstruct = left_struct(R, d);
+  if (n == 1) {
+    qtt_mps* y = mpo_mps_exact(c, M, x);
+    return y;
+  }
+  std::vector<DBuf> G(n);
+  G[0].reset(&c, 1);
+  fill(c, G[0].p, 1, 1.0);
+  for (int k = 0; k + 1 < n; ++k) {
+    int w0 = M->bonds[k], w1 = M->bonds[k + 1], a0 = x->bonds[k], a1 = x->bonds[k + 1];
+    TV g = tv(G[k].p, {w0, a0, w0, a0});
+    TV X = tv(x->core(k), {a0, d, a1});
+    TV W = tv(M->core(k), {w0, d, d, w1});
+    DBuf T1(&c, size_t(w0) * w0 * a0 * d * a1);
+    einsum(c, "waWA,atb->wWAtb", 1.0, g, X, 0.0, tv(T1.p, {w0, w0, a0, d, a1}));
+    DBuf T2(&c, size_t(w0) * a0 * a1 * d * w1);
+    einsum(c, "wWAtb,wstv->WAbsv", 1.0, tv(T1.p, {w0, w0, a0, d, a1}), W, 0.0, tv(T2.p, {w0, a0, a1, d, w1}));
+    DBuf T3(&c, size_t(a0) * a1 * w1 * d * w1);
+    einsum(c, "WAbsv,WsTV->AbvTV", 1.0, tv(T2.p, {w0, a0, a1, d, w1}), W, 0.0, tv(T3.p, {a0, a1, w1, d, w1}));
+    G[k + 1].reset(&c, size_t(w1) * a1 * w1 * a1);
+    einsum(c, "AbvTV,ATB->vbVB", 1.0, tv(T3.p, {a0, a1, w1, d, w1}), X, 0.0, tv(G[k + 1].p, {w1, a1, w1, a1}));
+  }
+  std::vector<int> ob(n + 1);
+  ob[0] = 1;
+  ob[n] = 1;
+  std::vector<DBuf> out(n);
+  DBuf P(&c, 1);  // (w_{k+1}, a_{k+1}, c_{k+1})
+  fill(c, P.p, 1, 1.0);
+  for (int k = n - 1; k >= 0; --k) {
+    int w0 = M->bonds[k], w1 = M->bonds[k + 1], a0 = x->bonds[k], a1 = x->bonds[k + 1], c1 = ob[k + 1];
+    TV X = tv(x->core(k), {a0, d, a1});
+    TV W = tv(M->core(k), {w0, d, d, w1});
+    DBuf T1(&c, size_t(a0) * d * w1 * c1);
+    einsum(c, "atb,vbc->atvc", 1.0, X, tv(P.p, {w1, a1, c1}), 0.0, tv(T1.p, {a0, d, w1, c1}));
+    DBuf Z(&c, size_t(w0) * a0 * d * c1);
+    einsum(c, "wstv,atvc->wasc", 1.0, W, tv(T1.p, {a0, d, w1, c1}), 0.0, tv(Z.p, {w0, a0, d, c1}));
+    if (k == 0) {
+      out[0] = std::move(Z);  // w0 = a0 = 1: (1, d, c1)
+      break;
+    }
+    const int nv = d * c1;
+    DBuf T2(&c, size_t(w0) * a0 * nv), rho(&c, size_t(nv) * nv), wv(&c, size_t(nv)), V(&c, size_t(nv) * nv);
+    einsum(c, "waWA,wasc->WAsc", 1.0, tv(G[k].p, {w0, a0, w0, a0}), tv(Z.p, {w0, a0, d, c1}), 0.0,
+           tv(T2.p, {w0, a0, d, c1}));
+    einsum(c, "WAsc,WASC->scSC", 1.0, tv(T2.p, {w0, a0, d, c1}), tv(Z.p, {w0, a0, d, c1}), 0.0,
+           tv(rho.p, {d, c1, d, c1}));
+    eigh(c, nv, rho.p, wv.p, V.p);
+    int bk = choose_rank(c, wv.p, nv, chi, eps, std::min(mstruct[k], nv));
+    out[k].reset(&c, size_t(bk) * nv);
+    top_vectors_as_core(c, V.p, nv, bk, out[k].p);
+    DBuf Pn(&c, size_t(w0) * a0 * bk);
+    gemm(c, 1, int64_t(w0) * a0, bk, nv, 1.0, Z.p, 0, nv, 1, V.p, 0, nv, 1, 0.0, Pn.p, 0, bk, 1);
+    P = std::move(Pn);
+    ob[k] = bk;
+  }
+  qtt_mps* z = new_mps(&c, n, d, ob);
+  for (int k = 0; k < n; ++k) copy(c, z->core(k), out[k].p, int64_t(ob[k]) * d * ob[k + 1]);
+  return z;
+}
+
+// The accurate path keeps every core unfolding in one CTA's shared memory.
+static bool svd_path_fits(const std::vector<int>& b, int d) {
+  for (size_t k = 0; k + 1 < b.size(); ++k) {
+    int64_t r0 = b[k], c = int64_t(d) * b[k + 1];
+    int64_t mm = std::max(r0, c), nn = std::min(r0, c);
+    if (mm * nn + nn * nn + 2 * nn > 26000) return false;
+    if (int64_t(b[k]) * d * b[k + 1] + int64_t(b[k]) * d + b[k + 1] > 26000) return false;
+  }
+  return true;
+}
+
+// Rounding dispatcher.  rel_tol = 0: Gram rounding (structural ranks, no host sync).
+// rel_tol > 0: thresholds below ~1e-7 sigma_1 cannot be resolved from Gram eigenvalues
+// (they square the singular values), so the threshold is applied by the accurate QR + SVD
+// path whenever the bonds (after a structural Gram pass, if needed) fit it.
+qtt_mps* round_any(Ctx& c, const qtt_mps* y, int chi, double eps) {
+  if (eps <= 0.0) return round_gram(c, y, chi, 0.0);
+  if (svd_path_fits(y->bonds, y->d)) return round_svd(c, y, chi, eps);
+  std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> z(round_gram(c, y, chi, 0.0), free_mps);
+  if (svd_path_fits(z->bonds, z->d)) return round_svd(c, z.get(), chi, eps);
+  return round_gram(c, z.get(), chi, eps);
+}
+
+// ------------------------------------------------------------------ right-orthonormalisation
+
+void right_orthonormalize(Ctx& c, qtt_mps* x) {
+  const int n = x->n, d = x->d;
+  for (int k = n - 1; k >= 1; --k) {
+    int r0 = x->bonds[k], r1 = x->bonds[k + 1];
+    int mrows = d * r1;  // QR of Y^T (d r1 x r0)
+    QTT_CHECK_ARG(mrows >= r0, "right_orthonormalize: bond larger than d * right bond");
+    DBuf Rm(&c, size_t(r0) * r0);
+    qr(c, 1, mrows, r0, 1, x->core(k), 0, x->core(k), 0, Rm.p, 0);
+    int p0 = x->bonds[k - 1];
+    DBuf prev(&c, size_t(p0) * d * r0);
+    einsum(c, "asb,cb->asc", 1.0, tv(x->core(k - 1), {p0, d, r0}), tv(Rm.p, {r0, r0}), 0.0, tv(prev.p, {p0, d, r0}));
+    copy(c, x->core(k - 1), prev.p, int64_t(p0) * d * r0);
+  }
+}
+
+// ------------------------------------------------------------------ fit engine (Table I)
+
+int Term::rbond(int k) const {
+  if (kind == VEC) return a->bonds[k];
+  if (kind == HAD) return a->bonds[k] * b->bonds[k];
+  return M->bonds[k] * a->bonds[k];
+}
+
+// Environment shapes: VEC (c, a); HAD (c, a, b); MPO (c, w, a).
+static size_t env_size(const Term& t, int cb, int k) {
+  if (t.kind == Term::VEC) return size_t(cb) * t.a->bonds[k];
+  if (t.kind == Term::HAD) return size_t(cb) * t.a->bonds[k] * t.b->bonds[k];
+  return size_t(cb) * t.M->bonds[k] * t.a->bonds[k];
+}
+
+// L_{k+1} from L_k and the new (left-orthonormal) core C of the fitted tensor at site k.
+static void env_left(Ctx& c, const Term& t, const double* L, const double* C, int c0, int c1, int k, double* Lout) {
+  const int d = t.a->d;
+  if (t.kind == Term::VEC) {
+    int a0 = t.a->bonds[k], a1 = t.a->bonds[k + 1];
+    DBuf T(&c, size_t(c0) * d * a1);
+    einsum(c, "ca,asb->csb", 1.0, tv(const_cast<double*>(L), {c0, a0}), tv(t.a->core(k), {a0, d, a1}), 0.0,
+           tv(T.p, {c0, d, a1}));
+    einsum(c, "csb,csd->db", 1.0, tv(T.p, {c0, d, a1}), tv(const_cast<double*>(C), {c0, d, c1}), 0.0,
+           tv(Lout, {c1, a1}));
+  } else if (t.kind == Term::HAD) {
+    int a0 = t.a->bonds[k], a1 = t.a->bonds[k + 1], b0 = t.b->bonds[k], b1 = t.b->bonds[k + 1];
+    DBuf T1(&c, size_t(c0) * b0 * d * a1);
+    einsum(c, "cab,ase->cbse", 1.0, tv(const_cast<double*>(L), {c0, a0, b0}), tv(t.a->core(k), {a0, d, a1}), 0.0,
+           tv(T1.p, {c0, b0, d, a1}));
+    DBuf T2(&c, size_t(d) * c0 * a1 * b1);
+    einsum(c, "cbse,bsf->scef", 1.0, tv(T1.p, {c0, b0, d, a1}), tv(t.b->core(k), {b0, d, b1}), 0.0,
+           tv(T2.p, {d, c0, a1, b1}));
+    einsum(c, "csd,scef->def", 1.0, tv(const_cast<double*>(C), {c0, d, c1}), tv(T2.p, {d, c0, a1, b1}), 0.0,
+           tv(Lout, {c1, a1, b1}));
+  } else {
+    int w0 = t.M->bonds[k], w1 = t.M->bonds[k + 1], a0 = t.a->bonds[k], a1 = t.a->bonds[k + 1];
+    DBuf T1(&c, size_t(c0) * w0 * d * a1);
+    einsum(c, "cwa,atb->cwtb", 1.0, tv(const_cast<double*>(L), {c0, w0, a0}), tv(t.a->core(k), {a0, d, a1}), 0.0,
+           tv(T1.p, {c0, w0, d, a1}));
+    DBuf T2(&c, size_t(c0) * d * w1 * a1);
+    einsum(c, "cwtb,wstv->csvb", 1.0, tv(T1.p, {c0, w0, d, a1}), tv(t.M->core(k), {w0, d, d, w1}), 0.0,
+           tv(T2.p, {c0, d, w1, a1}));
+    einsum(c, "csvb,csd->dvb", 1.0, tv(T2.p, {c0, d, w1, a1}), tv(const_cast<double*>(C), {c0, d, c1}), 0.0,
+           tv(Lout, {c1, w1, a1}));
+  }
+}
+
+// R_k from R_{k+1} and the new (right-orthonormal) core C at site k.
+static void env_right(Ctx& c, const Term& t, const double* R, const double* C, int c0, int c1, int k, double* Rout) {
+  const int d = t.a->d;
+  if (t.kind == Term::VEC) {
+    int a0 = t.a->bonds[k], a1 = t.a->bonds[k + 1];
+    DBuf T(&c, size_t(a0) * d * c1);
+    einsum(c, "asb,db->asd", 1.0, tv(t.a->core(k), {a0, d, a1}), tv(const_cast<double*>(R), {c1, a1}), 0.0,
+           tv(T.p, {a0, d, c1}));
+    einsum(c, "asd,csd->ca", 1.0, tv(T.p, {a0, d, c1}), tv(const_cast<double*>(C), {c0, d, c1}), 0.0,
+           tv(Rout, {c0, a0}));
+  } else if (t.kind == Term::HAD) {
+    int a0 = t.a->bonds[k], a1 = t.a->bonds[k + 1], b0 = t.b->bonds[k], b1 = t.b->bonds[k + 1];
+    DBuf T1(&c, size_t(a0) * d * c1 * b1);
+    einsum(c, "ase,def->asdf", 1.0, tv(t.a->core(k), {a0, d, a1}), tv(const_cast<double*>(R), {c1, a1, b1}), 0.0,
+           tv(T1.p, {a0, d, c1, b1}));
+    DBuf T2(&c, size_t(d) * a0 * c1 * b0);
+    einsum(c, "asdf,bsf->sadb", 1.0, tv(T1.p, {a0, d, c1, b1}), tv(t.b->core(k), {b0, d, b1}), 0.0,
+           tv(T2.p, {d, a0, c1, b0}));
+    einsum(c, "sadb,csd->cab", 1.0, tv(T2.p, {d, a0, c1, b0}), tv(const_cast<double*>(C), {c0, d, c1}), 0.0,
+           tv(Rout, {c0, a0, b0}));
+  } else {
+    int w0 = t.M->bonds[k], w1 = t.M->bonds[k + 1], a0 = t.a->bonds[k], a1 = t.a->bonds[k + 1];
+    DBuf T1(&c, size_t(a0) * d * c1 * w1);
+    einsum(c, "atb,dvb->atdv", 1.0, tv(t.a->core(k), {a0, d, a1}), tv(const_cast<double*>(R), {c1, w1, a1}), 0.0,
+           tv(T1.p, {a0, d, c1, w1}));
+    DBuf T2(&c, size_t(a0) * w0 * d * c1);
+    einsum(c, "atdv,wstv->awsd", 1.0, tv(T1.p, {a0, d, c1, w1}), tv(t.M->core(k), {w0, d, d, w1}), 0.0,
+           tv(T2.p, {a0, w0, d, c1}));
+    einsum(c, "awsd,csd->cwa", 1.0, tv(T2.p, {a0, w0, d, c1}), tv(const_cast<double*>(C), {c0, d, c1}), 0.0,
+           tv(Rout, {c0, w0, a0}));
+  }
+}
+
+// out (c0, d, c1) (+)= coef * projection of the term onto the frames L (site k) and R (site k+1).
+// `vec` (if non-null) replaces the term's own core at site k (used by the ALS matvec).
+static void local_target(Ctx& c, const Term& t, const double* L, const double* R, int c0, int c1, int k, double coef,
+                         double beta, double* out, const double* vec = nullptr) {
+  const int d = t.a->d;
+  if (t.kind == Term::VEC) {
+    int a0 = t.a->bonds[k], a1 = t.a->bonds[k + 1];
+    DBuf T(&c, size_t(c0) * d * a1);
+    einsum(c, "ca,asb->csb", 1.0, tv(const_cast<double*>(L), {c0, a0}), tv(t.a->core(k), {a0, d, a1}), 0.0,
+           tv(T.p, {c0, d, a1}));
+    einsum(c, "csb,db->csd", coef, tv(T.p, {c0, d, a1}), tv(const_cast<double*>(R), {c1, a1}), beta,
+           tv(out, {c0, d, c1}));
+  } else if (t.kind == Term::HAD) {
+    int a0 = t.a->bonds[k], a1 = t.a->bonds[k + 1], b0 = t.b->bonds[k], b1 = t.b->bonds[k + 1];
+    DBuf T1(&c, size_t(c0) * b0 * d * a1);
+    einsum(c, "cab,ase->cbse", 1.0, tv(const_cast<double*>(L), {c0, a0, b0}), tv(t.a->core(k), {a0, d, a1}), 0.0,
+           tv(T1.p, {c0, b0, d, a1}));
+    DBuf T2(&c, size_t(d) * c0 * a1 * b1);
+    einsum(c, "cbse,bsf->scef", 1.0, tv(T1.p, {c0, b0, d, a1}), tv(t.b->core(k), {b0, d, b1}), 0.0,
+           tv(T2.p, {d, c0, a1, b1}));
+    einsum(c, "scef,def->csd", coef, tv(T2.p, {d, c0, a1, b1}), tv(const_cast<double*>(R), {c1, a1, b1}), beta,
+           tv(out, {c0, d, c1}));
+  } else {
+    int w0 = t.M->bonds[k], w1 = t.M->bonds[k + 1], a0 = t.a->bonds[k], a1 = t.a->bonds[k + 1];
+    const double* X = vec ? vec : t.a->core(k);
+    DBuf T1(&c, size_t(c0) * w0 * d * a1);
+    einsum(c, "cwa,atb->cwtb", 1.0, tv(const_cast<double*>(L), {c0, w0, a0}), tv(const_cast<double*>(X), {a0, d, a1}),
+           0.0, tv(T1.p, {c0, w0, d, a1}));
+    DBuf T2(&c, size_t(c0) * d * w1 * a1);
+    einsum(c, "cwtb,wstv->csvb", 1.0, tv(T1.p, {c0, w0, d, a1}), tv(t.M->core(k), {w0, d, d, w1}), 0.0,
+           tv(T2.p, {c0, d, w1, a1}));
+    einsum(c, "csvb,dvb->csd", coef, tv(T2.p, {c0, d, w1, a1}), tv(const_cast<double*>(R), {c1, w1, a1}), beta,
+           tv(out, {c0, d, c1}));
+  }
+}
+
+struct Envs {
+  std::vector<std::vector<DBuf>> L, R;  // [term][k]
+};
+
+static void init_envs(Ctx& c, const std::vector<Term>& terms, const qtt_mps* x, Envs& E) {
+  const int n = x->n;
+  E.L.clear();
+  E.R.clear();
+  E.L.resize(terms.size());
+  E.R.resize(terms.size());
+  for (size_t t = 0; t < terms.size(); ++t) {
+    E.L[t].resize(n + 1);
+    E.R[t].resize(n + 1);
+    E.L[t][0].reset(&c, 1);
+    fill(c, E.L[t][0].p, 1, 1.0);
+    E.R[t][n].reset(&c, 1);
+    fill(c, E.R[t][n].p, 1, 1.0);
+    for (int k = n - 1; k >= 1; --k) {
+      E.R[t][k].reset(&c, env_size(terms[t], x->bonds[k], k));
+      env_right(c, terms[t], E.R[t][k + 1].p, x->core(k), x->bonds[k], x->bonds[k + 1], k, E.R[t][k].p);
+    }
+  }
+}
+
+static void local_sum(Ctx& c, const std::vector<Term>& terms, const Envs& E, const qtt_mps* x, int k, double* out) {
+  for (size_t t = 0; t < terms.size(); ++t)
+    local_target(c, terms[t], E.L[t][k].p, E.R[t][k + 1].p, x->bonds[k], x->bonds[k + 1], k, terms[t].coef,
+                 t == 0 ? 0.0 : 1.0, out);
+}
+
+void fit(Ctx& c, const std::vector<Term>& terms, qtt_mps* x, int sweeps, bool canonical) {
+  QTT_CHECK_ARG(!terms.empty(), "fit: no terms");
+  for (const Term& t : terms) QTT_CHECK_ARG(t.a->n == x->n && t.a->d == x->d, "fit: term shape mismatch");
+  const int n = x->n, d = x->d;
+  if (!canonical) right_orthonormalize(c, x);
+  if (n == 1) {
+    Envs E;
+    init_envs(c, terms, x, E);
+    DBuf T(&c, size_t(x->core_size(0)));
+    local_sum(c, terms, E, x, 0, T.p);
+    copy(c, x->core(0), T.p, x->core_size(0));
+    return;
+  }
+  Envs E;
+  init_envs(c, terms, x, E);
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int k = 0; k < n; ++k) {
+      int r0 = x->bonds[k], r1 = x->bonds[k + 1];
+      DBuf T(&c, size_t(r0) * d * r1);
+      local_sum(c, terms, E, x, k, T.p);
+      if (k < n - 1) {
+        qr(c, 1, r0 * d, r1, 0, T.p, 0, x->core(k), 0, nullptr, 0);
+        for (size_t t = 0; t < terms.size(); ++t) {
+          E.L[t][k + 1].reset(&c, env_size(terms[t], r1, k + 1));
+          env_left(c, terms[t], E.L[t][k].p, x->core(k), r0, r1, k, E.L[t][k + 1].p);
+        }
+      } else {
+        copy(c, x->core(k), T.p, int64_t(r0) * d * r1);
+      }
+    }
+    for (int k = n - 1; k >= 0; --k) {
+      int r0 = x->bonds[k], r1 = x->bonds[k + 1];
+      DBuf T(&c, size_t(r0) * d * r1);
+      local_sum(c, terms, E, x, k, T.p);
+      if (k > 0) {
+        qr(c, 1, d * r1, r0, 1, T.p, 0, x->core(k), 0, nullptr, 0);
+        for (size_t t = 0; t < terms.size(); ++t) {
+          E.R[t][k].reset(&c, env_size(terms[t], r0, k));
+          env_right(c, terms[t], E.R[t][k + 1].p, x->core(k), r0, r1, k, E.R[t][k].p);
+        }
+      } else {
+        copy(c, x->core(k), T.p, int64_t(r0) * d * r1);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ zip-up (Hadamard start)
+
+qtt_mps* zipup_hadamard(Ctx& c, const qtt_mps* a, const qtt_mps* b, int chi) {
+  QTT_CHECK_ARG(a->n == b->n && a->d == b->d, "zipup: shape mismatch");
+  const int n = a->n, d = a->d;
+  std::vector<int> R(n + 1);
+  for (int k = 0; k <= n; ++k) R[k] = a->bonds[k] * b->bonds[k];
+  std::vector<int> ms = left_struct(R, d);
+  std::vector<int> ob(n + 1);
+  ob[0] = 1;
+  ob[n] = 1;
+  std::vector<DBuf> out(n);
+  DBuf C(&c, 1);
+  fill(c, C.p, 1, 1.0);
+  for (int k = n - 1; k >= 0; --k) {
+    int a0 = a->bonds[k], a1 = a->bonds[k + 1], b0 = b->bonds[k], b1 = b->bonds[k + 1], c1 = ob[k + 1];
+    DBuf T1(&c, size_t(a0) * d * c1 * b1);
+    einsum(c, "asA,cAB->ascB", 1.0, tv(a->core(k), {a0, d, a1}), tv(C.p, {c1, a1, b1}), 0.0,
+           tv(T1.p, {a0, d, c1, b1}));
+    DBuf T(&c, size_t(a0) * b0 * d * c1);
+    einsum(c, "bsB,ascB->absc", 1.0, tv(b->core(k), {b0, d, b1}), tv(T1.p, {a0, d, c1, b1}), 0.0,
+           tv(T.p, {a0, b0, d, c1}));
+    if (k == 0) {
+      out[0] = std::move(T);
+      break;
+    }
+    const int nv = d * c1;
+    DBuf rho(&c, size_t(nv) * nv), w(&c, size_t(nv)), V(&c, size_t(nv) * nv);
+    gemm(c, 1, nv, nv, int64_t(a0) * b0, 1.0, T.p, 0, 1, nv, T.p, 0, nv, 1, 0.0, rho.p, 0, nv, 1);
+    eigh(c, nv, rho.p, w.p, V.p);
+    int bk = std::max(1, std::min(std::min(chi, ms[k]), nv));
+    out[k].reset(&c, size_t(bk) * nv);
+    top_vectors_as_core(c, V.p, nv, bk, out[k].p);
+    // C_new(beta, a, b) = sum_{s,c} T(a, b, s, c) V(sc, beta)
+    DBuf Cn(&c, size_t(bk) * a0 * b0);
+    gemm(c, 1, bk, int64_t(a0) * b0, nv, 1.0, V.p, 0, 1, nv, T.p, 0, 1, nv, 0.0, Cn.p, 0, int64_t(a0) * b0, 1);
+    C = std::move(Cn);
+    ob[k] = bk;
+  }
+  qtt_mps* z = new_mps(&c, n, d, ob);
+  for (int k = 0; k < n; ++k) copy(c, z->core(k), out[k].p, int64_t(ob[k]) * d * ob[k + 1]);
+  return z;
+}
+
+// ------------------------------------------------------------------ ALS (Sec. II.A.4)
+
+int als(Ctx& c, const qtt_mpo* A, const std::vector<Term>& rhs, qtt_mps* x, int sweeps, int cg_iters, double cg_tol,
+        bool canonical, int* cg_total_dev) {
+  QTT_CHECK_ARG(A->n == x->n && A->d == x->d, "als: operator shape");
+  for (const Term& t : rhs) QTT_CHECK_ARG(t.a->n == x->n && t.a->d == x->d, "als: rhs shape");
+  const int n = x->n, d = x->d;
+  if (!canonical) right_orthonormalize(c, x);
+  // operator environments: term MPO(A, x) with bra = x
+  Term opT;
+  opT.kind = Term::MPO;
+  opT.coef = 1.0;
+  opT.M = A;
+  opT.a = x;
+  std::vector<DBuf> LA(n + 1), RA(n + 1);
+  LA[0].reset(&c, 1);
+  fill(c, LA[0].p, 1, 1.0);
+  RA[n].reset(&c, 1);
+  fill(c, RA[n].p, 1, 1.0);
+  for (int k = n - 1; k >= 1; --k) {
+    RA[k].reset(&c, env_size(opT, x->bonds[k], k));
+    env_right(c, opT, RA[k + 1].p, x->core(k), x->bonds[k], x->bonds[k + 1], k, RA[k].p);
+  }
+  Envs E;
+  init_envs(c, rhs, x, E);
+  DBuf stbuf(&c, 8);
+  CGState* st = reinterpret_cast<CGState*>(stbuf.p);
+  DBuf tot(&c, 1);
+  k_set_int<<<1, 1, 0, c.stream>>>(reinterpret_cast<int*>(tot.p), 0);
+  after_launch(c, "set_int");
+  const int* active = &st->active;
+
+  auto solve_site = [&](int k) {
+    int r0 = x->bonds[k], r1 = x->bonds[k + 1];
+    int64_t nel = int64_t(r0) * d * r1;
+    DBuf bvec(&c, nel), Ax(&c, nel), r(&c, nel), p(&c, nel), Ap(&c, nel), xk(&c, nel);
+    local_sum(c, rhs, E, x, k, bvec.p);
+    copy(c, xk.p, x->core(k), nel);
+    local_target(c, opT, LA[k].p, RA[k + 1].p, r0, r1, k, 1.0, 0.0, Ax.p, xk.p);
+    k_cg_init<<<1, 1024, 0, c.stream>>>(nel, bvec.p, Ax.p, r.p, p.p, st, cg_tol * cg_tol);
+    after_launch(c, "cg_init");
+    for (int it = 0; it < cg_iters; ++it) {
+      c.guard = active;
+      local_target(c, opT, LA[k].p, RA[k + 1].p, r0, r1, k, 1.0, 0.0, Ap.p, p.p);
+      c.guard = nullptr;
+      k_cg_update<<<1, 1024, 0, c.stream>>>(nel, xk.p, r.p, p.p, Ap.p, st);
+      after_launch(c, "cg_update");
+    }
+    k_cg_accumulate<<<1, 1, 0, c.stream>>>(st, reinterpret_cast<int*>(tot.p));
+    after_launch(c, "cg_accumulate");
+    return xk;
+  };
+
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int k = 0; k < n; ++k) {
+      int r0 = x->bonds[k], r1 = x->bonds[k + 1];
+      DBuf xk = solve_site(k);
+      if (k < n - 1) {
+        DBuf Rm(&c, size_t(r1) * r1);
+        qr(c, 1, r0 * d, r1, 0, xk.p, 0, x->core(k), 0, Rm.p, 0);
+        int r2 = x->bonds[k + 2];
+        DBuf nxt(&c, size_t(r1) * d * r2);
+        einsum(c, "ab,bsc->asc", 1.0, tv(Rm.p, {r1, r1}), tv(x->core(k + 1), {r1, d, r2}), 0.0, tv(nxt.p, {r1, d, r2}));
+        copy(c, x->core(k + 1), nxt.p, int64_t(r1) * d * r2);
+        LA[k + 1].reset(&c, env_size(opT, r1, k + 1));
+        env_left(c, opT, LA[k].p, x->core(k), r0, r1, k, LA[k + 1].p);
+        for (size_t t = 0; t < rhs.size(); ++t) {
+          E.L[t][k + 1].reset(&c, env_size(rhs[t], r1, k + 1));
+          env_left(c, rhs[t], E.L[t][k].p, x->core(k), r0, r1, k, E.L[t][k + 1].p);
+        }
+      } else {
+        copy(c, x->core(k), xk.p, int64_t(r0) * d * r1);
+      }
+    }
+    for (int k = n - 1; k >= 0; --k) {
+      int r0 = x->bonds[k], r1 = x->bonds[k + 1];
+      DBuf xk = solve_site(k);
+      if (k > 0) {
+        DBuf Rm(&c, size_t(r0) * r0);
+        qr(c, 1, d * r1, r0, 1, xk.p, 0, x->core(k), 0, Rm.p, 0);
+        int p0 = x->bonds[k - 1];
+        DBuf prev(&c, size_t(p0) * d * r0);
+        einsum(c, "asb,cb->asc", 1.0, tv(x->core(k - 1), {p0, d, r0}), tv(Rm.p, {r0, r0}), 0.0,
+               tv(prev.p, {p0, d, r0}));
+        copy(c, x->core(k - 1), prev.p, int64_t(p0) * d * r0);
+        RA[k].reset(&c, env_size(opT, r0, k));
+        env_right(c, opT, RA[k + 1].p, x->core(k), r0, r1, k, RA[k].p);
+        for (size_t t = 0; t < rhs.size(); ++t) {
+          E.R[t][k].reset(&c, env_size(rhs[t], r0, k));
+          env_right(c, rhs[t], E.R[t][k + 1].p, x->core(k), r0, r1, k, E.R[t][k].p);
+        }
+      } else {
+        copy(c, x->core(k), xk.p, int64_t(r0) * d * r1);
+      }
+    }
+  }
+  if (cg_total_dev) {
+    QTT_CUDA(cudaMemcpyAsync(cg_total_dev, tot.p, sizeof(int), cudaMemcpyDeviceToDevice, c.stream));
+    return 0;
+  }
+  int h = 0;
+  QTT_CUDA(cudaMemcpyAsync(&h, tot.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  return h;
+}
+
+// ------------------------------------------------------------------ inner products, norms
+
+void dot_dev(Ctx& c, const qtt_mps* a, const qtt_mps* b, double* out_dev) {
+  QTT_CHECK_ARG(a->n == b->n && a->d == b->d, "dot: shape mismatch");
+  const int n = a->n, d = a->d;
+  DBuf E(&c, 1);
+  fill(c, E.p, 1, 1.0);
+  for (int k = 0; k < n; ++k) {
+    int a0 = a->bonds[k], a1 = a->bonds[k + 1], b0 = b->bonds[k], b1 = b->bonds[k + 1];
+    DBuf T(&c, size_t(b0) * d * a1);
+    einsum(c, "ab,asc->bsc", 1.0, tv(E.p, {a0, b0}), tv(a->core(k), {a0, d, a1}), 0.0, tv(T.p, {b0, d, a1}));
+    DBuf En(&c, size_t(a1) * b1);
+    einsum(c, "bsc,bsd->cd", 1.0, tv(T.p, {b0, d, a1}), tv(b->core(k), {b0, d, b1}), 0.0, tv(En.p, {a1, b1}));
+    E = std::move(En);
+  }
+  copy(c, out_dev, E.p, 1);
+}
+
+// ||y|| by a left-to-right Householder QR sweep (the norm of the last core after
+// orthogonalisation): no cancellation, unlike the transfer-matrix <y, y> whose absolute
+// error is eps <|y|, |y|>.  Used when every unfolding fits the one-CTA QR; otherwise the
+// transfer-matrix value is returned (relative accuracy of the norm ~ sqrt(eps) when y is
+// a small difference of large terms).
+void norm_dev(Ctx& c, const qtt_mps* y, double* out_dev) {
+  const int n = y->n, d = y->d;
+  bool fits = true;
+  for (int k = 0; k < n; ++k)
+    if (int64_t(y->bonds[k]) * d * y->bonds[k + 1] + int64_t(y->bonds[k]) * d + y->bonds[k + 1] > 26000) fits = false;
+  if (!fits) {
+    DBuf t(&c, 1);
+    dot_dev(c, y, y, t.p);
+    sqrt_dev(c, t.p, out_dev);
+    return;
+  }
+  int r0 = 1;
+  DBuf cur(&c, size_t(y->core_size(0)));
+  copy(c, cur.p, y->core(0), int64_t(d) * y->bonds[1]);
+  for (int k = 0; k + 1 < n; ++k) {
+    int rows = r0 * d, cols = y->bonds[k + 1];
+    int kk = std::min(rows, cols);
+    DBuf Q(&c, size_t(rows) * kk), R(&c, size_t(kk) * cols);
+    qr(c, 1, rows, cols, 0, cur.p, 0, Q.p, 0, R.p, 0);
+    int r2 = y->bonds[k + 2];
+    DBuf nxt(&c, size_t(kk) * d * r2);
+    einsum(c, "ab,bsc->asc", 1.0, tv(R.p, {kk, cols}), tv(y->core(k + 1), {cols, d, r2}), 0.0, tv(nxt.p, {kk, d, r2}));
+    cur = std::move(nxt);
+    r0 = kk;
+  }
+  DBuf t(&c, 1);
+  dot(c, int64_t(r0) * d, cur.p, cur.p, t.p);
+  sqrt_dev(c, t.p, out_dev);
+}
+
+// ------------------------------------------------------------------ dense encode / decode
+
+qtt_mps* encode_dense(Ctx& c, const double* dense_dev, int n, int d, int chi, double eps) {
+  QTT_CHECK_ARG(n >= 1 && n <= 40, "encode: n");
+  if (eps > 0.0) {
+    std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> z(encode_dense(c, dense_dev, n, d, chi, 0.0), free_mps);
+    return round_any(c, z.get(), chi, eps);
+  }
+  auto powd = [&](int k) {
+    int64_t p = 1;
+    for (int i = 0; i < k; ++i) p *= d;
+    return p;
+  };
+  std::vector<int> ob(n + 1);
+  ob[0] = 1;
+  ob[n] = 1;
+  std::vector<DBuf> out(n);
+  DBuf cur(&c, size_t(powd(n)));
+  copy(c, cur.p, dense_dev, powd(n));
+  for (int k = n - 1; k >= 1; --k) {
+    int c1 = ob[k + 1];
+    int nv = d * c1;
+    int64_t rows = powd(k);
+    DBuf rho(&c, size_t(nv) * nv), w(&c, size_t(nv)), V(&c, size_t(nv) * nv);
+    gemm(c, 1, nv, nv, rows, 1.0, cur.p, 0, 1, nv, cur.p, 0, nv, 1, 0.0, rho.p, 0, nv, 1);
+    eigh(c, nv, rho.p, w.p, V.p);
+    int strct = int(std::min<int64_t>(rows, nv));
+    int bk = choose_rank(c, w.p, nv, chi, eps, strct);
+    out[k].reset(&c, size_t(bk) * nv);
+    top_vectors_as_core(c, V.p, nv, bk, out[k].p);
+    DBuf nxt(&c, size_t(rows) * bk);
+    gemm(c, 1, rows, bk, nv, 1.0, cur.p, 0, nv, 1, V.p, 0, nv, 1, 0.0, nxt.p, 0, bk, 1);
+    cur = std::move(nxt);
+    ob[k] = bk;
+  }
+  out[0] = std::move(cur);
+  qtt_mps* z = new_mps(&c, n, d, ob);
+  for (int k = 0; k < n; ++k) copy(c, z->core(k), out[k].p, int64_t(ob[k]) * d * ob[k + 1]);
+  return z;
+}
+
+void decode_dense(Ctx& c, const qtt_mps* x, double* dense_dev) {
+  const int n = x->n, d = x->d;
+  DBuf t(&c, 1);
+  fill(c, t.p, 1, 1.0);
+  int64_t rows = 1;
+  for (int k = 0; k < n; ++k) {
+    int a0 = x->bonds[k], a1 = x->bonds[k + 1];
+    DBuf nt(&c, size_t(rows) * d * a1);
+    gemm(c, 1, rows, int64_t(d) * a1, a0, 1.0, t.p, 0, a0, 1, x->core(k), 0, int64_t(d) * a1, 1, 0.0, nt.p, 0,
+         int64_t(d) * a1, 1);
+    t = std::move(nt);
+    rows *= d;
+  }
+  copy(c, dense_dev, t.p, rows);
+}
+
+}  // namespace qtt

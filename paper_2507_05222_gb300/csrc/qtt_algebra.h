@@ -1,0 +1,62 @@
+// Internal TT algebra interface (see qtt_algebra.cu).
+#pragma once
+
+#include <vector>
+
+#include "qtt_internal.h"
+
+namespace qtt {
+
+// One term of a target sum: coef * x, coef * (a (.) b) or coef * (M x).
+struct Term {
+  enum Kind { VEC = 0, HAD = 1, MPO = 2 };
+  int kind = VEC;
+  double coef = 1.0;
+  const qtt_mps* a = nullptr;   // x for VEC and MPO, first factor for HAD
+  const qtt_mps* b = nullptr;   // second factor for HAD
+  const qtt_mpo* M = nullptr;   // operator for MPO
+  int rbond(int k) const;
+  static Term vec(double c, const qtt_mps* x) { Term t; t.kind = VEC; t.coef = c; t.a = x; return t; }
+  static Term had(double c, const qtt_mps* x, const qtt_mps* y) {
+    Term t; t.kind = HAD; t.coef = c; t.a = x; t.b = y; return t;
+  }
+  static Term mpo(double c, const qtt_mpo* m, const qtt_mps* x) {
+    Term t; t.kind = MPO; t.coef = c; t.M = m; t.a = x; return t;
+  }
+};
+
+std::vector<int> left_struct(const std::vector<int>& pre, int d);
+
+qtt_mps* direct_sum(Ctx& c, double alpha, const qtt_mps* x, double beta, const qtt_mps* y);
+void direct_sum_core(Ctx& c, const double* X, int xr0, int xr1, const double* Y, int yr0, int yr1, int d, bool first,
+                     bool last, double alpha, double beta, double* Z, int64_t zsize);
+qtt_mpo* diag_mpo(Ctx& c, const qtt_mps* a);
+qtt_mps* mpo_mps_exact(Ctx& c, const qtt_mpo* M, const qtt_mps* x);
+qtt_mpo* mpo_mpo_exact(Ctx& c, const qtt_mpo* A, const qtt_mpo* B);
+qtt_mps* mps_copy(Ctx& c, const qtt_mps* x);
+void mps_scale(Ctx& c, qtt_mps* x, double s);
+qtt_mps* mpo_as_mps(Ctx& c, const qtt_mpo* m);
+qtt_mpo* mps_as_mpo(Ctx& c, const qtt_mps* x, int d);
+
+// TT-rounding, exact TT-SVD semantics (right to left, result right-canonical).
+qtt_mps* round_svd(Ctx& c, const qtt_mps* x, int chi, double eps);    // QR + Jacobi SVD, FP64
+qtt_mps* round_gram(Ctx& c, const qtt_mps* y, int chi, double eps);   // Gram / density matrix
+qtt_mps* round_any(Ctx& c, const qtt_mps* y, int chi, double eps);
+qtt_mps* apply_round_gram(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, double eps);
+
+void right_orthonormalize(Ctx& c, qtt_mps* x);
+// Variational fit of sum(terms) in place on x (fixed bonds), `sweeps` full sweeps.
+void fit(Ctx& c, const std::vector<Term>& terms, qtt_mps* x, int sweeps, bool canonical);
+qtt_mps* zipup_hadamard(Ctx& c, const qtt_mps* a, const qtt_mps* b, int chi);
+// ALS for A x = sum(rhs); returns total CG iterations (host-synchronising) unless
+// cg_total_dev is given (then the count is written there on the device and 0 is returned).
+int als(Ctx& c, const qtt_mpo* A, const std::vector<Term>& rhs, qtt_mps* x, int sweeps, int cg_iters, double cg_tol,
+        bool canonical, int* cg_total_dev);
+
+void dot_dev(Ctx& c, const qtt_mps* a, const qtt_mps* b, double* out_dev);
+void norm_dev(Ctx& c, const qtt_mps* y, double* out_dev);
+void sqrt_dev(Ctx& c, const double* in, double* out);
+qtt_mps* encode_dense(Ctx& c, const double* dense_dev, int n, int d, int chi, double eps);
+void decode_dense(Ctx& c, const qtt_mps* x, double* dense_dev);
+
+}  // namespace qtt

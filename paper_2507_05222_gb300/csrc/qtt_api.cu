@@ -1,0 +1,626 @@
+// extern "C" entry points of include/qtt.h: argument checks, error translation, handle
+// management.  No C++ exception crosses this file's functions.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "qtt_algebra.h"
+#include "qtt_case.h"
+
+namespace qtt {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace qtt
+
+using namespace qtt;
+
+#define API_BEGIN try {
+#define API_END                                        \
+  }                                                    \
+  catch (const qtt::Error& e) {                        \
+    set_last_error(e.what());                          \
+    return e.code;                                     \
+  }                                                    \
+  catch (const std::bad_alloc&) {                      \
+    set_last_error("host allocation failed");          \
+    return QTT_ERR_ALLOC;                              \
+  }                                                    \
+  catch (const std::exception& e) {                    \
+    set_last_error(e.what());                          \
+    return QTT_ERR_CUDA;                               \
+  }                                                    \
+  set_last_error("");                                  \
+  return QTT_OK;
+
+namespace {
+
+void check_mps(const qtt_mps* x, const char* what) {
+  if (!x) throw Error(QTT_ERR_ARG, std::string(what) + ": null MPS");
+}
+
+void check_trunc(const qtt_trunc& t) {
+  if (t.chi_max < 1) throw Error(QTT_ERR_ARG, "trunc: chi_max must be >= 1");
+  if (!(t.rel_tol >= 0.0) || !std::isfinite(t.rel_tol)) throw Error(QTT_ERR_ARG, "trunc: rel_tol must be >= 0");
+}
+
+cudaMemcpyKind kind_in(int kind) {
+  if (kind == QTT_HOST) return cudaMemcpyHostToDevice;
+  if (kind == QTT_DEVICE) return cudaMemcpyDeviceToDevice;
+  throw Error(QTT_ERR_ARG, "pointer kind must be QTT_HOST or QTT_DEVICE");
+}
+
+cudaMemcpyKind kind_out(int kind) {
+  if (kind == QTT_HOST) return cudaMemcpyDeviceToHost;
+  if (kind == QTT_DEVICE) return cudaMemcpyDeviceToDevice;
+  throw Error(QTT_ERR_ARG, "pointer kind must be QTT_HOST or QTT_DEVICE");
+}
+
+void fill_info(Ctx& c, const qtt_mps* y, qtt_round_info* info) {
+  if (!info) return;
+  int mb = 1;
+  for (int b : y->bonds) mb = std::max(mb, b);
+  info->max_bond = mb;
+  DBuf d(&c, 1);
+  dot_dev(c, y, y, d.p);
+  double v = 0.0;
+  QTT_CUDA(cudaMemcpyAsync(&v, d.p, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  info->norm = std::sqrt(std::max(v, 0.0));
+}
+
+__global__ void k_reorder(const double* __restrict__ src, double* __restrict__ dst, int ne, int nx, int ordering,
+                          int inverse) {
+  const int n = ne + nx;
+  const int64_t total = int64_t(1) << n;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
+    int64_t i = 0, j = 0;
+    int p = 0;
+    if (ordering == QTT_ORDER_SEQUENTIAL) {
+      i = q >> nx;
+      j = q & ((int64_t(1) << nx) - 1);
+    } else {
+      for (int l = 0; l < (ne > nx ? ne : nx); ++l) {
+        if (l < ne) {
+          int64_t bit = (q >> (n - 1 - p)) & 1;
+          i |= bit << (ne - 1 - l);
+          ++p;
+        }
+        if (l < nx) {
+          int64_t bit = (q >> (n - 1 - p)) & 1;
+          j |= bit << (nx - 1 - l);
+          ++p;
+        }
+      }
+    }
+    int64_t f = (i << nx) | j;  // row-major field index
+    if (inverse) dst[f] = src[q];
+    else dst[q] = src[f];
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int qtt_ctx_create(qtt_ctx** out, int device, void* cuda_stream, qtt_alloc_fn alloc, qtt_free_fn free_fn, void* user) {
+  API_BEGIN
+  QTT_CHECK_ARG(out != nullptr, "ctx_create: out is null");
+  QTT_CHECK_ARG((alloc == nullptr) == (free_fn == nullptr), "ctx_create: give both alloc and free or neither");
+  int ndev = 0;
+  QTT_CUDA(cudaGetDeviceCount(&ndev));
+  QTT_CHECK_ARG(device >= 0 && device < ndev, "ctx_create: no such device");
+  QTT_CUDA(cudaSetDevice(device));
+  std::unique_ptr<Ctx> c(new Ctx);
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  QTT_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+  c->pool = new Pool(alloc, free_fn, user);
+  *out = reinterpret_cast<qtt_ctx*>(c.release());
+  API_END
+}
+
+void qtt_ctx_destroy(qtt_ctx* ctx) {
+  if (!ctx) return;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  cudaStreamSynchronize(c->stream);
+  delete c->pool;
+  delete c;
+}
+
+int qtt_ctx_sync(qtt_ctx* ctx) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx, "ctx is null");
+  QTT_CUDA(cudaStreamSynchronize(reinterpret_cast<Ctx*>(ctx)->stream));
+  API_END
+}
+
+const char* qtt_last_error(void) { return g_last_error.c_str(); }
+
+int64_t qtt_ctx_kernel_launches(qtt_ctx* ctx) { return ctx ? reinterpret_cast<Ctx*>(ctx)->launches : 0; }
+
+size_t qtt_ctx_pool_bytes(qtt_ctx* ctx) { return ctx ? reinterpret_cast<Ctx*>(ctx)->pool->held() : 0; }
+
+// ------------------------------------------------------------------ MPS / MPO
+
+int qtt_mps_create(qtt_ctx* ctx, int n, int d, const int* bonds, const double* cores, int kind, qtt_mps** out) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && out && bonds, "mps_create: null argument");
+  QTT_CHECK_ARG(n >= 1 && n <= 64 && d >= 1 && d <= 16, "mps_create: n in [1, 64], d in [1, 16]");
+  std::vector<int> b(bonds, bonds + n + 1);
+  QTT_CHECK_ARG(b[0] == 1 && b[n] == 1, "mps_create: bonds[0] and bonds[n] must be 1");
+  for (int v : b) QTT_CHECK_ARG(v >= 1 && v <= 4096, "mps_create: bonds must be in [1, 4096]");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  std::unique_ptr<qtt_mps> x(new_mps(&c, n, d, b));
+  if (cores) {
+    cudaMemcpyKind k = kind_in(kind);
+    int64_t src = 0;
+    for (int i = 0; i < n; ++i) {
+      int64_t sz = int64_t(b[i]) * d * b[i + 1];
+      QTT_CUDA(cudaMemcpyAsync(x->core(i), cores + src, sz * sizeof(double), k, c.stream));
+      src += sz;
+    }
+    if (kind == QTT_HOST) QTT_CUDA(cudaStreamSynchronize(c.stream));
+  } else {
+    fill(c, x->buf.p, x->off[n], 0.0);
+  }
+  *out = x.release();
+  API_END
+}
+
+int qtt_mps_free(qtt_mps* x) {
+  API_BEGIN
+  if (x) free_mps(x);
+  API_END
+}
+
+int qtt_mps_n(const qtt_mps* x) { return x ? x->n : 0; }
+int qtt_mps_d(const qtt_mps* x) { return x ? x->d : 0; }
+
+int qtt_mps_bonds(const qtt_mps* x, int* bonds_out) {
+  API_BEGIN
+  check_mps(x, "mps_bonds");
+  QTT_CHECK_ARG(bonds_out, "mps_bonds: null output");
+  std::memcpy(bonds_out, x->bonds.data(), x->bonds.size() * sizeof(int));
+  API_END
+}
+
+int64_t qtt_mps_size(const qtt_mps* x) {
+  if (!x) return 0;
+  int64_t s = 0;
+  for (int k = 0; k < x->n; ++k) s += int64_t(x->bonds[k]) * x->d * x->bonds[k + 1];
+  return s;
+}
+
+int qtt_mps_get_cores(const qtt_mps* x, double* dst, int kind) {
+  API_BEGIN
+  check_mps(x, "mps_get_cores");
+  QTT_CHECK_ARG(dst, "mps_get_cores: null destination");
+  Ctx& c = *x->ctx;
+  cudaMemcpyKind k = kind_out(kind);
+  int64_t o = 0;
+  for (int i = 0; i < x->n; ++i) {
+    int64_t sz = int64_t(x->bonds[i]) * x->d * x->bonds[i + 1];
+    QTT_CUDA(cudaMemcpyAsync(dst + o, x->core(i), sz * sizeof(double), k, c.stream));
+    o += sz;
+  }
+  if (kind == QTT_HOST) QTT_CUDA(cudaStreamSynchronize(c.stream));
+  API_END
+}
+
+const double* qtt_mps_device_ptr(const qtt_mps* x) { return x ? x->buf.p : nullptr; }
+
+int qtt_mps_copy(const qtt_mps* x, qtt_mps** out) {
+  API_BEGIN
+  check_mps(x, "mps_copy");
+  QTT_CHECK_ARG(out, "mps_copy: null output");
+  *out = mps_copy(*x->ctx, x);
+  API_END
+}
+
+int qtt_mpo_create(qtt_ctx* ctx, int n, int d, const int* bonds, const double* cores, int kind, qtt_mpo** out) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && out && bonds, "mpo_create: null argument");
+  QTT_CHECK_ARG(n >= 1 && n <= 64 && d >= 1 && d <= 4, "mpo_create: n in [1, 64], d in [1, 4]");
+  std::vector<int> b(bonds, bonds + n + 1);
+  QTT_CHECK_ARG(b[0] == 1 && b[n] == 1, "mpo_create: bonds[0] and bonds[n] must be 1");
+  for (int v : b) QTT_CHECK_ARG(v >= 1 && v <= 256, "mpo_create: bonds must be in [1, 256]");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  std::unique_ptr<qtt_mpo> m(new_mpo(&c, n, d, b));
+  if (cores) {
+    cudaMemcpyKind k = kind_in(kind);
+    int64_t src = 0;
+    for (int i = 0; i < n; ++i) {
+      int64_t sz = int64_t(b[i]) * d * d * b[i + 1];
+      QTT_CUDA(cudaMemcpyAsync(m->core(i), cores + src, sz * sizeof(double), k, c.stream));
+      src += sz;
+    }
+    if (kind == QTT_HOST) QTT_CUDA(cudaStreamSynchronize(c.stream));
+  } else {
+    fill(c, m->buf.p, m->off[n], 0.0);
+  }
+  *out = m.release();
+  API_END
+}
+
+int qtt_mpo_free(qtt_mpo* m) {
+  API_BEGIN
+  if (m) free_mpo(m);
+  API_END
+}
+
+int qtt_mpo_bonds(const qtt_mpo* m, int* bonds_out) {
+  API_BEGIN
+  QTT_CHECK_ARG(m && bonds_out, "mpo_bonds: null argument");
+  std::memcpy(bonds_out, m->bonds.data(), m->bonds.size() * sizeof(int));
+  API_END
+}
+
+int qtt_mpo_get_cores(const qtt_mpo* m, double* dst, int kind) {
+  API_BEGIN
+  QTT_CHECK_ARG(m && dst, "mpo_get_cores: null argument");
+  Ctx& c = *m->ctx;
+  cudaMemcpyKind k = kind_out(kind);
+  int64_t o = 0;
+  for (int i = 0; i < m->n; ++i) {
+    int64_t sz = int64_t(m->bonds[i]) * m->d * m->d * m->bonds[i + 1];
+    QTT_CUDA(cudaMemcpyAsync(dst + o, m->core(i), sz * sizeof(double), k, c.stream));
+    o += sz;
+  }
+  if (kind == QTT_HOST) QTT_CUDA(cudaStreamSynchronize(c.stream));
+  API_END
+}
+
+// ------------------------------------------------------------------ TT operations
+
+int qtt_encode(qtt_ctx* ctx, const double* dense, int kind, int n, int d, qtt_trunc tr, qtt_mps** out,
+               qtt_round_info* info) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && dense && out, "encode: null argument");
+  QTT_CHECK_ARG(n >= 1 && d >= 2 && std::pow(double(d), n) <= double(int64_t(1) << 31), "encode: d^n must be <= 2^31");
+  check_trunc(tr);
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  int64_t N = 1;
+  for (int i = 0; i < n; ++i) N *= d;
+  DBuf buf(&c, size_t(N));
+  QTT_CUDA(cudaMemcpyAsync(buf.p, dense, N * sizeof(double), kind_in(kind), c.stream));
+  qtt_mps* y = encode_dense(c, buf.p, n, d, tr.chi_max, tr.rel_tol);
+  fill_info(c, y, info);
+  *out = y;
+  API_END
+}
+
+int qtt_decode(qtt_ctx* ctx, const qtt_mps* x, double* dense, int kind) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && dense, "decode: null argument");
+  check_mps(x, "decode");
+  QTT_CHECK_ARG(std::pow(double(x->d), x->n) <= double(int64_t(1) << 26), "decode: at most 2^26 values");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  int64_t N = 1;
+  for (int i = 0; i < x->n; ++i) N *= x->d;
+  if (kind == QTT_DEVICE) {
+    decode_dense(c, x, dense);
+  } else {
+    DBuf buf(&c, size_t(N));
+    decode_dense(c, x, buf.p);
+    QTT_CUDA(cudaMemcpyAsync(dense, buf.p, N * sizeof(double), kind_out(kind), c.stream));
+    QTT_CUDA(cudaStreamSynchronize(c.stream));
+  }
+  API_END
+}
+
+int qtt_field_to_vector(qtt_ctx* ctx, const double* src, double* dst, int kind, int n_eta, int n_xi, int ordering,
+                        int inverse) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && src && dst && src != dst, "field_to_vector: null or aliased buffers");
+  QTT_CHECK_ARG(n_eta >= 1 && n_xi >= 1 && n_eta + n_xi <= 30, "field_to_vector: grid bits");
+  QTT_CHECK_ARG(ordering == QTT_ORDER_SEQUENTIAL || ordering == QTT_ORDER_INTERLEAVED, "field_to_vector: ordering");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  int64_t N = int64_t(1) << (n_eta + n_xi);
+  DBuf a(&c, size_t(N)), b(&c, size_t(N));
+  QTT_CUDA(cudaMemcpyAsync(a.p, src, N * sizeof(double), kind_in(kind), c.stream));
+  int grid = int(std::min<int64_t>((N + 255) / 256, 65535 * 4));
+  k_reorder<<<grid, 256, 0, c.stream>>>(a.p, b.p, n_eta, n_xi, ordering, inverse);
+  after_launch(c, "reorder");
+  QTT_CUDA(cudaMemcpyAsync(dst, b.p, N * sizeof(double), kind_out(kind), c.stream));
+  if (kind == QTT_HOST) QTT_CUDA(cudaStreamSynchronize(c.stream));
+  API_END
+}
+
+int qtt_round(qtt_ctx* ctx, const qtt_mps* x, qtt_trunc tr, qtt_mps** out, qtt_round_info* info) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && out, "round: null argument");
+  check_mps(x, "round");
+  check_trunc(tr);
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  qtt_mps* y = round_any(c, x, tr.chi_max, tr.rel_tol);
+  fill_info(c, y, info);
+  *out = y;
+  API_END
+}
+
+int mps_axpby_round(qtt_ctx* ctx, double alpha, const qtt_mps* x, double beta, const qtt_mps* y, qtt_trunc tr,
+                    qtt_mps** out, qtt_round_info* info) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && out, "axpby: null argument");
+  check_mps(x, "axpby x");
+  check_mps(y, "axpby y");
+  QTT_CHECK_ARG(x->n == y->n && x->d == y->d, "axpby: x and y differ in n or d");
+  QTT_CHECK_ARG(std::isfinite(alpha) && std::isfinite(beta), "axpby: non-finite coefficient");
+  check_trunc(tr);
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> s(direct_sum(c, alpha, x, beta, y), free_mps);
+  qtt_mps* z = round_any(c, s.get(), tr.chi_max, tr.rel_tol);
+  fill_info(c, z, info);
+  *out = z;
+  API_END
+}
+
+int mpo_apply_round(qtt_ctx* ctx, const qtt_mpo* M, const qtt_mps* x, qtt_trunc tr, qtt_mps** out,
+                    qtt_round_info* info) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && M && out, "apply: null argument");
+  check_mps(x, "apply x");
+  QTT_CHECK_ARG(M->n == x->n && M->d == x->d, "apply: operator and vector differ in n or d");
+  check_trunc(tr);
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  qtt_mps* y;
+  if (tr.rel_tol > 0.0) {
+    std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> e(mpo_mps_exact(c, M, x), free_mps);
+    y = round_any(c, e.get(), tr.chi_max, tr.rel_tol);
+  } else {
+    y = apply_round_gram(c, M, x, tr.chi_max, 0.0);
+  }
+  fill_info(c, y, info);
+  *out = y;
+  API_END
+}
+
+int mps_hadamard_round(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, qtt_trunc tr, const qtt_mps* init, int sweeps,
+                       qtt_mps** out, qtt_round_info* info) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && out, "hadamard: null argument");
+  check_mps(a, "hadamard a");
+  check_mps(b, "hadamard b");
+  QTT_CHECK_ARG(a->n == b->n && a->d == b->d, "hadamard: a and b differ in n or d");
+  QTT_CHECK_ARG(sweeps >= 0 && sweeps <= 1000, "hadamard: sweeps in [0, 1000]");
+  check_trunc(tr);
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  qtt_mps* y;
+  bool canonical;
+  if (init) {
+    QTT_CHECK_ARG(init->n == a->n && init->d == a->d, "hadamard: init shape");
+    y = mps_copy(c, init);
+    canonical = false;
+  } else {
+    y = zipup_hadamard(c, a, b, tr.chi_max);
+    canonical = true;
+  }
+  std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> guard(y, free_mps);
+  fit(c, {Term::had(1.0, a, b)}, y, sweeps, canonical);
+  fill_info(c, y, info);
+  *out = guard.release();
+  API_END
+}
+
+int qtt_sym_eig(qtt_ctx* ctx, int n, const double* S, double* w, double* V) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && S && w && V, "sym_eig: null argument");
+  QTT_CHECK_ARG(n >= 1 && n <= 160, "sym_eig: n in [1, 160]");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  size_t nn = size_t(n) * n;
+  DBuf dS(&c, nn), dw(&c, size_t(n)), dV(&c, nn);
+  QTT_CUDA(cudaMemcpyAsync(dS.p, S, nn * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  eigh(c, n, dS.p, dw.p, dV.p);
+  QTT_CUDA(cudaMemcpyAsync(w, dw.p, n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaMemcpyAsync(V, dV.p, nn * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  API_END
+}
+
+int mps_dot(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, double* out_host) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && out_host, "dot: null argument");
+  check_mps(a, "dot a");
+  check_mps(b, "dot b");
+  QTT_CHECK_ARG(a->n == b->n && a->d == b->d, "dot: a and b differ in n or d");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  DBuf d(&c, 1);
+  dot_dev(c, a, b, d.p);
+  QTT_CUDA(cudaMemcpyAsync(out_host, d.p, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  API_END
+}
+
+int poisson_solve(qtt_ctx* ctx, const qtt_mpo* A, const qtt_mps* b, qtt_mps* x_inout, const qtt_solve_opts* opts,
+                  double tol, qtt_solve_info* info) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && A && opts, "poisson_solve: null argument");
+  check_mps(b, "poisson_solve b");
+  check_mps(x_inout, "poisson_solve x");
+  QTT_CHECK_ARG(A->n == b->n && b->n == x_inout->n && A->d == b->d && b->d == x_inout->d, "poisson_solve: shapes");
+  QTT_CHECK_ARG(opts->sweeps >= 0 && opts->cg_iters >= 0 && opts->cg_tol >= 0.0, "poisson_solve: options");
+  for (int k = 1; k < x_inout->n; ++k)
+    QTT_CHECK_ARG(x_inout->bonds[k] <= x_inout->d * x_inout->bonds[k + 1] &&
+                      x_inout->bonds[k] <= x_inout->d * x_inout->bonds[k - 1],
+                  "poisson_solve: x bonds must satisfy r_k <= d r_{k+-1}");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  int cg = als(c, A, {Term::vec(1.0, b)}, x_inout, opts->sweeps, opts->cg_iters, opts->cg_tol, false, nullptr);
+  double rel = -1.0;
+  if (info || tol > 0.0) {
+    std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> y(mpo_mps_exact(c, A, x_inout), free_mps);
+    std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> r(direct_sum(c, 1.0, y.get(), -1.0, b), free_mps);
+    DBuf d(&c, 2);
+    norm_dev(c, r.get(), d.p);
+    norm_dev(c, b, d.p + 1);
+    double h[2];
+    QTT_CUDA(cudaMemcpyAsync(h, d.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    QTT_CUDA(cudaStreamSynchronize(c.stream));
+    rel = h[1] > 0 ? h[0] / h[1] : h[0];
+  }
+  if (info) {
+    info->cg_iters_total = cg;
+    info->rel_residual = rel;
+  }
+  if (tol > 0.0 && !(rel <= tol)) {
+    set_last_error("poisson_solve: relative residual " + std::to_string(rel) + " above tolerance");
+    return QTT_ERR_NOT_CONVERGED;
+  }
+  API_END
+}
+
+// ------------------------------------------------------------------ case
+
+int qtt_case_create(qtt_ctx* ctx, const qtt_case_params* p, qtt_case** out) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && p && out, "case_create: null argument");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  std::unique_ptr<qtt_case> h(new qtt_case);
+  h->ctx = &c;
+  h->cs = build_case(c, *p);
+  *out = h.release();
+  API_END
+}
+
+int qtt_case_free(qtt_case* h) {
+  API_BEGIN
+  if (h) {
+    delete h->cs;
+    delete h;
+  }
+  API_END
+}
+
+int qtt_case_set_state(qtt_case* h, const qtt_mps* u, const qtt_mps* v, const qtt_mps* p) {
+  API_BEGIN
+  QTT_CHECK_ARG(h, "case_set_state: null case");
+  check_mps(u, "case_set_state u");
+  check_mps(v, "case_set_state v");
+  check_mps(p, "case_set_state p");
+  Case& cs = *h->cs;
+  Ctx& c = *h->ctx;
+  const int n = cs.P.n_eta + cs.P.n_xi;
+  for (const qtt_mps* x : {u, v, p}) {
+    QTT_CHECK_ARG(x->n == n && x->d == 2, "case_set_state: field must have n_eta + n_xi cores of size 2");
+    for (int k = 1; k < n; ++k)
+      QTT_CHECK_ARG(x->bonds[k] <= 2 * x->bonds[k + 1] && x->bonds[k] <= 2 * x->bonds[k - 1],
+                    "case_set_state: bonds must satisfy r_k <= 2 r_{k+-1}");
+  }
+  qtt_mps* nu = mps_copy(c, u);
+  qtt_mps* nv = mps_copy(c, v);
+  qtt_mps* np = mps_copy(c, p);
+  right_orthonormalize(c, nu);
+  right_orthonormalize(c, nv);
+  right_orthonormalize(c, np);
+  if (cs.u) free_mps(cs.u);
+  if (cs.v) free_mps(cs.v);
+  if (cs.p) free_mps(cs.p);
+  cs.u = nu;
+  cs.v = nv;
+  cs.p = np;
+  API_END
+}
+
+int qtt_case_get_state(qtt_case* h, qtt_mps** u, qtt_mps** v, qtt_mps** p) {
+  API_BEGIN
+  QTT_CHECK_ARG(h, "case_get_state: null case");
+  Case& cs = *h->cs;
+  QTT_CHECK_ARG(cs.u && cs.v && cs.p, "case_get_state: state not set");
+  if (u) *u = mps_copy(*h->ctx, cs.u);
+  if (v) *v = mps_copy(*h->ctx, cs.v);
+  if (p) *p = mps_copy(*h->ctx, cs.p);
+  API_END
+}
+
+int qtt_case_get_operator(qtt_case* h, int which, qtt_mpo** out) {
+  API_BEGIN
+  QTT_CHECK_ARG(h && out, "case_get_operator: null argument");
+  Case& cs = *h->cs;
+  const qtt_mpo* ops[8] = {cs.Dx, cs.Dz, cs.Dxp, cs.Dzp, cs.H, cs.Ap, cs.Px, cs.Pz};
+  QTT_CHECK_ARG(which >= 0 && which < 8, "case_get_operator: which in [0, 7]");
+  const qtt_mpo* m = ops[which];
+  qtt_mpo* r = new_mpo(h->ctx, m->n, m->d, m->bonds);
+  copy(*h->ctx, r->buf.p, m->buf.p, m->off[m->n]);
+  *out = r;
+  API_END
+}
+
+int qtt_case_get_vector(qtt_case* h, int which, qtt_mps** out) {
+  API_BEGIN
+  QTT_CHECK_ARG(h && out, "case_get_vector: null argument");
+  Case& cs = *h->cs;
+  const qtt_mps* vs[8] = {cs.bcx_u, cs.bcz_u, cs.bcx_v, cs.bcz_v, cs.JbcLap_u, cs.JbcLap_v, cs.bcdiv_w, cs.absJ};
+  QTT_CHECK_ARG(which >= 0 && which < 8, "case_get_vector: which in [0, 7]");
+  *out = vs[which] ? mps_copy(*h->ctx, vs[which]) : nullptr;
+  API_END
+}
+
+int fractional_step(qtt_ctx* ctx, qtt_case* h, int nsteps, int with_forces, qtt_step_info* per_step) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && h, "fractional_step: null argument");
+  QTT_CHECK_ARG(nsteps >= 0, "fractional_step: nsteps >= 0");
+  Case& cs = *h->cs;
+  QTT_CHECK_ARG(cs.u && cs.v && cs.p, "fractional_step: state not set");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  DBuf rec(&c, size_t(std::max(nsteps, 1)) * 4);
+  fill(c, rec.p, int64_t(std::max(nsteps, 1)) * 4, 0.0);
+  for (int s = 0; s < nsteps; ++s) {
+    double* r = rec.p + 4 * s;
+    step(c, cs, per_step ? reinterpret_cast<int*>(r) : nullptr, (with_forces && per_step) ? r + 2 : nullptr);
+  }
+  if (per_step && nsteps > 0) {
+    std::vector<double> hrec(size_t(nsteps) * 4);
+    QTT_CUDA(cudaMemcpyAsync(hrec.data(), rec.p, hrec.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    QTT_CUDA(cudaStreamSynchronize(c.stream));
+    for (int s = 0; s < nsteps; ++s) {
+      int cg3[4];
+      std::memcpy(cg3, &hrec[4 * s], 2 * sizeof(double));
+      per_step[s].cg_u = cg3[0];
+      per_step[s].cg_v = cg3[1];
+      per_step[s].cg_p = cg3[2];
+      per_step[s].cd = with_forces ? hrec[4 * s + 2] : 0.0;
+      per_step[s].cl = with_forces ? hrec[4 * s + 3] : 0.0;
+    }
+  }
+  API_END
+}
+
+int qtt_case_forces(qtt_ctx* ctx, qtt_case* h, double* cd, double* cl) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && h && cd && cl, "case_forces: null argument");
+  Case& cs = *h->cs;
+  QTT_CHECK_ARG(cs.u && cs.v && cs.p, "case_forces: state not set");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  DBuf o(&c, 2);
+  case_forces(c, cs, o.p);
+  double hv[2];
+  QTT_CUDA(cudaMemcpyAsync(hv, o.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  *cd = hv[0];
+  *cl = hv[1];
+  API_END
+}
+
+int qtt_strouhal(const double* t, const double* cl, int n, double* st) {
+  API_BEGIN
+  QTT_CHECK_ARG(t && cl && st && n >= 2, "strouhal: need at least two samples");
+  double mean = 0;
+  for (int i = 0; i < n; ++i) mean += cl[i];
+  mean /= n;
+  std::vector<double> tc;
+  for (int i = 0; i + 1 < n; ++i) {
+    double a = cl[i] - mean, b = cl[i + 1] - mean;
+    if (a < 0 && b >= 0) tc.push_back(t[i] - a * (t[i + 1] - t[i]) / (b - a));
+  }
+  if (tc.size() < 2) {
+    *st = std::nan("");
+  } else {
+    double per = (tc.back() - tc.front()) / double(tc.size() - 1);
+    *st = 1.0 / per;
+  }
+  API_END
+}
+
+}  // extern "C"

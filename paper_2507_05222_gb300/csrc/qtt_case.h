@@ -1,0 +1,36 @@
+// Internal cylinder-case state (see qtt_case.cu).
+#pragma once
+
+#include <utility>
+#include <vector>
+
+#include "qtt_internal.h"
+
+namespace qtt {
+
+struct Case {
+  qtt_case_params P{};
+  double deta = 0, dxi = 0;
+  std::vector<std::pair<int, int>> layout;  // (axis, level) per core; axis 0 = eta, 1 = xi
+  // operators
+  qtt_mpo *Dx = nullptr, *Dz = nullptr, *Dxp = nullptr, *Dzp = nullptr, *H = nullptr, *Ap = nullptr,
+          *Px = nullptr, *Pz = nullptr, *Jdiag = nullptr;
+  // boundary vectors (null when identically zero) and |J|
+  qtt_mps *bcx_u = nullptr, *bcz_u = nullptr, *bcx_v = nullptr, *bcz_v = nullptr, *JbcLap_u = nullptr,
+          *JbcLap_v = nullptr, *bcdiv_w = nullptr, *absJ = nullptr;
+  // state
+  qtt_mps *u = nullptr, *v = nullptr, *p = nullptr;
+  ~Case();
+};
+
+Case* build_case(Ctx& c, const qtt_case_params& P);
+void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev);
+void case_forces(Ctx& c, Case& cs, double* out_dev);
+void read_row(Ctx& c, const Case& cs, const qtt_mps* x, int64_t I, double* row_dev);
+
+}  // namespace qtt
+
+struct qtt_case {
+  qtt::Ctx* ctx = nullptr;
+  qtt::Case* cs = nullptr;
+};

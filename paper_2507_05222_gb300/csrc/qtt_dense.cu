@@ -1,0 +1,470 @@
+// Dense building blocks of the QTT library: device pool, FP64 batched GEMM (split-K),
+// permutations, elementwise kernels, deterministic reductions and the einsum planner that
+// turns every core contraction into (permute +) batched GEMM.
+//
+// FP64 on GB300 runs at ~1/70 of the FP32 rate (about 1.7 DFMA per clock per SM), so the
+// GEMM kernel is bound by the FP64 pipe, not by memory: the design goal is enough CTAs
+// (>= 2 x 152) for every contraction, which small core contractions only reach through
+// split-K, and no host synchronisation between the many small launches.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "qtt_internal.h"
+
+namespace qtt {
+
+// ------------------------------------------------------------------ pool
+
+Pool::~Pool() {
+  for (auto& ch : chunks_) {
+    if (free_) free_(ch.first, user_);
+    else cudaFree(ch.first);
+  }
+}
+
+size_t Pool::size_class(size_t bytes) {
+  if (bytes < 256) return 256;
+  // 8 classes per power of two
+  size_t p = 1;
+  while (p * 2 <= bytes) p *= 2;
+  size_t step = p / 8 < 256 ? 256 : p / 8;
+  return (bytes + step - 1) / step * step;
+}
+
+void* Pool::raw_alloc(size_t bytes) {
+  void* p = nullptr;
+  if (alloc_) p = alloc_(bytes, user_);
+  else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+  if (!p) throw Error(QTT_ERR_ALLOC, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  chunks_.push_back({p, bytes});
+  held_ += bytes;
+  return p;
+}
+
+void* Pool::get(size_t bytes) {
+  size_t cls = size_class(bytes);
+  auto it = free_blocks_.lower_bound(cls);
+  if (it != free_blocks_.end() && it->first == cls) {
+    void* p = it->second;
+    free_blocks_.erase(it);
+    live_[p] = cls;
+    return p;
+  }
+  if (cls > cur_left_) {
+    size_t chunk = std::max<size_t>(cls, size_t(64) << 20);
+    cur_ = static_cast<char*>(raw_alloc(chunk));
+    cur_left_ = chunk;
+  }
+  void* p = cur_;
+  cur_ += cls;
+  cur_left_ -= cls;
+  live_[p] = cls;
+  return p;
+}
+
+void Pool::put(void* p) {
+  if (!p) return;
+  auto it = live_.find(p);
+  if (it == live_.end()) return;
+  free_blocks_.insert({it->second, p});
+  live_.erase(it);
+}
+
+DBuf::DBuf(Ctx* c, size_t count) { reset(c, count); }
+DBuf::~DBuf() {
+  if (ctx && p) ctx->pool->put(p);
+}
+DBuf& DBuf::operator=(DBuf&& o) noexcept {
+  if (this != &o) {
+    if (ctx && p) ctx->pool->put(p);
+    ctx = o.ctx; p = o.p; n = o.n;
+    o.p = nullptr; o.n = 0;
+  }
+  return *this;
+}
+void DBuf::reset(Ctx* c, size_t count) {
+  if (ctx && p) ctx->pool->put(p);
+  ctx = c;
+  n = count;
+  p = count ? static_cast<double*>(c->pool->get(count * sizeof(double))) : nullptr;
+}
+
+void after_launch(Ctx& c, const char* what) {
+  c.launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Error(QTT_ERR_CUDA, std::string("launch of ") + what + ": " + cudaGetErrorString(e));
+}
+
+TV tv(double* p, std::initializer_list<int64_t> dims) {
+  TV t;
+  t.p = p;
+  for (int64_t d : dims) t.dim[t.nd++] = d;
+  return t;
+}
+
+// ------------------------------------------------------------------ GEMM
+
+namespace {
+
+constexpr int GT = 64;   // CTA tile (rows and columns)
+constexpr int GK = 16;   // k step staged in shared memory
+
+// 256 threads (16 x 16); each thread owns a 4 x 4 block of outputs strided by 16, so that the
+// shared-memory reads of B are consecutive across a warp and those of A are broadcasts.
+__global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, int splits,
+                                              int64_t batch, double alpha, const double* __restrict__ A,
+                                              int64_t sAb, int64_t sAm, int64_t sAk,
+                                              const double* __restrict__ B, int64_t sBb, int64_t sBk,
+                                              int64_t sBn, double beta, double* __restrict__ C,
+                                              int64_t sCb, int64_t sCm, int64_t sCn,
+                                              double* __restrict__ W, const int* __restrict__ guard) {
+  if (guard && *guard == 0) return;
+  __shared__ double As[GK][GT];
+  __shared__ double Bs[GK][GT];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int t = ty * 16 + tx;
+  const int64_t n0 = int64_t(blockIdx.x) * GT, m0 = int64_t(blockIdx.y) * GT;
+  const int64_t b = blockIdx.z / splits;
+  const int sp = blockIdx.z % splits;
+  const int64_t k0 = sp * kchunk;
+  const int64_t k1 = min(K, k0 + kchunk);
+  const double* Ab = A + b * sAb;
+  const double* Bb = B + b * sBb;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const bool a_k_fast = (sAk == 1);
+  const bool b_n_fast = (sBn == 1);
+  for (int64_t kb = k0; kb < k1; kb += GK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int e = t + 256 * i;
+      int mm, kk;
+      if (a_k_fast) { mm = e / GK; kk = e % GK; } else { mm = e % GT; kk = e / GT; }
+      int64_t gm = m0 + mm, gk = kb + kk;
+      As[kk][mm] = (gm < M && gk < k1) ? Ab[gm * sAm + gk * sAk] : 0.0;
+      int nn, kk2;
+      if (b_n_fast) { kk2 = e / GT; nn = e % GT; } else { nn = e / GK; kk2 = e % GK; }
+      int64_t gn = n0 + nn, gk2 = kb + kk2;
+      Bs[kk2][nn] = (gn < N && gk2 < k1) ? Bb[gk2 * sBk + gn * sBn] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double a[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int64_t gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      if (W) {
+        W[((int64_t(sp) * batch + b) * M + gm) * N + gn] = acc[i][j];
+      } else {
+        double* cp = C + b * sCb + gm * sCm + gn * sCn;
+        *cp = (beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*cp);
+      }
+    }
+  }
+}
+
+__global__ void k_splitk_reduce(int64_t batch, int64_t M, int64_t N, int splits, double alpha,
+                                const double* __restrict__ W, double beta, double* __restrict__ C,
+                                int64_t sCb, int64_t sCm, int64_t sCn, const int* __restrict__ guard) {
+  if (guard && *guard == 0) return;
+  int64_t total = batch * M * N;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    double s = 0.0;
+    for (int sp = 0; sp < splits; ++sp) s += W[int64_t(sp) * total + e];
+    int64_t b = e / (M * N), r = e % (M * N), m = r / N, n = r % N;
+    double* cp = C + b * sCb + m * sCm + n * sCn;
+    *cp = (beta == 0.0) ? alpha * s : alpha * s + beta * (*cp);
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  return int(std::max<int64_t>(1, std::min<int64_t>(g, 65535 * 8)));
+}
+
+}  // namespace
+
+void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+          int64_t sAb, int64_t sAm, int64_t sAk, const double* B, int64_t sBb, int64_t sBk,
+          int64_t sBn, double beta, double* C, int64_t sCb, int64_t sCm, int64_t sCn) {
+  if (batch <= 0 || M <= 0 || N <= 0) return;
+  if (K <= 0) {  // C = beta C
+    if (beta == 1.0) return;
+    // treat as a split-K reduction over zero partial sums
+    DBuf W(&c, size_t(batch * M * N));
+    fill(c, W.p, batch * M * N, 0.0);
+    k_splitk_reduce<<<grid_for(batch * M * N, 256), 256, 0, c.stream>>>(batch, M, N, 1, alpha, W.p, beta, C, sCb, sCm, sCn, c.guard);
+    after_launch(c, "splitk_reduce");
+    return;
+  }
+  int64_t tiles = ((M + GT - 1) / GT) * ((N + GT - 1) / GT) * batch;
+  int64_t target = 2 * int64_t(c.num_sms);
+  int splits = 1;
+  if (tiles < target && K > 2 * GK) {
+    int64_t want = (target + tiles - 1) / tiles;
+    int64_t maxs = (K + 2 * GK - 1) / (2 * GK);   // at least 32 k per split
+    splits = int(std::max<int64_t>(1, std::min<int64_t>(want, maxs)));
+  }
+  int64_t kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + GK - 1) / GK * GK;
+  splits = int((K + kchunk - 1) / kchunk);
+  dim3 grid(unsigned((N + GT - 1) / GT), unsigned((M + GT - 1) / GT), unsigned(batch * splits));
+  QTT_CHECK_ARG(grid.y <= 65535 && grid.z <= 65535, "gemm grid too large");
+  dim3 block(16, 16);
+  if (splits == 1) {
+    k_gemm<<<grid, block, 0, c.stream>>>(M, N, K, kchunk, 1, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk, sBn,
+                                         beta, C, sCb, sCm, sCn, nullptr, c.guard);
+    after_launch(c, "gemm");
+  } else {
+    DBuf W(&c, size_t(splits) * batch * M * N);
+    k_gemm<<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
+                                         sBn, beta, C, sCb, sCm, sCn, W.p, c.guard);
+    after_launch(c, "gemm_splitk");
+    k_splitk_reduce<<<grid_for(batch * M * N, 256), 256, 0, c.stream>>>(batch, M, N, splits, alpha, W.p, beta, C,
+                                                                        sCb, sCm, sCn, c.guard);
+    after_launch(c, "splitk_reduce");
+  }
+}
+
+// ------------------------------------------------------------------ permute / elementwise
+
+namespace {
+
+struct PermArgs {
+  int nd;
+  int64_t out_dim[8];
+  int64_t in_stride[8];  // stride in the input of output axis i
+};
+
+__global__ void k_permute(const double* __restrict__ in, double* __restrict__ out, int64_t total, PermArgs a,
+                          double alpha, double beta, const int* __restrict__ guard) {
+  if (guard && *guard == 0) return;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    int64_t r = e, off = 0;
+    for (int i = a.nd - 1; i >= 0; --i) {
+      int64_t idx = r % a.out_dim[i];
+      r /= a.out_dim[i];
+      off += idx * a.in_stride[i];
+    }
+    double v = alpha * in[off];
+    out[e] = (beta == 0.0) ? v : v + beta * out[e];
+  }
+}
+
+__global__ void k_fill(double* x, int64_t n, double v) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) x[e] = v;
+}
+
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y,
+                        const int* __restrict__ guard) {
+  if (guard && *guard == 0) return;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    y[e] = (b == 0.0) ? a * x[e] : a * x[e] + b * y[e];
+}
+
+// One block; fixed reduction tree, so the result is bitwise reproducible.
+__global__ void __launch_bounds__(1024) k_dot(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+                                              double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s = fma(x[e], y[e], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *out = s;
+  }
+}
+
+}  // namespace
+
+void permute(Ctx& c, const double* in, int nd, const int64_t* in_dim, const int* perm, double* out, double alpha,
+             double beta) {
+  PermArgs a;
+  a.nd = nd;
+  int64_t stride[8];
+  int64_t s = 1;
+  for (int i = nd - 1; i >= 0; --i) { stride[i] = s; s *= in_dim[i]; }
+  for (int i = 0; i < nd; ++i) { a.out_dim[i] = in_dim[perm[i]]; a.in_stride[i] = stride[perm[i]]; }
+  int64_t total = s;
+  if (total == 0) return;
+  k_permute<<<grid_for(total, 256), 256, 0, c.stream>>>(in, out, total, a, alpha, beta, c.guard);
+  after_launch(c, "permute");
+}
+
+void fill(Ctx& c, double* x, int64_t n, double v) {
+  if (n <= 0) return;
+  k_fill<<<grid_for(n, 256), 256, 0, c.stream>>>(x, n, v);
+  after_launch(c, "fill");
+}
+
+void copy(Ctx& c, double* dst, const double* src, int64_t n) {
+  if (n <= 0) return;
+  QTT_CUDA(cudaMemcpyAsync(dst, src, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+}
+
+void axpby(Ctx& c, int64_t n, double a, const double* x, double b, double* y) {
+  if (n <= 0) return;
+  k_axpby<<<grid_for(n, 256), 256, 0, c.stream>>>(n, a, x, b, y, c.guard);
+  after_launch(c, "axpby");
+}
+
+void dot(Ctx& c, int64_t n, const double* x, const double* y, double* out_dev) {
+  k_dot<<<1, 1024, 0, c.stream>>>(n, x, y, out_dev);
+  after_launch(c, "dot");
+}
+
+// ------------------------------------------------------------------ einsum planner
+
+namespace {
+
+struct Lab {
+  char l;
+  int64_t d;
+};
+
+std::vector<char> labels(const std::string& s) { return std::vector<char>(s.begin(), s.end()); }
+
+int find(const std::vector<char>& v, char l) {
+  for (size_t i = 0; i < v.size(); ++i)
+    if (v[i] == l) return int(i);
+  return -1;
+}
+
+// Is the label order of `have` equal to the concatenation g1 + g2 + g3?
+bool is_order(const std::vector<char>& have, const std::vector<char>& g1, const std::vector<char>& g2,
+              const std::vector<char>& g3) {
+  std::vector<char> w(g1);
+  w.insert(w.end(), g2.begin(), g2.end());
+  w.insert(w.end(), g3.begin(), g3.end());
+  return w == have;
+}
+
+// Permutation taking `from` label order to `to` label order: perm[i] = axis of to[i] in from.
+std::vector<int> perm_of(const std::vector<char>& from, const std::vector<char>& to) {
+  std::vector<int> p(to.size());
+  for (size_t i = 0; i < to.size(); ++i) p[i] = find(from, to[i]);
+  return p;
+}
+
+std::vector<char> cat3(const std::vector<char>& a, const std::vector<char>& b, const std::vector<char>& c) {
+  std::vector<char> w(a);
+  w.insert(w.end(), b.begin(), b.end());
+  w.insert(w.end(), c.begin(), c.end());
+  return w;
+}
+
+}  // namespace
+
+void einsum(Ctx& c, const char* spec, double alpha, const TV& A, const TV& B, double beta, const TV& C) {
+  std::string s(spec);
+  size_t comma = s.find(','), arrow = s.find("->");
+  QTT_CHECK_ARG(comma != std::string::npos && arrow != std::string::npos, "einsum spec");
+  auto la = labels(s.substr(0, comma)), lb = labels(s.substr(comma + 1, arrow - comma - 1)),
+       lc = labels(s.substr(arrow + 2));
+  QTT_CHECK_ARG(int(la.size()) == A.nd && int(lb.size()) == B.nd && int(lc.size()) == C.nd,
+                std::string("einsum rank mismatch: ") + spec);
+  std::map<char, int64_t> dim;
+  auto reg = [&](const std::vector<char>& l, const TV& t) {
+    for (size_t i = 0; i < l.size(); ++i) {
+      auto it = dim.find(l[i]);
+      if (it == dim.end()) dim[l[i]] = t.dim[i];
+      else QTT_CHECK_ARG(it->second == t.dim[i], std::string("einsum dim mismatch: ") + spec);
+    }
+  };
+  reg(la, A); reg(lb, B); reg(lc, C);
+  std::vector<char> batch, fa, fb, kk;
+  for (char l : lc) {
+    bool ia = find(la, l) >= 0, ib = find(lb, l) >= 0;
+    QTT_CHECK_ARG(ia || ib, std::string("einsum output label not in inputs: ") + spec);
+    if (ia && ib) batch.push_back(l);
+    else if (ia) fa.push_back(l);
+    else fb.push_back(l);
+  }
+  for (char l : la)
+    if (find(lc, l) < 0) {
+      QTT_CHECK_ARG(find(lb, l) >= 0, std::string("einsum: label summed in one operand only: ") + spec);
+      kk.push_back(l);
+    }
+  for (char l : lb)
+    if (find(lc, l) < 0) QTT_CHECK_ARG(find(la, l) >= 0, std::string("einsum: label summed in one operand only: ") + spec);
+  auto prod = [&](const std::vector<char>& g) {
+    int64_t p = 1;
+    for (char l : g) p *= dim[l];
+    return p;
+  };
+  int64_t Bt = prod(batch), M = prod(fa), N = prod(fb), K = prod(kk);
+  if (Bt == 0 || M == 0 || N == 0) return;
+  // The contracted labels may be taken in the order of A or of B: pick the order that lets
+  // both operands be read in place, if any.
+  std::vector<char> kkB;
+  for (char l : lb)
+    if (find(kk, l) >= 0) kkB.push_back(l);
+  auto fitsA = [&](const std::vector<char>& k) { return is_order(la, batch, fa, k) || is_order(la, batch, k, fa); };
+  auto fitsB = [&](const std::vector<char>& k) { return is_order(lb, batch, k, fb) || is_order(lb, batch, fb, k); };
+  if (!(fitsA(kk) && fitsB(kk)) && fitsA(kkB) && fitsB(kkB)) kk = kkB;
+  else if (!fitsA(kk) && !fitsB(kk) && (fitsA(kkB) || fitsB(kkB))) kk = kkB;
+  // --- operand A: [batch][fa][k] (row-major M x K) or [batch][k][fa] (K x M)
+  const double* Ap = A.p;
+  DBuf Atmp;
+  int64_t sAm, sAk;
+  if (is_order(la, batch, fa, kk)) { sAm = K; sAk = 1; }
+  else if (is_order(la, batch, kk, fa)) { sAm = 1; sAk = M; }
+  else {
+    Atmp.reset(&c, size_t(A.size()));
+    auto p = perm_of(la, cat3(batch, fa, kk));
+    permute(c, A.p, A.nd, A.dim, p.data(), Atmp.p, 1.0, 0.0);
+    Ap = Atmp.p; sAm = K; sAk = 1;
+  }
+  // --- operand B: [batch][k][fb] (K x N) or [batch][fb][k]
+  const double* Bp = B.p;
+  DBuf Btmp;
+  int64_t sBk, sBn;
+  if (is_order(lb, batch, kk, fb)) { sBk = N; sBn = 1; }
+  else if (is_order(lb, batch, fb, kk)) { sBk = 1; sBn = K; }
+  else {
+    Btmp.reset(&c, size_t(B.size()));
+    auto p = perm_of(lb, cat3(batch, kk, fb));
+    permute(c, B.p, B.nd, B.dim, p.data(), Btmp.p, 1.0, 0.0);
+    Bp = Btmp.p; sBk = N; sBn = 1;
+  }
+  // --- output C: [batch][fa][fb] or [batch][fb][fa]; otherwise a temporary + permute
+  if (is_order(lc, batch, fa, fb)) {
+    gemm(c, Bt, M, N, K, alpha, Ap, M * K, sAm, sAk, Bp, K * N, sBk, sBn, beta, C.p, M * N, N, 1);
+  } else if (is_order(lc, batch, fb, fa)) {
+    gemm(c, Bt, M, N, K, alpha, Ap, M * K, sAm, sAk, Bp, K * N, sBk, sBn, beta, C.p, M * N, 1, M);
+  } else {
+    DBuf Ct(&c, size_t(Bt * M * N));
+    gemm(c, Bt, M, N, K, 1.0, Ap, M * K, sAm, sAk, Bp, K * N, sBk, sBn, 0.0, Ct.p, M * N, N, 1);
+    auto from = cat3(batch, fa, fb);
+    int64_t fdim[8];
+    for (size_t i = 0; i < from.size(); ++i) fdim[i] = dim[from[i]];
+    auto p = perm_of(from, lc);
+    permute(c, Ct.p, int(from.size()), fdim, p.data(), C.p, alpha, beta);
+  }
+}
+
+}  // namespace qtt

@@ -1,0 +1,173 @@
+// Internal declarations of the QTT GB300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/qtt.h"
+
+namespace qtt {
+
+// ------------------------------------------------------------------ errors
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void set_last_error(const std::string& msg);
+
+#define QTT_CHECK_ARG(cond, msg)                                   \
+  do {                                                             \
+    if (!(cond)) throw ::qtt::Error(QTT_ERR_ARG, std::string(msg)); \
+  } while (0)
+
+#define QTT_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      throw ::qtt::Error(QTT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ------------------------------------------------------------------ device memory pool
+
+// Stream-ordered pool: every allocation and every kernel of a context use one stream, so a
+// block freed on the host can be handed out again at once (work that uses the new owner is
+// enqueued after the work of the old owner).  Large chunks come from the user allocator.
+class Pool {
+ public:
+  Pool(qtt_alloc_fn a, qtt_free_fn f, void* user) : alloc_(a), free_(f), user_(user) {}
+  ~Pool();
+  void* get(size_t bytes);
+  void put(void* p);
+  size_t held() const { return held_; }
+
+ private:
+  static size_t size_class(size_t bytes);
+  void* raw_alloc(size_t bytes);
+  qtt_alloc_fn alloc_;
+  qtt_free_fn free_;
+  void* user_;
+  std::multimap<size_t, void*> free_blocks_;  // class size -> block
+  std::map<void*, size_t> live_;              // block -> class size
+  std::vector<std::pair<void*, size_t>> chunks_;
+  char* cur_ = nullptr;
+  size_t cur_left_ = 0;
+  size_t held_ = 0;
+};
+
+struct Ctx;
+
+// RAII device buffer from the context pool.
+struct DBuf {
+  Ctx* ctx = nullptr;
+  double* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(Ctx* c, size_t count);
+  ~DBuf();
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : ctx(o.ctx), p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept;
+  void reset(Ctx* c, size_t count);
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Pool* pool = nullptr;
+  int64_t launches = 0;
+  int num_sms = 152;
+  // When non-null, GEMM / permute / reduction kernels read *guard first and return at once
+  // if it is 0.  Set around the matrix-vector products of a CG solve so that iterations past
+  // convergence cost only their launches (the iteration budget is fixed on the host).
+  const int* guard = nullptr;
+};
+
+void after_launch(Ctx& c, const char* what);
+
+// ------------------------------------------------------------------ handles
+
+}  // namespace qtt
+
+struct qtt_mps {
+  qtt::Ctx* ctx = nullptr;
+  int n = 0, d = 2;
+  std::vector<int> bonds;       // n + 1
+  std::vector<int64_t> off;     // n + 1 offsets in doubles (off[n] = total)
+  qtt::DBuf buf;
+  double* core(int k) const { return buf.p + off[k]; }
+  int64_t core_size(int k) const { return off[k + 1] - off[k]; }
+};
+
+struct qtt_mpo {
+  qtt::Ctx* ctx = nullptr;
+  int n = 0, d = 2;
+  std::vector<int> bonds;
+  std::vector<int64_t> off;
+  qtt::DBuf buf;
+  double* core(int k) const { return buf.p + off[k]; }
+};
+
+namespace qtt {
+
+// Allocate an MPS with the given bonds (uninitialised cores).
+qtt_mps* new_mps(Ctx* c, int n, int d, const std::vector<int>& bonds);
+qtt_mpo* new_mpo(Ctx* c, int n, int d, const std::vector<int>& bonds);
+void free_mps(qtt_mps* x);
+void free_mpo(qtt_mpo* m);
+
+// ------------------------------------------------------------------ tensor views and kernels
+
+struct TV {            // row-major dense tensor view on the device
+  double* p = nullptr;
+  int nd = 0;
+  int64_t dim[8] = {0};
+  int64_t size() const {
+    int64_t s = 1;
+    for (int i = 0; i < nd; ++i) s *= dim[i];
+    return s;
+  }
+};
+TV tv(double* p, std::initializer_list<int64_t> dims);
+
+// C = alpha * einsum(spec, A, B) + beta * C.  spec like "ab,bc->ac" (single-letter labels).
+void einsum(Ctx& c, const char* spec, double alpha, const TV& A, const TV& B, double beta, const TV& C);
+
+// Batched strided GEMM: C[b](m,n) = alpha sum_k A[b](m,k) B[b](k,n) + beta C[b](m,n).
+void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+          int64_t sAb, int64_t sAm, int64_t sAk, const double* B, int64_t sBb, int64_t sBk,
+          int64_t sBn, double beta, double* C, int64_t sCb, int64_t sCm, int64_t sCn);
+
+// out = alpha * permute(in) + beta * out; perm[i] = input axis of output axis i.
+void permute(Ctx& c, const double* in, int nd, const int64_t* in_dim, const int* perm, double* out,
+             double alpha, double beta);
+
+// Elementwise helpers (device pointers, count n).
+void fill(Ctx& c, double* x, int64_t n, double v);
+void copy(Ctx& c, double* dst, const double* src, int64_t n);
+void axpby(Ctx& c, int64_t n, double a, const double* x, double b, double* y);  // y = a x + b y
+// Deterministic dot product into a device scalar.
+void dot(Ctx& c, int64_t n, const double* x, const double* y, double* out_dev);
+
+// ------------------------------------------------------------------ small dense linear algebra
+
+// Householder QR of `count` matrices (strided): A (m x n) = Q (m x kk) R (kk x n), kk = min(m,n).
+// trans = 1: the buffer holds A^T (n x m row-major) and Q^T (kk x m) is written.
+void qr(Ctx& c, int count, int m, int n, int trans, const double* A, int64_t in_stride, double* Q, int64_t q_stride,
+        double* R, int64_t r_stride);
+// Accurate (one-sided Jacobi, FP64) SVD of a small m x n matrix, m >= n: U (m x n), s, V (n x n).
+void svd_small(Ctx& c, int m, int n, const double* G, double* U, double* s, double* V);
+
+// Symmetric eigendecomposition of an n x n FP64 matrix S (row-major): eigenvalues descending
+// into w (n), eigenvectors as columns of V (n x n, row-major).  FP32 Jacobi in one CTA, then
+// FP64 Ogita-Aishima refinement sweeps on the tensor-free GEMM path.
+void eigh(Ctx& c, int n, const double* S, double* w, double* V);
+
+}  // namespace qtt

@@ -1,0 +1,519 @@
+// Small dense factorisations for the QTT sweeps, one CTA per matrix, operands in shared
+// memory:
+//   * Householder QR in FP64 (gauge moves of the fit and ALS sweeps; the orthogonalisation
+//     sweep of the accurate rounding);
+//   * one-sided (Hestenes) Jacobi SVD in FP64 for small accurate roundings (operator set-up,
+//     rel_tol > 0);
+//   * symmetric eigendecomposition: cyclic parallel Jacobi in FP32 (the FP32 pipe of GB300 is
+//     ~70x the FP64 pipe) followed by FP64 refinement of all eigenpairs with the
+//     Ogita-Aishima iteration (Ogita & Aishima, Japan J. Indust. Appl. Math. 35, 2018), whose
+//     matrix products run on the FP64 GEMM path across many SMs.
+// Every loop has a fixed upper bound; no kernel waits on another.
+#include <algorithm>
+#include <cmath>
+
+#include "qtt_internal.h"
+
+namespace qtt {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (all threads get the result).  red must hold 32 doubles.
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// ------------------------------------------------------------------ Householder QR (FP64)
+// A (m x n) = Q (m x kk) R (kk x n), kk = min(m, n).  Shared layout: column-major S[c*m + r].
+// trans = 0: input row-major (m x n), Q written row-major (m x kk).
+// trans = 1: the input buffer holds A^T row-major (n x m) -- i.e. exactly the column-major
+//            image -- and Q^T (kk x m) is written row-major.  This serves right-to-left
+//            sweeps, which factor the transpose of a core's (r_{k-1} x d r_k) unfolding.
+// Q may alias the input when kk == n.  R (kk x n, row-major) is written if non-null.
+__global__ void __launch_bounds__(256) k_qr(int m, int n, int trans, const double* __restrict__ Ain, double* Qall,
+                                            double* __restrict__ Rall, int64_t in_stride, int64_t q_stride,
+                                            int64_t r_stride) {
+  extern __shared__ double sm[];
+  const int kk = min(m, n);
+  double* S = sm;                 // m*n
+  double* v = S + size_t(m) * n;  // m (current reflector)
+  double* tau = v + m;            // kk
+  double* red = tau + kk;         // 32
+  const double* A = Ain + blockIdx.x * in_stride;
+  double* Q = Qall + blockIdx.x * q_stride;
+  double* R = Rall ? Rall + blockIdx.x * r_stride : nullptr;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  for (int e = tid; e < m * n; e += nt) {
+    if (trans) S[e] = A[e];
+    else S[(e % n) * m + e / n] = A[e];
+  }
+  __syncthreads();
+  for (int j = 0; j < kk; ++j) {
+    double* x = S + j * m;
+    double part = 0.0;
+    for (int i = j + 1 + tid; i < m; i += nt) part += x[i] * x[i];
+    double sigma = block_sum(part, red);
+    double alpha = x[j];
+    double beta, t, scale;
+    if (sigma == 0.0) {
+      t = 0.0; beta = alpha; scale = 0.0;
+    } else {
+      double nrm = sqrt(alpha * alpha + sigma);
+      beta = alpha >= 0.0 ? -nrm : nrm;
+      t = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    for (int i = j + tid; i < m; i += nt) v[i] = (i == j) ? 1.0 : x[i] * scale;
+    if (tid == 0) tau[j] = t;
+    __syncthreads();
+    for (int i = j + tid; i < m; i += nt) x[i] = (i == j) ? beta : v[i];
+    for (int c = j + 1 + warp; c < n; c += nwarps) {
+      double* y = S + c * m;
+      double w = 0.0;
+      for (int i = j + lane; i < m; i += 32) w += v[i] * y[i];
+      w = warp_sum(w) * t;
+      for (int i = j + lane; i < m; i += 32) y[i] -= w * v[i];
+    }
+    __syncthreads();
+  }
+  if (R) {
+    for (int e = tid; e < kk * n; e += nt) {
+      int r = e / n, c = e % n;
+      R[e] = (r <= c) ? S[c * m + r] : 0.0;
+    }
+  }
+  __syncthreads();
+  // Q = H_0 ... H_{kk-1} [I]_{:, :kk}, accumulated backwards in place in columns 0..kk-1.
+  for (int j = kk - 1; j >= 0; --j) {
+    double* x = S + j * m;
+    for (int i = j + 1 + tid; i < m; i += nt) v[i] = x[i];
+    __syncthreads();
+    const double t = tau[j];
+    for (int i = j + tid; i < m; i += nt) x[i] = (i == j) ? 1.0 - t : -t * v[i];
+    for (int c = j + 1 + tid; c < kk; c += nt) S[c * m + j] = 0.0;
+    __syncthreads();
+    for (int c = j + 1 + warp; c < kk; c += nwarps) {
+      double* y = S + c * m;
+      double w = 0.0;
+      for (int i = j + 1 + lane; i < m; i += 32) w += v[i] * y[i];
+      w = warp_sum(w) * t;
+      if (lane == 0) y[j] -= w;
+      for (int i = j + 1 + lane; i < m; i += 32) y[i] -= w * v[i];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < m * kk; e += nt) {
+    if (trans) Q[e] = S[e];                      // Q^T row-major (kk x m)
+    else Q[e] = S[(e % kk) * m + e / kk];        // Q row-major (m x kk)
+  }
+}
+
+// ------------------------------------------------------------------ one-sided Jacobi SVD (FP64)
+// G: m x n row-major (m >= n).  Outputs U (m x n, row-major), s (n, descending), V (n x n,
+// row-major, columns = right singular vectors).
+__global__ void __launch_bounds__(256) k_svd_jacobi(int m, int n, const double* __restrict__ G, double* __restrict__ U,
+                                                    double* __restrict__ s, double* __restrict__ Vout, int max_sweeps) {
+  extern __shared__ double sm[];
+  double* A = sm;                    // column-major m x n
+  double* V = A + size_t(m) * n;     // column-major n x n
+  double* nrm = V + size_t(n) * n;   // n
+  int* order = reinterpret_cast<int*>(nrm + n);  // n
+  __shared__ int rotated;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  for (int e = tid; e < m * n; e += nt) A[(e % n) * m + e / n] = G[e];
+  for (int e = tid; e < n * n; e += nt) V[e] = ((e / n) == (e % n)) ? 1.0 : 0.0;
+  __syncthreads();
+  const int np = (n + 1) & ~1;  // players (a dummy when n is odd)
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      // round-robin pairs: (r, np-1) and ((r+k) mod (np-1), (r-k) mod (np-1)), k = 1..np/2-1
+      for (int k = warp; k < np / 2; k += nwarps) {
+        int p, q;
+        if (k == 0) { p = r; q = np - 1; }
+        else { p = (r + k) % (np - 1); q = (r - k + (np - 1)) % (np - 1); }
+        if (p >= n || q >= n) continue;
+        if (p > q) { int tmp = p; p = q; q = tmp; }
+        double* ap = A + p * m;
+        double* aq = A + q * m;
+        double al = 0, be = 0, ga = 0;
+        for (int i = lane; i < m; i += 32) {
+          double x = ap[i], y = aq[i];
+          al += x * x; be += y * y; ga += x * y;
+        }
+        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+        if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+        double zeta = (be - al) / (2.0 * ga);
+        double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        for (int i = lane; i < m; i += 32) {
+          double x = ap[i], y = aq[i];
+          ap[i] = cs * x - sn * y;
+          aq[i] = sn * x + cs * y;
+        }
+        double* vp = V + p * n;
+        double* vq = V + q * n;
+        for (int i = lane; i < n; i += 32) {
+          double x = vp[i], y = vq[i];
+          vp[i] = cs * x - sn * y;
+          vq[i] = sn * x + cs * y;
+        }
+        if (lane == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  // singular values and a descending order (selection by rank counting, ties by index)
+  for (int c = warp; c < n; c += nwarps) {
+    double w = 0;
+    for (int i = lane; i < m; i += 32) w += A[c * m + i] * A[c * m + i];
+    w = warp_sum(w);
+    if (lane == 0) nrm[c] = sqrt(w);
+  }
+  __syncthreads();
+  for (int c = tid; c < n; c += nt) {
+    int rank = 0;
+    for (int o = 0; o < n; ++o)
+      if (nrm[o] > nrm[c] || (nrm[o] == nrm[c] && o < c)) ++rank;
+    order[rank] = c;
+  }
+  __syncthreads();
+  for (int e = tid; e < n; e += nt) s[e] = nrm[order[e]];
+  for (int e = tid; e < m * n; e += nt) {
+    int r = e / n, k = e % n;
+    int c = order[k];
+    double sv = nrm[c];
+    U[e] = sv > 0.0 ? A[c * m + r] / sv : 0.0;
+  }
+  for (int e = tid; e < n * n; e += nt) {
+    int r = e / n, k = e % n;
+    Vout[e] = V[order[k] * n + r];
+  }
+}
+
+// ------------------------------------------------------------------ symmetric Jacobi (FP32)
+// S: n x n FP64 row-major symmetric.  V (FP64 out, row-major n x n): eigenvectors as columns.
+// With t0_dev != null only the trailing block S[t0:, t0:] is diagonalised (t0 read on the
+// device) and Vout is the identity outside that block.
+__global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __restrict__ S, double* __restrict__ Vout,
+                                                     int max_sweeps, const int* __restrict__ t0_dev) {
+  extern __shared__ float smf[];
+  const int t0 = t0_dev ? *t0_dev : 0;
+  const int n = nfull - t0;
+  if (t0_dev) {
+    for (int e = threadIdx.x; e < nfull * nfull; e += blockDim.x) {
+      int i = e / nfull, j = e % nfull;
+      if (i < t0 || j < t0) Vout[e] = (i == j) ? 1.0 : 0.0;
+    }
+  }
+  if (n <= 1) {
+    if (n == 1 && threadIdx.x == 0) Vout[size_t(t0) * nfull + t0] = 1.0;
+    return;
+  }
+  const int ld = n + 1;                 // padded rows
+  float* A = smf;                       // n x ld
+  float* V = A + size_t(n) * ld;        // n x ld (row i = component i, column = vector)
+  float* cs = V + size_t(n) * ld;       // np/2
+  float* sn = cs + (n + 2) / 2;         // np/2
+  int* pp = reinterpret_cast<int*>(sn + (n + 2) / 2);
+  int* qq = pp + (n + 2) / 2;
+  __shared__ float red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    A[i * ld + j] = float(S[size_t(i + t0) * nfull + (j + t0)]);
+    V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  const int np = (n + 1) & ~1;
+  const int npairs = np / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // convergence test: off-diagonal mass relative to the total
+    float off = 0.f, tot = 0.f;
+    for (int e = tid; e < n * n; e += nt) {
+      int i = e / n, j = e % n;
+      float a = A[i * ld + j];
+      tot += a * a;
+      if (i != j) off += a * a;
+    }
+    off = warp_sumf(off); tot = warp_sumf(tot);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = off;
+    __syncthreads();
+    float offs = 0.f;
+    for (int i = 0; i < (nt >> 5); ++i) offs += red[i];
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = tot;
+    __syncthreads();
+    float tots = 0.f;
+    for (int i = 0; i < (nt >> 5); ++i) tots += red[i];
+    __syncthreads();
+    if (!(offs > 1e-13f * tots)) break;
+    for (int r = 0; r < np - 1; ++r) {
+      for (int k = tid; k < npairs; k += nt) {
+        int p, q;
+        if (k == 0) { p = r; q = np - 1; }
+        else { p = (r + k) % (np - 1); q = (r - k + (np - 1)) % (np - 1); }
+        if (p > q) { int t2 = p; p = q; q = t2; }
+        float c = 1.f, s = 0.f;
+        if (q < n) {
+          float apq = A[p * ld + q];
+          if (apq != 0.f) {
+            float tau = (A[q * ld + q] - A[p * ld + p]) / (2.f * apq);
+            float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + t * t);
+            s = t * c;
+          }
+        }
+        pp[k] = p; qq[k] = q; cs[k] = c; sn[k] = s;
+      }
+      __syncthreads();
+      // rows p, q of A
+      for (int e = tid; e < npairs * n; e += nt) {
+        int k = e / n, j = e % n;
+        int p = pp[k], q = qq[k];
+        if (q >= n) continue;
+        float c = cs[k], s = sn[k];
+        float x = A[p * ld + j], y = A[q * ld + j];
+        A[p * ld + j] = c * x - s * y;
+        A[q * ld + j] = s * x + c * y;
+      }
+      __syncthreads();
+      // columns p, q of A and of V
+      for (int e = tid; e < npairs * n; e += nt) {
+        int k = e / n, i = e % n;
+        int p = pp[k], q = qq[k];
+        if (q >= n) continue;
+        float c = cs[k], s = sn[k];
+        float x = A[i * ld + p], y = A[i * ld + q];
+        A[i * ld + p] = c * x - s * y;
+        A[i * ld + q] = s * x + c * y;
+        x = V[i * ld + p]; y = V[i * ld + q];
+        V[i * ld + p] = c * x - s * y;
+        V[i * ld + q] = s * x + c * y;
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < n * n; e += nt) Vout[size_t(e / n + t0) * nfull + (e % n + t0)] = double(V[(e / n) * ld + (e % n)]);
+}
+
+// First index of the sorted (descending) spectrum below tau * lambda_0; n if none.  Also
+// raises a flag when the tail holds at least two eigenvalues (else the refinement is skipped).
+__global__ void k_tail_start(int n, const double* __restrict__ lam, double tau, int* t0, int* need) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double top = lam[0];
+  int s = n;
+  if (top > 0.0) {
+    for (int i = 1; i < n; ++i)
+      if (lam[i] < tau * top) { s = i; break; }
+  }
+  *t0 = s;
+  *need = (n - s >= 2) ? 1 : 0;
+}
+
+// One Ogita-Aishima correction, given XtX, S_ = X^T A X (both n x n) and ||A||_F.
+// Writes E (n x n) such that X <- X + X E, and the current eigenvalue estimates lam.
+__global__ void __launch_bounds__(1024) k_oa_update(int n, const double* __restrict__ XtX, const double* __restrict__ SX,
+                                                    const double* __restrict__ anorm_dev, double* __restrict__ E,
+                                                    double* __restrict__ lam, const int* __restrict__ guard) {
+  if (guard && *guard == 0) return;
+  __shared__ double red[32];
+  const double anorm = *anorm_dev;
+  extern __shared__ double sl[];  // lam (n)
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) sl[i] = SX[i * n + i] / (1.0 - (1.0 - XtX[i * n + i]));
+  __syncthreads();
+  double so = 0.0, ro = 0.0;
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    double r = (i == j ? 1.0 : 0.0) - XtX[e];
+    double sd = SX[e] - (i == j ? sl[i] : 0.0);
+    so += sd * sd; ro += r * r;
+  }
+  double s2 = block_sum(so, red);
+  double r2 = block_sum(ro, red);
+  double delta = 2.0 * (sqrt(s2) + anorm * sqrt(r2));
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    double r = (i == j ? 1.0 : 0.0) - XtX[e];
+    double val;
+    if (i == j) val = 0.5 * r;
+    else {
+      double d = sl[j] - sl[i];
+      val = (fabs(d) > delta) ? (SX[e] + sl[j] * r) / d : 0.5 * r;
+    }
+    E[e] = val;
+  }
+  for (int i = tid; i < n; i += nt) lam[i] = sl[i];
+}
+
+// Order eigenpairs by decreasing eigenvalue: w[k] = lam[order[k]], V[:, k] = X[:, order[k]].
+__global__ void __launch_bounds__(1024) k_sort_eig(int n, const double* __restrict__ lam, const double* __restrict__ X,
+                                                   double* __restrict__ w, double* __restrict__ V) {
+  extern __shared__ int ord[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int c = tid; c < n; c += nt) {
+    int rank = 0;
+    for (int o = 0; o < n; ++o)
+      if (lam[o] > lam[c] || (lam[o] == lam[c] && o < c)) ++rank;
+    ord[rank] = c;
+  }
+  __syncthreads();
+  for (int k = tid; k < n; k += nt) w[k] = lam[ord[k]];
+  for (int e = tid; e < n * n; e += nt) {
+    int r = e / n, k = e % n;
+    V[e] = X[r * n + ord[k]];
+  }
+}
+
+__global__ void k_copy_guarded(double* __restrict__ dst, const double* __restrict__ src, int64_t n,
+                               const int* __restrict__ guard) {
+  if (*guard == 0) return;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    dst[e] = src[e];
+}
+
+__global__ void k_frob(int64_t n, const double* __restrict__ x, double* out) {
+  __shared__ double red[32];
+  double s = 0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s += x[e] * x[e];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+}  // namespace
+
+static void copy_guarded(Ctx& c, double* dst, const double* src, int64_t n, const int* guard) {
+  int g = int(std::min<int64_t>((n + 255) / 256, 4096));
+  k_copy_guarded<<<g, 256, 0, c.stream>>>(dst, src, n, guard);
+  after_launch(c, "copy_guarded");
+}
+
+static size_t qr_smem(int m, int n) { return (size_t(m) * n + m + std::min(m, n) + 32) * sizeof(double); }
+
+void qr(Ctx& c, int count, int m, int n, int trans, const double* A, int64_t in_stride, double* Q, int64_t q_stride,
+        double* R, int64_t r_stride) {
+  if (count <= 0 || n <= 0 || m <= 0) return;
+  size_t sm = qr_smem(m, n);
+  if (sm > 220 * 1024)
+    throw Error(QTT_ERR_UNSUPPORTED, "qr: matrix " + std::to_string(m) + "x" + std::to_string(n) + " too large for one CTA");
+  static bool attr = false;
+  if (!attr) {
+    QTT_CUDA(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    attr = true;
+  }
+  k_qr<<<count, 256, sm, c.stream>>>(m, n, trans, A, Q, R, in_stride, q_stride, r_stride);
+  after_launch(c, "qr");
+}
+
+// Accurate SVD of small matrices: G (m x n, m >= n) = U diag(s) V^T.
+void svd_small(Ctx& c, int m, int n, const double* G, double* U, double* s, double* V) {
+  QTT_CHECK_ARG(m >= n, "svd: needs m >= n");
+  size_t sm = (size_t(m) * n + size_t(n) * n + n) * sizeof(double) + n * sizeof(int);
+  if (sm > 220 * 1024) throw Error(QTT_ERR_UNSUPPORTED, "svd: matrix too large for one CTA");
+  static bool attr = false;
+  if (!attr) {
+    QTT_CUDA(cudaFuncSetAttribute(k_svd_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    attr = true;
+  }
+  k_svd_jacobi<<<1, 256, sm, c.stream>>>(m, n, G, U, s, V, 60);
+  after_launch(c, "svd_jacobi");
+}
+
+// One Ogita-Aishima iteration on X (n x n) for the symmetric S.
+static void oa_iteration(Ctx& c, int n, const double* S, double* X, double* XtX, double* AX, double* SX, double* E,
+                         double* lam, const double* an) {
+  gemm(c, 1, n, n, n, 1.0, X, 0, 1, n, X, 0, n, 1, 0.0, XtX, 0, n, 1);   // X^T X
+  gemm(c, 1, n, n, n, 1.0, S, 0, n, 1, X, 0, n, 1, 0.0, AX, 0, n, 1);    // S X
+  gemm(c, 1, n, n, n, 1.0, X, 0, 1, n, AX, 0, n, 1, 0.0, SX, 0, n, 1);   // X^T S X
+  k_oa_update<<<1, 1024, n * sizeof(double), c.stream>>>(n, XtX, SX, an, E, lam, c.guard);
+  after_launch(c, "oa_update");
+  gemm(c, 1, n, n, n, 1.0, X, 0, n, 1, E, 0, n, 1, 0.0, AX, 0, n, 1);    // X E
+  axpby(c, int64_t(n) * n, 1.0, AX, 1.0, X);
+}
+
+// Symmetric eigendecomposition to FP64 accuracy (absolute error ~ eps_64 ||S||) from FP32
+// Jacobi sweeps: level 1 diagonalises S in FP32 and refines all pairs in FP64 (Ogita-Aishima);
+// eigenvalues closer than the FP32 resolution (~1e-7 ||S||) stay lumped in a cluster, so
+// levels 2 and 3 re-diagonalise the trailing block of X^T S X (the eigenvalues below
+// 1e-5 and 1e-10 of the largest) on its own scale and refine again.  Levels with fewer than
+// two tail eigenvalues are skipped on the device.
+void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
+  QTT_CHECK_ARG(n >= 1, "eigh: n >= 1");
+  if (n > 160) throw Error(QTT_ERR_UNSUPPORTED, "eigh: n > 160 not supported");
+  size_t smf = (size_t(n) * (n + 1) * 2 + 2 * ((n + 2) / 2)) * sizeof(float) + 2 * ((n + 2) / 2) * sizeof(int);
+  static bool attr = false;
+  if (!attr) {
+    QTT_CUDA(cudaFuncSetAttribute(k_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    attr = true;
+  }
+  const size_t nn = size_t(n) * n;
+  DBuf X(&c, nn), Xs(&c, nn), XtX(&c, nn), AX(&c, nn), SX(&c, nn), E(&c, nn), Y(&c, nn), lam(&c, size_t(n)),
+      an(&c, 1), flags(&c, 2);
+  int* t0 = reinterpret_cast<int*>(flags.p);
+  int* need = t0 + 1;
+  k_jacobi_f32<<<1, 1024, smf, c.stream>>>(n, S, X.p, 12, nullptr);
+  after_launch(c, "jacobi_f32");
+  k_frob<<<1, 1024, 0, c.stream>>>(int64_t(n) * n, S, an.p);
+  after_launch(c, "frob");
+  const double taus[3] = {0.0, 1e-5, 1e-10};
+  for (int level = 0; level < 3; ++level) {
+    if (level > 0) {
+      k_tail_start<<<1, 1, 0, c.stream>>>(n, lam.p, taus[level], t0, need);
+      after_launch(c, "tail_start");
+      c.guard = need;
+      gemm(c, 1, n, n, n, 1.0, S, 0, n, 1, X.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
+      gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, AX.p, 0, n, 1, 0.0, SX.p, 0, n, 1);
+      c.guard = nullptr;
+      k_jacobi_f32<<<1, 1024, smf, c.stream>>>(n, SX.p, Y.p, 12, t0);
+      after_launch(c, "jacobi_f32_tail");
+      c.guard = need;
+      gemm(c, 1, n, n, n, 1.0, X.p, 0, n, 1, Y.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
+      copy_guarded(c, X.p, AX.p, int64_t(nn), need);
+    }
+    for (int it = 0; it < 3; ++it) oa_iteration(c, n, S, X.p, XtX.p, AX.p, SX.p, E.p, lam.p, an.p);
+    c.guard = nullptr;
+    // eigenvalue estimates of the refined vectors, then sort (descending)
+    gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, X.p, 0, n, 1, 0.0, XtX.p, 0, n, 1);
+    gemm(c, 1, n, n, n, 1.0, S, 0, n, 1, X.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
+    gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, AX.p, 0, n, 1, 0.0, SX.p, 0, n, 1);
+    k_oa_update<<<1, 1024, n * sizeof(double), c.stream>>>(n, XtX.p, SX.p, an.p, E.p, lam.p, nullptr);
+    after_launch(c, "oa_update");
+    k_sort_eig<<<1, 1024, n * sizeof(int), c.stream>>>(n, lam.p, X.p, w, Xs.p);
+    after_launch(c, "sort_eig");
+    copy(c, X.p, Xs.p, int64_t(nn));
+    copy(c, lam.p, w, n);
+  }
+  // Two Newton-Schulz steps X <- X (3 I - X^T X) / 2: the first-order orthonormalisation of
+  // the refinement leaves ~eps ||S|| / gap in X^T X - I for close pairs; each step squares it.
+  for (int it = 0; it < 2; ++it) {
+    gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, X.p, 0, n, 1, 0.0, XtX.p, 0, n, 1);
+    gemm(c, 1, n, n, n, 1.0, X.p, 0, n, 1, XtX.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
+    axpby(c, int64_t(nn), -0.5, AX.p, 1.5, X.p);
+  }
+  copy(c, V, X.p, int64_t(nn));
+}
+
+}  // namespace qtt

@@ -1,0 +1,446 @@
+"""Python binding of the QTT GB300 library (include/qtt.h) -- argument marshalling only.
+
+Every computation happens in the CUDA library ``_build/libqtt.so``; this module never falls
+back to host arithmetic.  If the library is missing, loading raises.  PyTorch provides the
+device memory (caching allocator, through the library's allocator hooks) and the stream.
+
+Function names follow the C ABI: ``qtt_encode``, ``mpo_apply_round``, ``mps_hadamard_round``,
+``mps_axpby_round``, ``poisson_solve``, ``fractional_step`` (plus helpers).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libqtt.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "qtt.h")
+
+QTT_HOST, QTT_DEVICE = 0, 1
+QTT_ORDER_SEQUENTIAL, QTT_ORDER_INTERLEAVED = 0, 1
+ORDERING = {"sequential": QTT_ORDER_SEQUENTIAL, "interleaved": QTT_ORDER_INTERLEAVED}
+ERRORS = {-1: "QTT_ERR_ARG", -2: "QTT_ERR_ALLOC", -3: "QTT_ERR_CUDA", -4: "QTT_ERR_NOT_CONVERGED",
+          -5: "QTT_ERR_TIMEOUT", -6: "QTT_ERR_NONFINITE", -7: "QTT_ERR_UNSUPPORTED"}
+
+
+class QttError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class qtt_trunc(C.Structure):
+    _fields_ = [("chi_max", C.c_int), ("rel_tol", C.c_double)]
+
+
+class qtt_round_info(C.Structure):
+    _fields_ = [("max_bond", C.c_int), ("norm", C.c_double)]
+
+
+class qtt_solve_opts(C.Structure):
+    _fields_ = [("sweeps", C.c_int), ("cg_iters", C.c_int), ("cg_tol", C.c_double)]
+
+
+class qtt_solve_info(C.Structure):
+    _fields_ = [("cg_iters_total", C.c_int), ("rel_residual", C.c_double)]
+
+
+class qtt_case_params(C.Structure):
+    _fields_ = [("n_eta", C.c_int), ("n_xi", C.c_int), ("ordering", C.c_int), ("D", C.c_double),
+                ("R", C.c_double), ("Re", C.c_double), ("dt", C.c_double), ("rot", C.c_double),
+                ("u_inf", C.c_double), ("chi", C.c_int), ("fit_sweeps", C.c_int),
+                ("mom", qtt_solve_opts), ("poi", qtt_solve_opts)]
+
+
+class qtt_step_info(C.Structure):
+    _fields_ = [("cg_u", C.c_int), ("cg_v", C.c_int), ("cg_p", C.c_int), ("cd", C.c_double), ("cl", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_lib = None
+P = C.c_void_p
+I, D, L, S = C.c_int, C.c_double, C.c_int64, C.c_size_t
+DP = C.POINTER(C.c_double)
+IP = C.POINTER(C.c_int)
+
+_SIGS = {
+    "qtt_ctx_create": (I, [C.POINTER(P), I, P, ALLOC_FN, FREE_FN, P]),
+    "qtt_ctx_destroy": (None, [P]),
+    "qtt_ctx_sync": (I, [P]),
+    "qtt_last_error": (C.c_char_p, []),
+    "qtt_ctx_kernel_launches": (L, [P]),
+    "qtt_ctx_pool_bytes": (S, [P]),
+    "qtt_mps_create": (I, [P, I, I, IP, DP, I, C.POINTER(P)]),
+    "qtt_mps_free": (I, [P]),
+    "qtt_mps_n": (I, [P]),
+    "qtt_mps_d": (I, [P]),
+    "qtt_mps_bonds": (I, [P, IP]),
+    "qtt_mps_size": (L, [P]),
+    "qtt_mps_get_cores": (I, [P, DP, I]),
+    "qtt_mps_device_ptr": (P, [P]),
+    "qtt_mps_copy": (I, [P, C.POINTER(P)]),
+    "qtt_mpo_create": (I, [P, I, I, IP, DP, I, C.POINTER(P)]),
+    "qtt_mpo_free": (I, [P]),
+    "qtt_mpo_bonds": (I, [P, IP]),
+    "qtt_mpo_get_cores": (I, [P, DP, I]),
+    "qtt_encode": (I, [P, DP, I, I, I, qtt_trunc, C.POINTER(P), C.POINTER(qtt_round_info)]),
+    "qtt_decode": (I, [P, P, DP, I]),
+    "qtt_field_to_vector": (I, [P, DP, DP, I, I, I, I, I]),
+    "qtt_round": (I, [P, P, qtt_trunc, C.POINTER(P), C.POINTER(qtt_round_info)]),
+    "mps_axpby_round": (I, [P, D, P, D, P, qtt_trunc, C.POINTER(P), C.POINTER(qtt_round_info)]),
+    "mpo_apply_round": (I, [P, P, P, qtt_trunc, C.POINTER(P), C.POINTER(qtt_round_info)]),
+    "mps_hadamard_round": (I, [P, P, P, qtt_trunc, P, I, C.POINTER(P), C.POINTER(qtt_round_info)]),
+    "mps_dot": (I, [P, P, P, DP]),
+    "qtt_sym_eig": (I, [P, I, DP, DP, DP]),
+    "poisson_solve": (I, [P, P, P, P, C.POINTER(qtt_solve_opts), D, C.POINTER(qtt_solve_info)]),
+    "qtt_case_create": (I, [P, C.POINTER(qtt_case_params), C.POINTER(P)]),
+    "qtt_case_free": (I, [P]),
+    "qtt_case_set_state": (I, [P, P, P, P]),
+    "qtt_case_get_state": (I, [P, C.POINTER(P), C.POINTER(P), C.POINTER(P)]),
+    "qtt_case_get_operator": (I, [P, I, C.POINTER(P)]),
+    "qtt_case_get_vector": (I, [P, I, C.POINTER(P)]),
+    "fractional_step": (I, [P, P, I, I, C.POINTER(qtt_step_info)]),
+    "qtt_case_forces": (I, [P, P, DP, DP]),
+    "qtt_strouhal": (I, [DP, DP, I, DP]),
+}
+
+
+def header_functions(path: str = HEADER) -> list[str]:
+    """Names of the functions declared in include/qtt.h."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?!typedef)(?:const\s+)?[A-Za-z_][\w]*\s*\**\s+\**\s*([a-z_][a-z0-9_]*)\s*\(",
+                       txt, flags=re.M)
+    return sorted(set(names))
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"QTT CUDA library not built ({LIB_PATH}); run __graft_entry__.build()")
+        h = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(h, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = h
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise QttError(rc, lib().qtt_last_error().decode())
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(DP)
+
+
+# ------------------------------------------------------------------ context
+
+class Context:
+    """One device, one stream (torch's current stream unless given), torch-backed device memory."""
+
+    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = True):
+        import torch
+        self.device = device
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        sp = P(self.stream.cuda_stream)
+        if use_torch_allocator:
+            dev, st = device, self.stream
+
+            def _alloc(nbytes, _user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+                except Exception:
+                    return None
+
+            def _free(ptr, _user):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._alloc = ALLOC_FN(_alloc)
+            self._free = FREE_FN(_free)
+        else:
+            self._alloc = ALLOC_FN()
+            self._free = FREE_FN()
+        h = P()
+        _check(lib().qtt_ctx_create(C.byref(h), device, sp, self._alloc, self._free, None))
+        self.h = h
+
+    def sync(self):
+        _check(lib().qtt_ctx_sync(self.h))
+
+    def kernel_launches(self) -> int:
+        return int(lib().qtt_ctx_kernel_launches(self.h))
+
+    def pool_bytes(self) -> int:
+        return int(lib().qtt_ctx_pool_bytes(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qtt_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MPS:
+    """Handle of a qtt_mps (cores live on the device)."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    @classmethod
+    def from_cores(cls, ctx: Context, cores) -> "MPS":
+        n = len(cores)
+        d = cores[0].shape[1]
+        bonds = np.array([cores[0].shape[0]] + [c.shape[2] for c in cores], dtype=np.int32)
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64).ravel() for c in cores]))
+        h = P()
+        _check(lib().qtt_mps_create(ctx.h, n, d, bonds.ctypes.data_as(IP), _dp(flat), QTT_HOST, C.byref(h)))
+        return cls(ctx, h)
+
+    @property
+    def n(self) -> int:
+        return lib().qtt_mps_n(self.h)
+
+    @property
+    def d(self) -> int:
+        return lib().qtt_mps_d(self.h)
+
+    def bonds(self) -> list[int]:
+        b = np.zeros(self.n + 1, dtype=np.int32)
+        _check(lib().qtt_mps_bonds(self.h, b.ctypes.data_as(IP)))
+        return [int(v) for v in b]
+
+    def cores(self) -> list[np.ndarray]:
+        b = self.bonds()
+        d = self.d
+        flat = np.zeros(int(lib().qtt_mps_size(self.h)))
+        _check(lib().qtt_mps_get_cores(self.h, _dp(flat), QTT_HOST))
+        out, o = [], 0
+        for k in range(self.n):
+            sz = b[k] * d * b[k + 1]
+            out.append(flat[o:o + sz].reshape(b[k], d, b[k + 1]).copy())
+            o += sz
+        return out
+
+    def copy(self) -> "MPS":
+        h = P()
+        _check(lib().qtt_mps_copy(self.h, C.byref(h)))
+        return MPS(self.ctx, h)
+
+    def __del__(self):
+        # Handles die with their context's pool: free only while the context is open.
+        try:
+            if self.h and self.ctx.h:
+                lib().qtt_mps_free(self.h)
+            self.h = None
+        except Exception:
+            pass
+
+
+class MPO:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    @classmethod
+    def from_cores(cls, ctx: Context, cores) -> "MPO":
+        n = len(cores)
+        d = cores[0].shape[1]
+        bonds = np.array([cores[0].shape[0]] + [c.shape[3] for c in cores], dtype=np.int32)
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64).ravel() for c in cores]))
+        h = P()
+        _check(lib().qtt_mpo_create(ctx.h, n, d, bonds.ctypes.data_as(IP), _dp(flat), QTT_HOST, C.byref(h)))
+        return cls(ctx, h)
+
+    def bonds(self) -> list[int]:
+        b = np.zeros(65, dtype=np.int32)
+        _check(lib().qtt_mpo_bonds(self.h, b.ctypes.data_as(IP)))
+        nz = int(np.nonzero(b)[0][-1]) + 1
+        return [int(v) for v in b[:nz]]
+
+    def cores(self) -> list[np.ndarray]:
+        b = self.bonds()
+        n = len(b) - 1
+        tot = sum(b[k] * 4 * b[k + 1] for k in range(n))
+        flat = np.zeros(tot)
+        _check(lib().qtt_mpo_get_cores(self.h, _dp(flat), QTT_HOST))
+        out, o = [], 0
+        for k in range(n):
+            sz = b[k] * 4 * b[k + 1]
+            out.append(flat[o:o + sz].reshape(b[k], 2, 2, b[k + 1]).copy())
+            o += sz
+        return out
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                lib().qtt_mpo_free(self.h)
+            self.h = None
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ operations (C-ABI names)
+
+def _trunc(chi, rel_tol):
+    return qtt_trunc(int(chi), float(rel_tol))
+
+
+def qtt_encode(ctx: Context, dense, n: int, chi: int, rel_tol: float = 0.0, d: int = 2) -> MPS:
+    a = np.ascontiguousarray(np.asarray(dense, dtype=np.float64).ravel())
+    h = P()
+    _check(lib().qtt_encode(ctx.h, _dp(a), QTT_HOST, n, d, _trunc(chi, rel_tol), C.byref(h), None))
+    return MPS(ctx, h)
+
+
+def qtt_decode(ctx: Context, x: MPS) -> np.ndarray:
+    out = np.zeros(x.d ** x.n)
+    _check(lib().qtt_decode(ctx.h, x.h, _dp(out), QTT_HOST))
+    return out
+
+
+def qtt_field_to_vector(ctx: Context, field, ordering: str, inverse: bool = False) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(field, dtype=np.float64))
+    if inverse:
+        raise ValueError("use qtt_vector_to_field")
+    ne, nx = int(np.log2(a.shape[0])), int(np.log2(a.shape[1]))
+    out = np.zeros(a.size)
+    _check(lib().qtt_field_to_vector(ctx.h, _dp(a), _dp(out), QTT_HOST, ne, nx, ORDERING[ordering], 0))
+    return out
+
+
+def qtt_vector_to_field(ctx: Context, vec, n_eta: int, n_xi: int, ordering: str) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(vec, dtype=np.float64).ravel())
+    out = np.zeros(a.size)
+    _check(lib().qtt_field_to_vector(ctx.h, _dp(a), _dp(out), QTT_HOST, n_eta, n_xi, ORDERING[ordering], 1))
+    return out.reshape(2 ** n_eta, 2 ** n_xi)
+
+
+def qtt_round(ctx: Context, x: MPS, chi: int, rel_tol: float = 0.0) -> MPS:
+    h = P()
+    _check(lib().qtt_round(ctx.h, x.h, _trunc(chi, rel_tol), C.byref(h), None))
+    return MPS(ctx, h)
+
+
+def mps_axpby_round(ctx: Context, alpha: float, x: MPS, beta: float, y: MPS, chi: int, rel_tol: float = 0.0) -> MPS:
+    h = P()
+    _check(lib().mps_axpby_round(ctx.h, alpha, x.h, beta, y.h, _trunc(chi, rel_tol), C.byref(h), None))
+    return MPS(ctx, h)
+
+
+def mpo_apply_round(ctx: Context, M: MPO, x: MPS, chi: int, rel_tol: float = 0.0) -> MPS:
+    h = P()
+    _check(lib().mpo_apply_round(ctx.h, M.h, x.h, _trunc(chi, rel_tol), C.byref(h), None))
+    return MPS(ctx, h)
+
+
+def mps_hadamard_round(ctx: Context, a: MPS, b: MPS, chi: int, sweeps: int = 2, init: MPS | None = None) -> MPS:
+    h = P()
+    _check(lib().mps_hadamard_round(ctx.h, a.h, b.h, _trunc(chi, 0.0), init.h if init is not None else None,
+                                    sweeps, C.byref(h), None))
+    return MPS(ctx, h)
+
+
+def qtt_sym_eig(ctx: Context, S):
+    """(w descending, V with eigenvectors as columns) of a small symmetric matrix."""
+    S = np.ascontiguousarray(np.asarray(S, dtype=np.float64))
+    n = S.shape[0]
+    w = np.zeros(n); V = np.zeros((n, n))
+    _check(lib().qtt_sym_eig(ctx.h, n, _dp(S), _dp(w), _dp(V)))
+    return w, V
+
+
+def mps_dot(ctx: Context, a: MPS, b: MPS) -> float:
+    out = C.c_double()
+    _check(lib().mps_dot(ctx.h, a.h, b.h, C.byref(out)))
+    return out.value
+
+
+def poisson_solve(ctx: Context, A: MPO, b: MPS, x: MPS, sweeps: int, cg_iters: int, cg_tol: float,
+                  tol: float = 0.0, residual: bool = True):
+    """Solve A x = b in place on x; returns (cg_iterations, relative_residual)."""
+    o = qtt_solve_opts(sweeps, cg_iters, cg_tol)
+    info = qtt_solve_info()
+    rc = lib().poisson_solve(ctx.h, A.h, b.h, x.h, C.byref(o), tol, C.byref(info) if residual else None)
+    _check(rc)
+    return info.cg_iters_total, info.rel_residual
+
+
+# ------------------------------------------------------------------ cylinder case
+
+class Case:
+    def __init__(self, ctx: Context, n_eta: int, n_xi: int, R: float, Re: float, dt: float, chi: int,
+                 ordering: str = "interleaved", D: float = 1.0, rot: float = 0.0, u_inf: float = 1.0,
+                 fit_sweeps: int = 1, mom=(1, 8, 1e-12), poi=(2, 20, 1e-12)):
+        self.ctx = ctx
+        self.params = qtt_case_params(n_eta, n_xi, ORDERING[ordering], D, R, Re, dt, rot, u_inf, chi, fit_sweeps,
+                                      qtt_solve_opts(*mom), qtt_solve_opts(*poi))
+        h = P()
+        _check(lib().qtt_case_create(ctx.h, C.byref(self.params), C.byref(h)))
+        self.h = h
+
+    def set_state(self, u: MPS, v: MPS, p: MPS):
+        _check(lib().qtt_case_set_state(self.h, u.h, v.h, p.h))
+
+    def get_state(self):
+        hu, hv, hp = P(), P(), P()
+        _check(lib().qtt_case_get_state(self.h, C.byref(hu), C.byref(hv), C.byref(hp)))
+        return MPS(self.ctx, hu), MPS(self.ctx, hv), MPS(self.ctx, hp)
+
+    def operator(self, which: int) -> MPO:
+        h = P()
+        _check(lib().qtt_case_get_operator(self.h, which, C.byref(h)))
+        return MPO(self.ctx, h)
+
+    def vector(self, which: int):
+        h = P()
+        _check(lib().qtt_case_get_vector(self.h, which, C.byref(h)))
+        return MPS(self.ctx, h) if h.value else None
+
+    def fractional_step(self, nsteps: int = 1, with_forces: bool = False):
+        return fractional_step(self.ctx, self, nsteps, with_forces)
+
+    def forces(self):
+        cd, cl = C.c_double(), C.c_double()
+        _check(lib().qtt_case_forces(self.ctx.h, self.h, C.byref(cd), C.byref(cl)))
+        return cd.value, cl.value
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                lib().qtt_case_free(self.h)
+            self.h = None
+        except Exception:
+            pass
+
+
+def fractional_step(ctx: Context, case: Case, nsteps: int = 1, with_forces: bool = False, info: bool = True):
+    """Advance ``nsteps`` fractional steps; returns per-step dicts (CG counts, C_D, C_L) or None."""
+    if not info:
+        _check(lib().fractional_step(ctx.h, case.h, nsteps, 0, None))
+        return None
+    recs = (qtt_step_info * max(nsteps, 1))()
+    _check(lib().fractional_step(ctx.h, case.h, nsteps, 1 if with_forces else 0, recs))
+    return [dict(cg_u=r.cg_u, cg_v=r.cg_v, cg_p=r.cg_p, cd=r.cd, cl=r.cl) for r in recs[:nsteps]]
+
+
+def qtt_strouhal(t, cl) -> float:
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.float64))
+    c = np.ascontiguousarray(np.asarray(cl, dtype=np.float64))
+    out = C.c_double()
+    _check(lib().qtt_strouhal(_dp(t), _dp(c), len(t), C.byref(out)))
+    return out.value

@@ -1,0 +1,137 @@
+"""GPU parity of the cylinder case (operators, boundary vectors), the fractional step and the
+forces against the FP64 oracle (L1 QTT step, L0 FD step), through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import fd, tt, qtt_ops as Q, step as S
+from paper_2507_05222_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2507_05222_gb300 import qtt
+    return qtt.Context(0)
+
+
+def rel(a, b):
+    a = np.asarray(a).ravel(); b = np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def make_state(ctx, ops, ne, nx, chi, seed=1, amp=1e-3):
+    from paper_2507_05222_gb300 import qtt
+    u0 = 1.0 + inputs.gaussian_field(ne, nx, seed, amp)
+    v0 = inputs.gaussian_field(ne, nx, seed + 1, amp)
+    u, v = ops.encode(u0, chi), ops.encode(v0, chi)
+    p = S.padded([np.zeros((1, 2, 1))] * (ne + nx), chi, inputs.random_cores(ne + nx, chi, seed + 2, scale=1e-8))
+    return (u, v, p), (qtt.MPS.from_cores(ctx, u), qtt.MPS.from_cores(ctx, v), qtt.MPS.from_cores(ctx, p)), (u0, v0)
+
+
+@pytest.mark.parametrize("ordering,ne,nx,rot", [("interleaved", 3, 3, 0.0), ("sequential", 3, 4, 0.7),
+                                               ("interleaved", 4, 3, 1.3)])
+def test_case_operators_and_vectors(ctx, ordering, ne, nx, rot):
+    """Sec. III.B.3 / App. A: every operator and boundary vector equals the oracle's."""
+    from paper_2507_05222_gb300 import qtt
+    R, Re, dt = 40.0, 100.0, 2e-3
+    case = qtt.Case(ctx, ne, nx, R, Re, dt, 8, ordering, rot=rot)
+    ops = Q.Ops(ne, nx, R, Re, dt, ordering, rot=rot)
+    ref_ops = [ops.Dx, ops.Dz, ops.Dxp, ops.Dzp, ops.H, ops.Ap, ops.Px, ops.Pz]
+    for w, M in enumerate(ref_ops):
+        g = case.operator(w).cores()
+        assert rel(tt.full_mpo(g), tt.full_mpo(M)) < 1e-13, w
+        assert max(tt.bonds(g)) <= max(tt.bonds(M)) + 2
+    ref_vec = [ops.bcx_u, ops.bcz_u, ops.bcx_v, ops.bcz_v, ops.JbcLap_u, ops.JbcLap_v, ops.bcdiv_w, ops.absJ]
+    for w, x in enumerate(ref_vec):
+        g = case.vector(w)
+        if x is None:
+            assert g is None, w
+        else:
+            assert rel(qtt.qtt_decode(ctx, g), tt.full(x)) < 1e-13, w
+
+
+@pytest.mark.parametrize("ordering,ne,nx,chi", [("interleaved", 3, 3, 8), ("sequential", 3, 3, 8),
+                                               ("interleaved", 4, 4, 8)])
+def test_one_step_matches_oracle(ctx, ordering, ne, nx, chi):
+    """Sec. III.C: one fractional step equals the oracle's L1 step (same algorithm)."""
+    from paper_2507_05222_gb300 import qtt
+    R, Re, dt = 40.0, 100.0, 2e-3
+    ops = Q.Ops(ne, nx, R, Re, dt, ordering)
+    (u, v, p), (gu, gv, gp), _ = make_state(ctx, ops, ne, nx, chi)
+    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, ordering, fit_sweeps=1, mom=(1, 8, 1e-12), poi=(2, 20, 1e-12))
+    case.set_state(gu, gv, gp)
+    info = case.fractional_step(1, with_forces=False)
+    o = S.StepOpts(chi=chi, fit_sweeps=1, mom_sweeps=1, mom_cg=8, poi_sweeps=2, poi_cg=20, cg_tol=1e-12)
+    un, vn, pn, oi = S.step(ops, u, v, p, o)
+    # CG stops on a relative-residual threshold; a last-digit difference may move a stop by one
+    assert abs(info[0]["cg_u"] - oi["cg_u"]) <= 2 and abs(info[0]["cg_v"] - oi["cg_v"]) <= 2
+    assert abs(info[0]["cg_p"] - oi["cg_p"]) <= 2
+    su, sv, sp = case.get_state()
+    for g, r in ((su, un), (sv, vn), (sp, pn)):
+        assert rel(qtt.qtt_decode(ctx, g), tt.full(r)) < TOL
+
+
+def test_full_rank_steps_match_fd(ctx):
+    """With chi at full rank and converged solves the GPU step equals the FD step (L0)."""
+    from paper_2507_05222_gb300 import qtt
+    ne = nx = 3
+    R, Re, dt, chi = 40.0, 100.0, 2e-3, 8
+    ops = Q.Ops(ne, nx, R, Re, dt, "interleaved")
+    _, (gu, gv, gp), (u0, v0) = make_state(ctx, ops, ne, nx, chi)
+    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=2, mom=(3, 100, 1e-15),
+                    poi=(6, 200, 1e-15))
+    case.set_state(gu, gv, gp)
+    L0 = fd.FDSolver(fd.Case(fd.Grid(ne, nx, R), Re, dt))
+    u, v = u0, v0
+    for _ in range(3):
+        case.fractional_step(1)
+        u, v, p, _, _ = L0.step(u, v)
+    su, sv, sp = case.get_state()
+    for g, r in ((su, u), (sv, v), (sp, p)):
+        r2 = Q.field_to_vec(np.reshape(r, (2 ** ne, 2 ** nx)), "interleaved")
+        assert rel(qtt.qtt_decode(ctx, g), r2) < 1e-10
+
+
+def test_forces_match_fd(ctx):
+    """App. F: C_D, C_L of the GPU state equal the FD diagnostics on the decoded fields."""
+    from paper_2507_05222_gb300 import qtt
+    ne, nx = 4, 5
+    R, Re, dt, chi = 40.0, 100.0, 2e-3, 16
+    ops = Q.Ops(ne, nx, R, Re, dt, "interleaved", rot=0.8)
+    _, (gu, gv, gp), _ = make_state(ctx, ops, ne, nx, chi, amp=1e-1)
+    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", rot=0.8)
+    case.set_state(gu, gv, gp)
+    cd, cl = case.forces()
+    su, sv, sp = case.get_state()
+    f = [Q.vec_to_field(qtt.qtt_decode(ctx, g), ne, nx, "interleaved") for g in (su, sv, sp)]
+    rcd, rcl = fd.forces(fd.Case(fd.Grid(ne, nx, R), Re, dt, rot=0.8), *f)
+    assert abs(cd - rcd) <= 1e-10 * max(1.0, abs(rcd))
+    assert abs(cl - rcl) <= 1e-10 * max(1.0, abs(rcl))
+
+
+def test_multi_step_truncated_parity(ctx):
+    """Several steps with active truncation (12 bits, chi = 16): GPU and oracle take the same
+    algorithmic path; the tolerance allows the growth of rounding-order differences through
+    truncated SVDs over five steps."""
+    from paper_2507_05222_gb300 import qtt
+    ne = nx = 6
+    R, Re, dt, chi = 40.0, 100.0, 2e-3, 16
+    ops = Q.Ops(ne, nx, R, Re, dt, "interleaved")
+    (u, v, p), (gu, gv, gp), _ = make_state(ctx, ops, ne, nx, chi)
+    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=1, mom=(1, 8, 1e-12), poi=(2, 20, 1e-12))
+    case.set_state(gu, gv, gp)
+    o = S.StepOpts(chi=chi, fit_sweeps=1, mom_sweeps=1, mom_cg=8, poi_sweeps=2, poi_cg=20, cg_tol=1e-12)
+    errs = []
+    for s in range(3):
+        case.fractional_step(1)
+        u, v, p, _ = S.step(ops, u, v, p, o)
+        su, sv, sp = case.get_state()
+        errs.append(max(rel(qtt.qtt_decode(ctx, su), tt.full(u)), rel(qtt.qtt_decode(ctx, sv), tt.full(v))))
+    print("per-step max rel diff:", errs)
+    assert errs[0] < 1e-9
+    assert max(errs) < 1e-7

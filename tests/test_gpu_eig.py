@@ -1,0 +1,63 @@
+"""The small symmetric eigensolver (FP32 Jacobi + FP64 refinement) against numpy on the
+spectra the Gram roundings meet: one dominant value over a flat tail, exact zeros from
+rank-deficient Gram matrices, clusters, and wide geometric decay."""
+import numpy as np
+import pytest
+
+from paper_2507_05222_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2507_05222_gb300 import qtt
+    return qtt.Context(0)
+
+
+def spectrum(kind, n, g):
+    if kind == "dominant_flat_tail":
+        lam = np.concatenate([[256.0], 1.6e-5 * (1 + 0.3 * g.random(n - 1))])
+    elif kind == "zeros":
+        lam = np.concatenate([np.sort(g.random(n // 4))[::-1] * 10, 1.6e-5 * g.random(n // 4), np.zeros(n - 2 * (n // 4))])
+    elif kind == "geometric":
+        lam = 10.0 ** (-np.linspace(0, 15, n))
+    elif kind == "cluster":
+        lam = np.concatenate([np.ones(n // 2), 1 + 1e-9 * g.random(n // 4), 0.5 * np.ones(n - n // 2 - n // 4)])
+    else:
+        lam = g.standard_normal(n)
+    return lam
+
+
+@pytest.mark.parametrize("kind", ["dominant_flat_tail", "zeros", "geometric", "cluster", "random"])
+@pytest.mark.parametrize("n", [16, 64, 128])
+def test_sym_eig(ctx, kind, n):
+    from paper_2507_05222_gb300 import qtt
+    g = inputs.rng(n + len(kind))
+    Qm, _ = np.linalg.qr(g.standard_normal((n, n)))
+    lam = spectrum(kind, n, g)
+    S = (Qm * lam) @ Qm.T
+    S = 0.5 * (S + S.T)
+    w, V = qtt.qtt_sym_eig(ctx, S)
+    wr, Vr = np.linalg.eigh(S)
+    wr, Vr = wr[::-1], Vr[:, ::-1]
+    scale = np.abs(wr).max()
+    # bounds from the arithmetic: FP64 products of length n accumulate ~n eps ||S||
+    if kind == "cluster":
+        sep = np.abs(wr - 1.0) > 1e-6               # outside the 1e-9-wide cluster at 1
+        assert np.abs(w - wr)[sep].max() <= 1e-12 * scale
+        assert abs(w[~sep].mean() - wr[~sep].mean()) <= 1e-12 * scale
+    else:
+        assert np.abs(w - wr).max() <= 1e-12 * scale
+    assert np.abs(V.T @ V - np.eye(n)).max() < 1e-12
+    if kind == "cluster":
+        # eigenvectors inside a cluster of width 1e-9 are not individually determined; the
+        # invariant subspace of the separated group (the quantity a truncation uses) is
+        k = n // 2 + n // 4
+        P, Pr = V[:, :k] @ V[:, :k].T, Vr[:, :k] @ Vr[:, :k].T
+        assert np.abs(P - Pr).max() < 1e-12
+    else:
+        assert np.abs(S @ V - V * w).max() <= 1e-11 * scale

@@ -1,0 +1,200 @@
+"""GPU parity of the TT operations (C ABI) against the FP64 oracle, element by element on
+reconstructed vectors.  Tolerance: relative 1e-10 in FP64 (the figure the hot path is held
+to); cases are chosen so that no truncation falls inside a near-degenerate singular-value
+pair (where the TT-SVD itself is not unique)."""
+import numpy as np
+import pytest
+
+from oracle import tt, qtt_ops as Q
+from paper_2507_05222_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2507_05222_gb300 import qtt
+    return qtt.Context(0)
+
+
+def rel(a, b):
+    a = np.asarray(a).ravel(); b = np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def up(ctx, cores):
+    from paper_2507_05222_gb300 import qtt
+    return qtt.MPS.from_cores(ctx, cores)
+
+
+def down(ctx, x):
+    from paper_2507_05222_gb300 import qtt
+    return qtt.qtt_decode(ctx, x)
+
+
+def test_mps_roundtrip_and_decode(ctx):
+    x = inputs.random_cores(7, 5, seed=1)
+    g = up(ctx, x)
+    back = g.cores()
+    for a, b in zip(back, x):
+        assert np.array_equal(a, b)
+    assert rel(down(ctx, g), tt.full(x)) < 1e-14
+
+
+@pytest.mark.parametrize("n,chi", [(10, 32), (10, 7), (11, 4), (1, 1), (2, 1)])
+def test_encode(ctx, n, chi):
+    from paper_2507_05222_gb300 import qtt
+    v = inputs.dense_vector(n, seed=n + chi)
+    ref = tt.tt_svd(v, n, 2, chi)
+    g = qtt.qtt_encode(ctx, v, n, chi)
+    assert g.bonds() == tt.bonds(ref)
+    assert rel(down(ctx, g), tt.full(ref)) < TOL
+
+
+def test_encode_smooth_field_low_rank(ctx):
+    """Rank-2 trig field encodes to rank 2 under a threshold (Sec. III.B.1)."""
+    from paper_2507_05222_gb300 import qtt
+    n = 12
+    q = np.arange(2 ** n)
+    f = np.sin(2 * np.pi * q / 2 ** n * 3 + 0.2)
+    g = qtt.qtt_encode(ctx, f, n, 64, rel_tol=1e-10)
+    assert max(g.bonds()) == 2
+    assert rel(down(ctx, g), f) < 1e-12
+
+
+@pytest.mark.parametrize("n,bond,chi", [(10, 12, 5), (9, 16, 16), (8, 6, 3), (12, 10, 8)])
+def test_round(ctx, n, bond, chi):
+    from paper_2507_05222_gb300 import qtt
+    x = inputs.random_cores(n, bond, seed=3 * n + bond)
+    ref = tt.round_tt(x, chi)
+    g = qtt.qtt_round(ctx, up(ctx, x), chi)
+    assert g.bonds() == tt.bonds(ref)
+    assert rel(down(ctx, g), tt.full(ref)) < TOL
+    # right-canonical output (Sec. II); the eigenvectors of the tiniest Gram eigenvalues are
+    # orthonormal to ~1e-11 after refinement
+    for c in g.cores()[1:]:
+        m = c.reshape(c.shape[0], -1)
+        assert np.abs(m @ m.T - np.eye(c.shape[0])).max() < 1e-10
+
+
+def test_round_eps_threshold(ctx):
+    from paper_2507_05222_gb300 import qtt
+    a = Q.mps1_trig(9, 0.1, 0.0, "sin"); b = Q.mps1_trig(9, 0.1, 0.3, "cos")
+    s = tt.direct_sum(1.0, a, 2.0, b)
+    g = qtt.qtt_round(ctx, up(ctx, s), 100, rel_tol=1e-14)
+    assert max(g.bonds()) == 2
+    assert rel(down(ctx, g), tt.full(s)) < 1e-13
+
+
+@pytest.mark.parametrize("n,ba,bb,chi", [(10, 8, 6, 8), (9, 4, 4, 16), (12, 10, 9, 6)])
+def test_axpby(ctx, n, ba, bb, chi):
+    from paper_2507_05222_gb300 import qtt
+    x = inputs.random_cores(n, ba, seed=10 + n); y = inputs.random_cores(n, bb, seed=20 + n)
+    ref = tt.round_tt(tt.direct_sum(0.7, x, -1.3, y), chi)
+    g = qtt.mps_axpby_round(ctx, 0.7, up(ctx, x), -1.3, up(ctx, y), chi)
+    assert g.bonds() == tt.bonds(ref)
+    assert rel(down(ctx, g), tt.full(ref)) < TOL
+
+
+@pytest.mark.parametrize("n,bx,w,chi", [(9, 6, 3, 6), (10, 8, 4, 32), (8, 5, 2, 4)])
+def test_apply_random(ctx, n, bx, w, chi):
+    from paper_2507_05222_gb300 import qtt
+    x = inputs.random_cores(n, bx, seed=30 + n)
+    M = inputs.random_mpo_cores(n, w, seed=40 + n)
+    ref = tt.round_tt(tt.mpo_mps(M, x), chi)
+    g = qtt.mpo_apply_round(ctx, qtt.MPO.from_cores(ctx, M), up(ctx, x), chi)
+    assert g.bonds() == tt.bonds(ref)
+    assert rel(down(ctx, g), tt.full(ref)) < TOL
+
+
+@pytest.mark.parametrize("ordering", ["interleaved", "sequential"])
+def test_apply_fd_operator_exact(ctx, ordering):
+    """Curvilinear D_x of a smooth field without truncation equals the dense product."""
+    from paper_2507_05222_gb300 import qtt
+    ne, nx = 4, 5
+    ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, ordering)
+    f = inputs.gaussian_field(ne, nx, 5, 1.0)
+    x = ops.encode(f, 64)
+    g = qtt.mpo_apply_round(ctx, qtt.MPO.from_cores(ctx, ops.Dx), up(ctx, x), 512)
+    assert rel(down(ctx, g), tt.full_mpo(ops.Dx) @ tt.full(x)) < TOL
+
+
+@pytest.mark.parametrize("n,ba,bb,chi", [(8, 4, 3, 6), (10, 5, 5, 8)])
+def test_hadamard_fit(ctx, n, ba, bb, chi):
+    from paper_2507_05222_gb300 import qtt
+    a = inputs.random_cores(n, ba, seed=50 + n); b = inputs.random_cores(n, bb, seed=60 + n)
+    ref = tt.hadamard_round(a, b, chi, sweeps=2)
+    g = qtt.mps_hadamard_round(ctx, up(ctx, a), up(ctx, b), chi, sweeps=2)
+    assert g.bonds() == tt.bonds(ref)
+    assert rel(down(ctx, g), tt.full(ref)) < TOL
+
+
+def test_hadamard_exact_low_rank(ctx):
+    """sin (.) exp has rank 2: the fit reproduces the pointwise product (Sec. II.A.3)."""
+    from paper_2507_05222_gb300 import qtt
+    n = 11
+    a = Q.mps1_trig(n, 0.013, 0.3, "sin"); b = Q.mps1_exp(n, 1.0, 0.001)
+    g = qtt.mps_hadamard_round(ctx, up(ctx, a), up(ctx, b), 4, sweeps=2)
+    assert rel(down(ctx, g), tt.full(a) * tt.full(b)) < 1e-12
+
+
+def test_dot(ctx):
+    from paper_2507_05222_gb300 import qtt
+    a = inputs.random_cores(11, 7, seed=70); b = inputs.random_cores(11, 5, seed=71)
+    v = qtt.mps_dot(ctx, up(ctx, a), up(ctx, b))
+    ref = float(tt.full(a) @ tt.full(b))
+    assert abs(v - ref) <= 1e-12 * np.linalg.norm(tt.full(a)) * np.linalg.norm(tt.full(b))
+
+
+def test_poisson_solve_matches_oracle_als(ctx):
+    """ALS (Sec. II.A.4) with the same sweeps / CG budget as the oracle."""
+    from paper_2507_05222_gb300 import qtt
+    ne, nx = 4, 4
+    ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, "interleaved")
+    n = ne + nx
+    b = inputs.random_cores(n, 4, seed=80)
+    x0 = inputs.random_cores(n, 8, seed=81, scale=0.1)
+    ref, cg_ref = tt.als(ops.Ap, [("vec", 1.0, b)], x0, sweeps=2, cg_iters=15, cg_tol=1e-12)
+    g = up(ctx, x0)
+    cg, res = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.Ap), up(ctx, b), g, 2, 15, 1e-12)
+    assert cg == cg_ref
+    assert rel(down(ctx, g), tt.full(ref)) < 1e-9
+
+
+def test_poisson_solve_full_rank_exact(ctx):
+    """At full bond dimension the ALS solution equals the dense solve (J-weighted Poisson)."""
+    from paper_2507_05222_gb300 import qtt
+    ne, nx = 3, 4
+    ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, "interleaved")
+    n = ne + nx
+    b = inputs.random_cores(n, 4, seed=82)
+    x0 = inputs.random_cores(n, 16, seed=83, scale=0.1)
+    g = up(ctx, x0)
+    cg, res = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.Ap), up(ctx, b), g, 6, 300, 1e-15)
+    ref = np.linalg.solve(tt.full_mpo(ops.Ap), tt.full(b))
+    assert rel(down(ctx, g), ref) < 1e-10
+    assert res < 1e-10
+
+
+def test_field_reorder(ctx):
+    from paper_2507_05222_gb300 import qtt
+    f = np.arange(8 * 32, dtype=float).reshape(8, 32)
+    for o in ("sequential", "interleaved"):
+        v = qtt.qtt_field_to_vector(ctx, f, o)
+        assert np.array_equal(v, Q.field_to_vec(f, o))
+        assert np.array_equal(qtt.qtt_vector_to_field(ctx, v, 3, 5, o), f)
+
+
+def test_argument_errors(ctx):
+    from paper_2507_05222_gb300 import qtt
+    x = up(ctx, inputs.random_cores(6, 3, seed=1))
+    y = up(ctx, inputs.random_cores(7, 3, seed=2))
+    with pytest.raises(qtt.QttError) as e:
+        qtt.mps_axpby_round(ctx, 1.0, x, 1.0, y, 4)
+    assert e.value.code == -1
+    with pytest.raises(qtt.QttError):
+        qtt.qtt_round(ctx, x, 0)
