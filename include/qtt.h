@@ -107,6 +107,12 @@ const char* qtt_last_error(void);
 int64_t qtt_ctx_kernel_launches(qtt_ctx* ctx);
 /* Bytes currently held by the context's device pool (in use + cached). */
 size_t qtt_ctx_pool_bytes(qtt_ctx* ctx);
+/* Per-kernel-class timing.  Synchronises the stream, then writes, for classes 0 FP64 GEMM,
+ * 1 Householder QR, 2 Jacobi eigensolver, 3 CG update, 4 other, the summed CUDA-event time
+ * (ms), the algorithmic flops and the launch count recorded since the previous call (each
+ * array of 5, any may be NULL), resets them, and turns event recording on (on != 0) or off.
+ * Events are recorded on the context stream around each launch of a timed class. */
+int qtt_ctx_profile(qtt_ctx* ctx, int on, double* ms_out, double* flops_out, int64_t* launches_out);
 
 /* ------------------------------------------------------------------------ MPS and MPO */
 

@@ -872,6 +872,7 @@ int als(Ctx& c, const qtt_mpo* A, const std::vector<Term>& rhs, qtt_mps* x, int 
       c.guard = active;
       local_target(c, opT, LA[k].p, RA[k + 1].p, r0, r1, k, 1.0, 0.0, Ap.p, p.p);
       c.guard = nullptr;
+      ProfScope ps(c, KC_CG);
       k_cg_update<<<1, 1024, 0, c.stream>>>(nel, xk.p, r.p, p.p, Ap.p, st);
       after_launch(c, "cg_update");
     }

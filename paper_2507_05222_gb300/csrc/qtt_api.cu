@@ -126,6 +126,12 @@ void qtt_ctx_destroy(qtt_ctx* ctx) {
   if (!ctx) return;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   cudaStreamSynchronize(c->stream);
+  for (auto e : c->prof.free_events) cudaEventDestroy(e);
+  for (int k = 0; k < KC_N; ++k)
+    for (auto& pr : c->prof.pending[k]) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
   delete c->pool;
   delete c;
 }
@@ -142,6 +148,31 @@ const char* qtt_last_error(void) { return g_last_error.c_str(); }
 int64_t qtt_ctx_kernel_launches(qtt_ctx* ctx) { return ctx ? reinterpret_cast<Ctx*>(ctx)->launches : 0; }
 
 size_t qtt_ctx_pool_bytes(qtt_ctx* ctx) { return ctx ? reinterpret_cast<Ctx*>(ctx)->pool->held() : 0; }
+
+int qtt_ctx_profile(qtt_ctx* ctx, int on, double* ms_out, double* flops_out, int64_t* launches_out) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx, "ctx is null");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  for (int k = 0; k < KC_N; ++k) {
+    double ms = 0.0;
+    for (auto& pr : c.prof.pending[k]) {
+      float t = 0.f;
+      QTT_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+      ms += t;
+      c.prof.free_events.push_back(pr.first);
+      c.prof.free_events.push_back(pr.second);
+    }
+    c.prof.pending[k].clear();
+    if (ms_out) ms_out[k] = ms;
+    if (flops_out) flops_out[k] = c.prof.flops[k];
+    if (launches_out) launches_out[k] = c.prof.launches[k];
+    c.prof.flops[k] = 0.0;
+    c.prof.launches[k] = 0;
+  }
+  c.prof.on = on != 0;
+  API_END
+}
 
 // ------------------------------------------------------------------ MPS / MPO
 

@@ -96,6 +96,32 @@ void after_launch(Ctx& c, const char* what) {
   if (e != cudaSuccess) throw Error(QTT_ERR_CUDA, std::string("launch of ") + what + ": " + cudaGetErrorString(e));
 }
 
+static cudaEvent_t take_event(Ctx& c) {
+  if (!c.prof.free_events.empty()) {
+    cudaEvent_t e = c.prof.free_events.back();
+    c.prof.free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  QTT_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+ProfScope::ProfScope(Ctx& ctx, int kclass, double flops) : c(ctx), k(kclass) {
+  if (!c.prof.on) return;
+  c.prof.flops[k] += flops;
+  c.prof.launches[k] += 1;
+  e0 = take_event(c);
+  cudaEventRecord(e0, c.stream);
+}
+
+ProfScope::~ProfScope() {
+  if (!e0) return;
+  cudaEvent_t e1 = take_event(c);
+  cudaEventRecord(e1, c.stream);
+  c.prof.pending[k].push_back({e0, e1});
+}
+
 TV tv(double* p, std::initializer_list<int64_t> dims) {
   TV t;
   t.p = p;
@@ -229,6 +255,7 @@ void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, 
   int64_t kchunk = (K + splits - 1) / splits;
   kchunk = (kchunk + GK - 1) / GK * GK;
   splits = int((K + kchunk - 1) / kchunk);
+  ProfScope ps(c, KC_GEMM, 2.0 * double(batch) * double(M) * double(N) * double(K));
   dim3 grid(unsigned((N + GT - 1) / GT), unsigned((M + GT - 1) / GT), unsigned(batch * splits));
   QTT_CHECK_ARG(grid.y <= 65535 && grid.z <= 65535, "gemm grid too large");
   dim3 block(16, 16);

@@ -78,6 +78,17 @@ struct DBuf {
   void reset(Ctx* c, size_t count);
 };
 
+// Kernel classes for the optional per-class timing (CUDA events around each launch).
+enum KClass { KC_GEMM = 0, KC_QR = 1, KC_EIG = 2, KC_CG = 3, KC_OTHER = 4, KC_N = 5 };
+
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> free_events;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[KC_N];
+  double flops[KC_N] = {0};
+  int64_t launches[KC_N] = {0};
+};
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -88,9 +99,19 @@ struct Ctx {
   // if it is 0.  Set around the matrix-vector products of a CG solve so that iterations past
   // convergence cost only their launches (the iteration budget is fixed on the host).
   const int* guard = nullptr;
+  Profiler prof;
 };
 
 void after_launch(Ctx& c, const char* what);
+
+// RAII bracket of one launch (or launch group) of class k when profiling is on.
+struct ProfScope {
+  Ctx& c;
+  int k;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(Ctx& ctx, int kclass, double flops = 0.0);
+  ~ProfScope();
+};
 
 // ------------------------------------------------------------------ handles
 

@@ -424,6 +424,8 @@ void qr(Ctx& c, int count, int m, int n, int trans, const double* A, int64_t in_
     QTT_CUDA(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     attr = true;
   }
+  int kk = std::min(m, n);
+  ProfScope ps(c, KC_QR, double(count) * 8.0 * (double(m) * n * kk - 0.5 * (double(m) + n) * kk * kk + kk * kk * kk / 3.0));
   k_qr<<<count, 256, sm, c.stream>>>(m, n, trans, A, Q, R, in_stride, q_stride, r_stride);
   after_launch(c, "qr");
 }
@@ -474,8 +476,11 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
       an(&c, 1), flags(&c, 2);
   int* t0 = reinterpret_cast<int*>(flags.p);
   int* need = t0 + 1;
-  k_jacobi_f32<<<1, 1024, smf, c.stream>>>(n, S, X.p, 12, nullptr);
-  after_launch(c, "jacobi_f32");
+  {
+    ProfScope ps(c, KC_EIG);
+    k_jacobi_f32<<<1, 1024, smf, c.stream>>>(n, S, X.p, 12, nullptr);
+    after_launch(c, "jacobi_f32");
+  }
   k_frob<<<1, 1024, 0, c.stream>>>(int64_t(n) * n, S, an.p);
   after_launch(c, "frob");
   const double taus[3] = {0.0, 1e-5, 1e-10};
@@ -487,8 +492,11 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
       gemm(c, 1, n, n, n, 1.0, S, 0, n, 1, X.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
       gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, AX.p, 0, n, 1, 0.0, SX.p, 0, n, 1);
       c.guard = nullptr;
-      k_jacobi_f32<<<1, 1024, smf, c.stream>>>(n, SX.p, Y.p, 12, t0);
-      after_launch(c, "jacobi_f32_tail");
+      {
+        ProfScope ps(c, KC_EIG);
+        k_jacobi_f32<<<1, 1024, smf, c.stream>>>(n, SX.p, Y.p, 12, t0);
+        after_launch(c, "jacobi_f32_tail");
+      }
       c.guard = need;
       gemm(c, 1, n, n, n, 1.0, X.p, 0, n, 1, Y.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
       copy_guarded(c, X.p, AX.p, int64_t(nn), need);

@@ -75,6 +75,7 @@ _SIGS = {
     "qtt_last_error": (C.c_char_p, []),
     "qtt_ctx_kernel_launches": (L, [P]),
     "qtt_ctx_pool_bytes": (S, [P]),
+    "qtt_ctx_profile": (I, [P, I, DP, DP, C.POINTER(C.c_int64)]),
     "qtt_mps_create": (I, [P, I, I, IP, DP, I, C.POINTER(P)]),
     "qtt_mps_free": (I, [P]),
     "qtt_mps_n": (I, [P]),
@@ -184,6 +185,16 @@ class Context:
     def pool_bytes(self) -> int:
         return int(lib().qtt_ctx_pool_bytes(self.h))
 
+    PROFILE_CLASSES = ("gemm_f64", "qr_f64", "eig_jacobi", "cg_update", "other")
+
+    def profile(self, on: bool):
+        """Read and reset the per-class kernel timing; switch recording on/off."""
+        ms = np.zeros(5); fl = np.zeros(5); n = np.zeros(5, dtype=np.int64)
+        _check(lib().qtt_ctx_profile(self.h, 1 if on else 0, _dp(ms), _dp(fl),
+                                     n.ctypes.data_as(C.POINTER(C.c_int64))))
+        return {k: dict(ms=float(ms[i]), flops=float(fl[i]), launches=int(n[i]))
+                for i, k in enumerate(self.PROFILE_CLASSES)}
+
     def close(self):
         if getattr(self, "h", None):
             lib().qtt_ctx_destroy(self.h)
@@ -211,6 +222,20 @@ class MPS:
         h = P()
         _check(lib().qtt_mps_create(ctx.h, n, d, bonds.ctypes.data_as(IP), _dp(flat), QTT_HOST, C.byref(h)))
         return cls(ctx, h)
+
+    @classmethod
+    def from_flat(cls, ctx: Context, bonds, d: int, flat_ptr: int) -> "MPS":
+        """New MPS whose cores are copied from host memory at ``flat_ptr`` (all cores
+        concatenated, float64; may be pinned memory) -- no intermediate host copy."""
+        b = np.asarray(bonds, dtype=np.int32)
+        h = P()
+        _check(lib().qtt_mps_create(ctx.h, len(b) - 1, d, b.ctypes.data_as(IP), C.cast(flat_ptr, DP), QTT_HOST,
+                                    C.byref(h)))
+        return cls(ctx, h)
+
+    def get_flat(self, flat_ptr: int):
+        """Copy all cores (concatenated) into host memory at ``flat_ptr``."""
+        _check(lib().qtt_mps_get_cores(self.h, C.cast(flat_ptr, DP), QTT_HOST))
 
     @property
     def n(self) -> int:
