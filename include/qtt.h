@@ -170,6 +170,26 @@ int mpo_apply_round(qtt_ctx* ctx, const qtt_mpo* M, const qtt_mps* x, qtt_trunc 
  * then `sweeps` fit sweeps. */
 int mps_hadamard_round(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, qtt_trunc tr,
                        const qtt_mps* init, int sweeps, qtt_mps** out, qtt_round_info* info);
+/* <a, b> without any device memory allocation (the paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need an overlap -- code
+ * running inside another allocator's callback, loops that cannot afford a cudaMalloc that may
+ * synchronise the device, or processes whose device memory is fully reserved by another pool).
+ *   n, d       number of cores and physical size (1 <= d <= 4)
+ *   a_bonds, b_bonds   host arrays of n+1 bonds, each in [1, 128], first and last equal to 1
+ *   a_cores, b_cores   device arrays: all cores concatenated, each (r_{k-1}, d, r_k) row-major,
+ *                      no padding between cores (caller-owned, read only)
+ *   out_dev    device pointer receiving the overlap (one double, caller-owned)
+ *   cuda_stream  stream (cudaStream_t) the work is enqueued on; the call returns without
+ *                waiting for it
+ * Intermediates live in one fixed 768 KiB array of device memory compiled into the library,
+ * held by every device that loads the library until the process exits.  Bonds above 128 or
+ * d > 4 return QTT_ERR_UNSUPPORTED.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents: calls that overlap on the GPU (other
+ * streams or host threads) race and must be serialised by the caller.  No context is used and
+ * nothing is allocated: not by cudaMalloc, not by the context pool, not by any library. */
+int mps_dot_noalloc(int n, int d, const int* a_bonds, const double* a_cores, const int* b_bonds,
+                    const double* b_cores, double* out_dev, void* cuda_stream);
 /* Symmetric eigendecomposition of a small dense matrix (n <= 160), the building block of every
  * Gram-based rounding: FP32 Jacobi sweeps refined to FP64 accuracy.  S (n x n row-major,
  * symmetric), w (n, descending) and V (n x n row-major, eigenvectors as columns) are host

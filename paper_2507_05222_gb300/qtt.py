@@ -98,6 +98,7 @@ _SIGS = {
     "mps_hadamard_round": (I, [P, P, P, qtt_trunc, P, I, C.POINTER(P), C.POINTER(qtt_round_info)]),
     "mps_dot": (I, [P, P, P, DP]),
     "qtt_sym_eig": (I, [P, I, DP, DP, DP]),
+    "mps_dot_noalloc": (I, [I, I, IP, P, IP, P, P, P]),
     "poisson_solve": (I, [P, P, P, P, C.POINTER(qtt_solve_opts), D, C.POINTER(qtt_solve_info)]),
     "qtt_case_create": (I, [P, C.POINTER(qtt_case_params), C.POINTER(P)]),
     "qtt_case_free": (I, [P]),
@@ -378,6 +379,16 @@ def mps_hadamard_round(ctx: Context, a: MPS, b: MPS, chi: int, sweeps: int = 2, 
     _check(lib().mps_hadamard_round(ctx.h, a.h, b.h, _trunc(chi, 0.0), init.h if init is not None else None,
                                     sweeps, C.byref(h), None))
     return MPS(ctx, h)
+
+
+def mps_dot_noalloc(n: int, d: int, a_bonds, a_cores_dev: int, b_bonds, b_cores_dev: int, out_dev: int,
+                    stream: int = 0):
+    """<a, b> into the device double at ``out_dev`` without allocating device memory; cores are
+    given as device pointers to unpadded concatenated cores (see include/qtt.h)."""
+    ab = np.ascontiguousarray(np.asarray(a_bonds, dtype=np.int32))
+    bb = np.ascontiguousarray(np.asarray(b_bonds, dtype=np.int32))
+    _check(lib().mps_dot_noalloc(n, d, ab.ctypes.data_as(IP), a_cores_dev, bb.ctypes.data_as(IP), b_cores_dev,
+                                 out_dev, stream))
 
 
 def qtt_sym_eig(ctx: Context, S):
