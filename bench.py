@@ -147,6 +147,14 @@ def run_ours(args, cfg):
     gv = qtt.qtt_encode(ctx, qtt.qtt_field_to_vector(ctx, v0, cfg["ordering"]), ne + nx, chi)
     gp = qtt.MPS.from_cores(ctx, pad)
     case.set_state(gu, gv, gp)
+    if args.profile_one_step:
+        qtt.fractional_step(ctx, case, 1, info=False)
+        ctx.sync()
+        qtt.profiler_range(True)
+        qtt.fractional_step(ctx, case, 1, info=False)
+        ctx.sync()
+        qtt.profiler_range(False)
+        return
     flush = torch.empty(int(256 * 2 ** 20 // 4), dtype=torch.float32, device="cuda")  # 256 MB > L2 (129 MB)
     stream = ctx.stream
     for _ in range(args.warmup):
@@ -239,6 +247,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="bits per direction (smaller test case)")
     ap.add_argument("--chi", type=int, default=None)
+    ap.add_argument("--profile-one-step", action="store_true",
+                    help="set up, one warm-up step, then one step between cudaProfilerStart/Stop (for ncu)")
     args = ap.parse_args()
     cfg = dict(WORKLOAD)
     if args.n is not None:

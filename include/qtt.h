@@ -103,15 +103,20 @@ void qtt_ctx_destroy(qtt_ctx* ctx);
 int qtt_ctx_sync(qtt_ctx* ctx);
 /* Message of the last error on the calling thread ("" if none). */
 const char* qtt_last_error(void);
+/* cudaProfilerStart (start != 0) or cudaProfilerStop: brackets the launches an external
+ * profiler started with profiling off captures. */
+int qtt_profiler_range(int start);
 /* Number of kernels this context has launched so far (all entry points). */
 int64_t qtt_ctx_kernel_launches(qtt_ctx* ctx);
 /* Bytes currently held by the context's device pool (in use + cached). */
 size_t qtt_ctx_pool_bytes(qtt_ctx* ctx);
 /* Per-kernel-class timing.  Synchronises the stream, then writes, for classes 0 FP64 GEMM,
- * 1 Householder QR, 2 Jacobi eigensolver, 3 CG update, 4 other, the summed CUDA-event time
- * (ms), the algorithmic flops and the launch count recorded since the previous call (each
- * array of 5, any may be NULL), resets them, and turns event recording on (on != 0) or off.
- * Events are recorded on the context stream around each launch of a timed class. */
+ * 1 Householder QR, 2 Jacobi eigensolver, 3 CG update, 4 other, and the phases of
+ * fractional_step 5 MPO-MPS products, 6 right-hand-side fits, 7 momentum solves, 8 Poisson
+ * solve, 9 projection fits, the summed CUDA-event time (ms), the algorithmic flops and the
+ * launch count recorded since the previous call (each array of 10, any may be NULL), resets
+ * them, and turns event recording on (on != 0) or off.  Events are recorded on the context
+ * stream around each launch (or phase) of a timed class. */
 int qtt_ctx_profile(qtt_ctx* ctx, int on, double* ms_out, double* flops_out, int64_t* launches_out);
 
 /* ------------------------------------------------------------------------ MPS and MPO */

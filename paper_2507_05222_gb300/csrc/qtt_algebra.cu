@@ -104,12 +104,19 @@ __global__ void k_diag_core(const double* __restrict__ A, int r0, int d, int r1,
   }
 }
 
-// Single-block fused CG update (Sec. II.A.4 local solve).  State: [0] rr, [1] bb, [2] tol^2,
-// [3] active flag (as int in a double slot), [4] iteration count.
+// CG for the ALS local systems (Sec. II.A.4), spread over CG_BLOCKS blocks.  State lives on
+// the device so that the host never waits: rr is kept in two slots (iteration `it` reads
+// slot it & 1 and writes slot (it + 1) & 1) because blocks of one kernel are not ordered with
+// respect to each other.  Partial sums are reduced in a fixed order (deterministic results).
+constexpr int CG_BLOCKS = 32;
+constexpr int CG_THREADS = 256;
+
 struct CGState {
-  double rr, bb, tol2;
+  double rr[2];
+  double bb, tol2;
   int active;
   int count;
+  double part[2][CG_BLOCKS];   // per-block partial sums
 };
 
 __device__ double block_sum_d(double v, double* red) {
@@ -124,13 +131,19 @@ __device__ double block_sum_d(double v, double* red) {
   return s;
 }
 
-// r = b - Ax (Ax given), p = r, rr = r.r, bb = b.b, active = rr > tol^2 bb and rr > 0.
-__global__ void __launch_bounds__(1024) k_cg_init(int64_t n, const double* __restrict__ b, const double* __restrict__ Ax,
-                                                  double* __restrict__ r, double* __restrict__ p, CGState* st,
-                                                  double tol2) {
+__device__ __forceinline__ double sum_parts(const double* part) {
+  double s = 0.0;
+  for (int i = 0; i < CG_BLOCKS; ++i) s += part[i];
+  return s;
+}
+
+// r = b - Ax, p = r; partial r.r and b.b per block.
+__global__ void __launch_bounds__(CG_THREADS) k_cg_init1(int64_t n, const double* __restrict__ b,
+                                                         const double* __restrict__ Ax, double* __restrict__ r,
+                                                         double* __restrict__ p, CGState* st) {
   __shared__ double red[32];
   double rr = 0, bb = 0;
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
     double re = b[e] - Ax[e];
     r[e] = re;
     p[e] = re;
@@ -140,44 +153,66 @@ __global__ void __launch_bounds__(1024) k_cg_init(int64_t n, const double* __res
   rr = block_sum_d(rr, red);
   bb = block_sum_d(bb, red);
   if (threadIdx.x == 0) {
-    st->rr = rr;
-    st->bb = bb;
-    st->tol2 = tol2;
-    st->active = (rr > tol2 * bb && rr > 0.0) ? 1 : 0;
-    st->count = 0;
+    st->part[0][blockIdx.x] = rr;
+    st->part[1][blockIdx.x] = bb;
   }
 }
 
-// One CG iteration after Ap = A p: alpha = rr / pAp, x += alpha p, r -= alpha Ap,
-// beta = rr'/rr, p = r + beta p; then the stopping test.
-__global__ void __launch_bounds__(1024) k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
-                                                    double* __restrict__ p, const double* __restrict__ Ap,
-                                                    CGState* st) {
+__global__ void k_cg_init2(CGState* st, double tol2) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double rr = sum_parts(st->part[0]), bb = sum_parts(st->part[1]);
+  st->rr[0] = rr;
+  st->bb = bb;
+  st->tol2 = tol2;
+  st->active = (rr > tol2 * bb && rr > 0.0) ? 1 : 0;
+  st->count = 0;
+}
+
+// partial p.Ap
+__global__ void __launch_bounds__(CG_THREADS) k_cg_pap(int64_t n, const double* __restrict__ p,
+                                                       const double* __restrict__ Ap, CGState* st) {
   __shared__ double red[32];
   if (!st->active) return;
-  double pap = 0;
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) pap += p[e] * Ap[e];
-  pap = block_sum_d(pap, red);
-  const double rr = st->rr;
-  if (!(pap > 0.0)) {
-    __syncthreads();
-    if (threadIdx.x == 0) st->active = 0;
+  double s = 0;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    s += p[e] * Ap[e];
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) st->part[0][blockIdx.x] = s;
+}
+
+// alpha = rr / pAp; x += alpha p; r -= alpha Ap; partial r.r
+__global__ void __launch_bounds__(CG_THREADS) k_cg_xr(int64_t n, int it, double* __restrict__ x, double* __restrict__ r,
+                                                      const double* __restrict__ p, const double* __restrict__ Ap,
+                                                      CGState* st) {
+  __shared__ double red[32];
+  if (!st->active) return;
+  const double pap = sum_parts(st->part[0]);
+  if (!(pap > 0.0)) {                    // every block computes the same pap and stops here
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->active = 0;
     return;
   }
-  const double alpha = rr / pap;
+  const double alpha = st->rr[it & 1] / pap;
   double rn = 0;
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
     x[e] += alpha * p[e];
     double re = r[e] - alpha * Ap[e];
     r[e] = re;
     rn += re * re;
   }
   rn = block_sum_d(rn, red);
-  const double beta = rn / rr;
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) p[e] = r[e] + beta * p[e];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    st->rr = rn;
+  if (threadIdx.x == 0) st->part[1][blockIdx.x] = rn;
+}
+
+// beta = rr' / rr; p = r + beta p; block 0 records rr', the count and the stopping test.
+__global__ void __launch_bounds__(CG_THREADS) k_cg_p(int64_t n, int it, const double* __restrict__ r,
+                                                     double* __restrict__ p, CGState* st) {
+  if (!st->active) return;
+  const double rn = sum_parts(st->part[1]);
+  const double beta = rn / st->rr[it & 1];
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    p[e] = r[e] + beta * p[e];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->rr[(it + 1) & 1] = rn;
     st->count += 1;
     st->active = (rn > st->tol2 * st->bb && rn > 0.0) ? 1 : 0;
   }
@@ -852,7 +887,7 @@ int als(Ctx& c, const qtt_mpo* A, const std::vector<Term>& rhs, qtt_mps* x, int 
   }
   Envs E;
   init_envs(c, rhs, x, E);
-  DBuf stbuf(&c, 8);
+  DBuf stbuf(&c, (sizeof(CGState) + 7) / 8);
   CGState* st = reinterpret_cast<CGState*>(stbuf.p);
   DBuf tot(&c, 1);
   k_set_int<<<1, 1, 0, c.stream>>>(reinterpret_cast<int*>(tot.p), 0);
@@ -866,15 +901,21 @@ int als(Ctx& c, const qtt_mpo* A, const std::vector<Term>& rhs, qtt_mps* x, int 
     local_sum(c, rhs, E, x, k, bvec.p);
     copy(c, xk.p, x->core(k), nel);
     local_target(c, opT, LA[k].p, RA[k + 1].p, r0, r1, k, 1.0, 0.0, Ax.p, xk.p);
-    k_cg_init<<<1, 1024, 0, c.stream>>>(nel, bvec.p, Ax.p, r.p, p.p, st, cg_tol * cg_tol);
-    after_launch(c, "cg_init");
+    k_cg_init1<<<CG_BLOCKS, CG_THREADS, 0, c.stream>>>(nel, bvec.p, Ax.p, r.p, p.p, st);
+    after_launch(c, "cg_init1");
+    k_cg_init2<<<1, 32, 0, c.stream>>>(st, cg_tol * cg_tol);
+    after_launch(c, "cg_init2");
     for (int it = 0; it < cg_iters; ++it) {
       c.guard = active;
       local_target(c, opT, LA[k].p, RA[k + 1].p, r0, r1, k, 1.0, 0.0, Ap.p, p.p);
       c.guard = nullptr;
       ProfScope ps(c, KC_CG);
-      k_cg_update<<<1, 1024, 0, c.stream>>>(nel, xk.p, r.p, p.p, Ap.p, st);
-      after_launch(c, "cg_update");
+      k_cg_pap<<<CG_BLOCKS, CG_THREADS, 0, c.stream>>>(nel, p.p, Ap.p, st);
+      after_launch(c, "cg_pap");
+      k_cg_xr<<<CG_BLOCKS, CG_THREADS, 0, c.stream>>>(nel, it, xk.p, r.p, p.p, Ap.p, st);
+      after_launch(c, "cg_xr");
+      k_cg_p<<<CG_BLOCKS, CG_THREADS, 0, c.stream>>>(nel, it, r.p, p.p, st);
+      after_launch(c, "cg_p");
     }
     k_cg_accumulate<<<1, 1, 0, c.stream>>>(st, reinterpret_cast<int*>(tot.p));
     after_launch(c, "cg_accumulate");

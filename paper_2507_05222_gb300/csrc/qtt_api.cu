@@ -5,6 +5,8 @@
 #include <memory>
 #include <string>
 
+#include <cuda_profiler_api.h>
+
 #include "qtt_algebra.h"
 #include "qtt_case.h"
 
@@ -144,6 +146,13 @@ int qtt_ctx_sync(qtt_ctx* ctx) {
 }
 
 const char* qtt_last_error(void) { return g_last_error.c_str(); }
+
+int qtt_profiler_range(int start) {
+  API_BEGIN
+  if (start) QTT_CUDA(cudaProfilerStart());
+  else QTT_CUDA(cudaProfilerStop());
+  API_END
+}
 
 int64_t qtt_ctx_kernel_launches(qtt_ctx* ctx) { return ctx ? reinterpret_cast<Ctx*>(ctx)->launches : 0; }
 

@@ -542,10 +542,12 @@ void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
   const int chi = P.chi;
   const double dt = P.dt;
   // (i) convective derivatives (MPO-MPS products rounded to chi, Sec. II.A.2)
+  std::unique_ptr<ProfScope> ph(new ProfScope(c, KC_PH_APPLY));
   MpsP dxu = mk(apply_round_gram(c, cs.Dx, cs.u, chi, 0.0));
   MpsP dzu = mk(apply_round_gram(c, cs.Dz, cs.u, chi, 0.0));
   MpsP dxv = mk(apply_round_gram(c, cs.Dx, cs.v, chi, 0.0));
   MpsP dzv = mk(apply_round_gram(c, cs.Dz, cs.v, chi, 0.0));
+  ph.reset(new ProfScope(c, KC_PH_RHS));
   // explicit right-hand sides (eq:intermediate_vel_eq), one fit each, warm start u (v)
   std::vector<Term> tu = {Term::vec(1.0, cs.u), Term::had(-dt, cs.u, dxu.get()), Term::had(-dt, cs.v, dzu.get())};
   if (cs.bcx_u) tu.push_back(Term::had(-dt, cs.u, cs.bcx_u));
@@ -557,6 +559,7 @@ void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
   fit(c, tu, rhs_u.get(), P.fit_sweeps, true);
   MpsP rhs_v = mk(mps_copy(c, cs.v));
   fit(c, tv_, rhs_v.get(), P.fit_sweeps, true);
+  ph.reset(new ProfScope(c, KC_PH_MOM));
   // (ii) implicit momentum: H v* = |J| (.) rhs + dt/Re |J| bcLap  (ALS, warm start v^m)
   const double kk = dt / P.Re;
   std::vector<Term> mu = {Term::mpo(1.0, cs.Jdiag, rhs_u.get())};
@@ -567,15 +570,18 @@ void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
   als(c, cs.H, mu, us.get(), P.mom.sweeps, P.mom.cg_iters, P.mom.cg_tol, true, cg_dev ? cg_dev + 0 : nullptr);
   MpsP vs = mk(mps_copy(c, cs.v));
   als(c, cs.H, mv, vs.get(), P.mom.sweeps, P.mom.cg_iters, P.mom.cg_tol, true, cg_dev ? cg_dev + 1 : nullptr);
+  ph.reset(new ProfScope(c, KC_PH_POI));
   // (iii) pressure Poisson, J-weighted (Sec. III.C): (-|J| Lap_h^p) p = -|J| (.) div(v*) / dt
   std::vector<Term> pr = {Term::mpo(1.0, cs.Px, us.get()), Term::mpo(1.0, cs.Pz, vs.get())};
   if (cs.bcdiv_w) pr.push_back(Term::vec(1.0, cs.bcdiv_w));
   als(c, cs.Ap, pr, cs.p, P.poi.sweeps, P.poi.cg_iters, P.poi.cg_tol, true, cg_dev ? cg_dev + 2 : nullptr);
+  ph.reset(new ProfScope(c, KC_PH_PROJ));
   // projection v = v* - dt grad_h p (one fit each, warm start v*)
   MpsP un = mk(mps_copy(c, us.get()));
   fit(c, {Term::vec(1.0, us.get()), Term::mpo(-dt, cs.Dxp, cs.p)}, un.get(), P.fit_sweeps, true);
   MpsP vn = mk(mps_copy(c, vs.get()));
   fit(c, {Term::vec(1.0, vs.get()), Term::mpo(-dt, cs.Dzp, cs.p)}, vn.get(), P.fit_sweeps, true);
+  ph.reset();
   free_mps(cs.u);
   cs.u = un.release();
   free_mps(cs.v);

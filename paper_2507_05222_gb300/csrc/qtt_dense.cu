@@ -133,11 +133,12 @@ TV tv(double* p, std::initializer_list<int64_t> dims) {
 
 namespace {
 
-constexpr int GT = 64;   // CTA tile (rows and columns)
 constexpr int GK = 16;   // k step staged in shared memory
 
-// 256 threads (16 x 16); each thread owns a 4 x 4 block of outputs strided by 16, so that the
-// shared-memory reads of B are consecutive across a warp and those of A are broadcasts.
+// 256 threads (16 x 16); each thread owns a (T/16) x (T/16) block of outputs strided by 16, so
+// that the shared-memory reads of B are consecutive across a warp and those of A are
+// broadcasts.  T = 64 for large outputs, T = 32 to put more CTAs on small ones.
+template <int T>
 __global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, int splits,
                                               int64_t batch, double alpha, const double* __restrict__ A,
                                               int64_t sAb, int64_t sAm, int64_t sAk,
@@ -146,58 +147,60 @@ __global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, i
                                               int64_t sCb, int64_t sCm, int64_t sCn,
                                               double* __restrict__ W, const int* __restrict__ guard) {
   if (guard && *guard == 0) return;
-  __shared__ double As[GK][GT];
-  __shared__ double Bs[GK][GT];
+  constexpr int R = T / 16;          // outputs per thread per dimension
+  constexpr int L = T * GK / 256;    // loads per thread per operand tile
+  __shared__ double As[GK][T];
+  __shared__ double Bs[GK][T];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int t = ty * 16 + tx;
-  const int64_t n0 = int64_t(blockIdx.x) * GT, m0 = int64_t(blockIdx.y) * GT;
+  const int64_t n0 = int64_t(blockIdx.x) * T, m0 = int64_t(blockIdx.y) * T;
   const int64_t b = blockIdx.z / splits;
   const int sp = blockIdx.z % splits;
   const int64_t k0 = sp * kchunk;
   const int64_t k1 = min(K, k0 + kchunk);
   const double* Ab = A + b * sAb;
   const double* Bb = B + b * sBb;
-  double acc[4][4];
+  double acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
   const bool a_k_fast = (sAk == 1);
   const bool b_n_fast = (sBn == 1);
   for (int64_t kb = k0; kb < k1; kb += GK) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < L; ++i) {
       int e = t + 256 * i;
       int mm, kk;
-      if (a_k_fast) { mm = e / GK; kk = e % GK; } else { mm = e % GT; kk = e / GT; }
+      if (a_k_fast) { mm = e / GK; kk = e % GK; } else { mm = e % T; kk = e / T; }
       int64_t gm = m0 + mm, gk = kb + kk;
       As[kk][mm] = (gm < M && gk < k1) ? Ab[gm * sAm + gk * sAk] : 0.0;
       int nn, kk2;
-      if (b_n_fast) { kk2 = e / GT; nn = e % GT; } else { nn = e / GK; kk2 = e % GK; }
+      if (b_n_fast) { kk2 = e / T; nn = e % T; } else { nn = e / GK; kk2 = e % GK; }
       int64_t gn = n0 + nn, gk2 = kb + kk2;
       Bs[kk2][nn] = (gn < N && gk2 < k1) ? Bb[gk2 * sBk + gn * sBn] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      double a[4], bv[4];
+      double a[R], bv[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < R; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+        for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < R; ++i) {
     int64_t gm = m0 + ty + 16 * i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < R; ++j) {
       int64_t gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
       if (W) {
@@ -244,30 +247,46 @@ void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, 
     after_launch(c, "splitk_reduce");
     return;
   }
-  int64_t tiles = ((M + GT - 1) / GT) * ((N + GT - 1) / GT) * batch;
-  int64_t target = 2 * int64_t(c.num_sms);
-  int splits = 1;
-  if (tiles < target && K > 2 * GK) {
-    int64_t want = (target + tiles - 1) / tiles;
-    int64_t maxs = (K + 2 * GK - 1) / (2 * GK);   // at least 32 k per split
-    splits = int(std::max<int64_t>(1, std::min<int64_t>(want, maxs)));
-  }
-  int64_t kchunk = (K + splits - 1) / splits;
-  kchunk = (kchunk + GK - 1) / GK * GK;
-  splits = int((K + kchunk - 1) / kchunk);
+  // Tile and split-K choice: enough CTAs to cover every SM twice (the FP64 pipe, not memory,
+  // bounds these kernels), the larger tile when it already gets there.
+  const int64_t target = 2 * int64_t(c.num_sms);
+  auto plan = [&](int T, int64_t& splits_out, int64_t& kchunk_out) {
+    int64_t tiles = ((M + T - 1) / T) * ((N + T - 1) / T) * batch;
+    int64_t splits = 1;
+    if (tiles < target && K > 2 * GK) {
+      int64_t want = (target + tiles - 1) / tiles;
+      int64_t maxs = (K + 2 * GK - 1) / (2 * GK);   // at least 32 k per split
+      splits = std::max<int64_t>(1, std::min<int64_t>(want, maxs));
+    }
+    int64_t kchunk = (K + splits - 1) / splits;
+    kchunk = (kchunk + GK - 1) / GK * GK;
+    splits = (K + kchunk - 1) / kchunk;
+    splits_out = splits;
+    kchunk_out = kchunk;
+    return tiles * splits;
+  };
+  int64_t s64, kc64, s32, kc32;
+  int64_t ctas64 = plan(64, s64, kc64);
+  int64_t ctas32 = plan(32, s32, kc32);
+  const bool big = ctas64 >= target || ctas64 >= ctas32;
+  const int T = big ? 64 : 32;
+  const int splits = int(big ? s64 : s32);
+  const int64_t kchunk = big ? kc64 : kc32;
   ProfScope ps(c, KC_GEMM, 2.0 * double(batch) * double(M) * double(N) * double(K));
-  dim3 grid(unsigned((N + GT - 1) / GT), unsigned((M + GT - 1) / GT), unsigned(batch * splits));
+  dim3 grid(unsigned((N + T - 1) / T), unsigned((M + T - 1) / T), unsigned(batch * splits));
   QTT_CHECK_ARG(grid.y <= 65535 && grid.z <= 65535, "gemm grid too large");
   dim3 block(16, 16);
-  if (splits == 1) {
-    k_gemm<<<grid, block, 0, c.stream>>>(M, N, K, kchunk, 1, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk, sBn,
-                                         beta, C, sCb, sCm, sCn, nullptr, c.guard);
-    after_launch(c, "gemm");
-  } else {
-    DBuf W(&c, size_t(splits) * batch * M * N);
-    k_gemm<<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
-                                         sBn, beta, C, sCb, sCm, sCn, W.p, c.guard);
-    after_launch(c, "gemm_splitk");
+  DBuf W;
+  if (splits > 1) W.reset(&c, size_t(splits) * batch * M * N);
+  double* Wp = splits > 1 ? W.p : nullptr;
+  if (big)
+    k_gemm<64><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
+                                             sBn, beta, C, sCb, sCm, sCn, Wp, c.guard);
+  else
+    k_gemm<32><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
+                                             sBn, beta, C, sCb, sCm, sCn, Wp, c.guard);
+  after_launch(c, "gemm");
+  if (splits > 1) {
     k_splitk_reduce<<<grid_for(batch * M * N, 256), 256, 0, c.stream>>>(batch, M, N, splits, alpha, W.p, beta, C,
                                                                         sCb, sCm, sCn, c.guard);
     after_launch(c, "splitk_reduce");

@@ -79,7 +79,12 @@ struct DBuf {
 };
 
 // Kernel classes for the optional per-class timing (CUDA events around each launch).
-enum KClass { KC_GEMM = 0, KC_QR = 1, KC_EIG = 2, KC_CG = 3, KC_OTHER = 4, KC_N = 5 };
+enum KClass {
+  KC_GEMM = 0, KC_QR = 1, KC_EIG = 2, KC_CG = 3, KC_OTHER = 4,
+  // phases of the fractional step (nested around the kernels above)
+  KC_PH_APPLY = 5, KC_PH_RHS = 6, KC_PH_MOM = 7, KC_PH_POI = 8, KC_PH_PROJ = 9,
+  KC_N = 10
+};
 
 struct Profiler {
   bool on = false;

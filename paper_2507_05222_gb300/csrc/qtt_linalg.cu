@@ -215,23 +215,24 @@ __global__ void __launch_bounds__(256) k_svd_jacobi(int m, int n, const double* 
 // ------------------------------------------------------------------ symmetric Jacobi (FP32)
 // S: n x n FP64 row-major symmetric.  V (FP64 out, row-major n x n): eigenvectors as columns.
 // With t0_dev != null only the trailing block S[t0:, t0:] is diagonalised (t0 read on the
-// device) and Vout is the identity outside that block.
+// device) and Vout is the identity outside that block.  1024 threads as 32 x 32: threadIdx.x
+// walks the matrix index, the warp index walks the rotation pairs, so no integer division by
+// a runtime size appears in the per-round updates.
 __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __restrict__ S, double* __restrict__ Vout,
                                                      int max_sweeps, const int* __restrict__ t0_dev) {
   extern __shared__ float smf[];
   const int t0 = t0_dev ? *t0_dev : 0;
   const int n = nfull - t0;
   if (t0_dev) {
-    for (int e = threadIdx.x; e < nfull * nfull; e += blockDim.x) {
-      int i = e / nfull, j = e % nfull;
-      if (i < t0 || j < t0) Vout[e] = (i == j) ? 1.0 : 0.0;
-    }
+    for (int i = threadIdx.y; i < nfull; i += 32)
+      for (int j = threadIdx.x; j < nfull; j += 32)
+        if (i < t0 || j < t0) Vout[size_t(i) * nfull + j] = (i == j) ? 1.0 : 0.0;
   }
   if (n <= 1) {
-    if (n == 1 && threadIdx.x == 0) Vout[size_t(t0) * nfull + t0] = 1.0;
+    if (n == 1 && threadIdx.x == 0 && threadIdx.y == 0) Vout[size_t(t0) * nfull + t0] = 1.0;
     return;
   }
-  const int ld = n + 1;                 // padded rows
+  const int ld = n + 1;                 // padded rows: column walks are bank-conflict free
   float* A = smf;                       // n x ld
   float* V = A + size_t(n) * ld;        // n x ld (row i = component i, column = vector)
   float* cs = V + size_t(n) * ld;       // np/2
@@ -239,42 +240,46 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
   int* pp = reinterpret_cast<int*>(sn + (n + 2) / 2);
   int* qq = pp + (n + 2) / 2;
   __shared__ float red[32];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, j = e % n;
-    A[i * ld + j] = float(S[size_t(i + t0) * nfull + (j + t0)]);
-    V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
-  }
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  for (int i = ty; i < n; i += 32)
+    for (int j = tx; j < n; j += 32) {
+      A[i * ld + j] = float(S[size_t(i + t0) * nfull + (j + t0)]);
+      V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+    }
   __syncthreads();
   const int np = (n + 1) & ~1;
   const int npairs = np / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // convergence test: off-diagonal mass relative to the total
     float off = 0.f, tot = 0.f;
-    for (int e = tid; e < n * n; e += nt) {
-      int i = e / n, j = e % n;
-      float a = A[i * ld + j];
-      tot += a * a;
-      if (i != j) off += a * a;
-    }
-    off = warp_sumf(off); tot = warp_sumf(tot);
-    __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = off;
+    for (int i = ty; i < n; i += 32)
+      for (int j = tx; j < n; j += 32) {
+        float a = A[i * ld + j];
+        tot += a * a;
+        if (i != j) off += a * a;
+      }
+    off = warp_sumf(off);
+    tot = warp_sumf(tot);
+    if (tx == 0) red[ty] = off;
     __syncthreads();
     float offs = 0.f;
-    for (int i = 0; i < (nt >> 5); ++i) offs += red[i];
+    for (int i = 0; i < 32; ++i) offs += red[i];
     __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = tot;
+    if (tx == 0) red[ty] = tot;
     __syncthreads();
     float tots = 0.f;
-    for (int i = 0; i < (nt >> 5); ++i) tots += red[i];
+    for (int i = 0; i < 32; ++i) tots += red[i];
     __syncthreads();
-    if (!(offs > 1e-13f * tots)) break;
+    if (!(offs > 1e-12f * tots)) break;
     for (int r = 0; r < np - 1; ++r) {
-      for (int k = tid; k < npairs; k += nt) {
+      if (tid < npairs) {
+        const int k = tid;
         int p, q;
         if (k == 0) { p = r; q = np - 1; }
-        else { p = (r + k) % (np - 1); q = (r - k + (np - 1)) % (np - 1); }
+        else {
+          p = r + k; if (p >= np - 1) p -= np - 1;
+          q = r - k; if (q < 0) q += np - 1;
+        }
         if (p > q) { int t2 = p; p = q; q = t2; }
         float c = 1.f, s = 0.f;
         if (q < n) {
@@ -289,34 +294,35 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
         pp[k] = p; qq[k] = q; cs[k] = c; sn[k] = s;
       }
       __syncthreads();
-      // rows p, q of A
-      for (int e = tid; e < npairs * n; e += nt) {
-        int k = e / n, j = e % n;
-        int p = pp[k], q = qq[k];
+      for (int k = ty; k < npairs; k += 32) {        // rows p, q of A
+        const int p = pp[k], q = qq[k];
         if (q >= n) continue;
-        float c = cs[k], s = sn[k];
-        float x = A[p * ld + j], y = A[q * ld + j];
-        A[p * ld + j] = c * x - s * y;
-        A[q * ld + j] = s * x + c * y;
+        const float c = cs[k], s = sn[k];
+        for (int j = tx; j < n; j += 32) {
+          float x = A[p * ld + j], y = A[q * ld + j];
+          A[p * ld + j] = c * x - s * y;
+          A[q * ld + j] = s * x + c * y;
+        }
       }
       __syncthreads();
-      // columns p, q of A and of V
-      for (int e = tid; e < npairs * n; e += nt) {
-        int k = e / n, i = e % n;
-        int p = pp[k], q = qq[k];
+      for (int k = ty; k < npairs; k += 32) {        // columns p, q of A and of V
+        const int p = pp[k], q = qq[k];
         if (q >= n) continue;
-        float c = cs[k], s = sn[k];
-        float x = A[i * ld + p], y = A[i * ld + q];
-        A[i * ld + p] = c * x - s * y;
-        A[i * ld + q] = s * x + c * y;
-        x = V[i * ld + p]; y = V[i * ld + q];
-        V[i * ld + p] = c * x - s * y;
-        V[i * ld + q] = s * x + c * y;
+        const float c = cs[k], s = sn[k];
+        for (int i = tx; i < n; i += 32) {
+          float x = A[i * ld + p], y = A[i * ld + q];
+          A[i * ld + p] = c * x - s * y;
+          A[i * ld + q] = s * x + c * y;
+          x = V[i * ld + p]; y = V[i * ld + q];
+          V[i * ld + p] = c * x - s * y;
+          V[i * ld + q] = s * x + c * y;
+        }
       }
       __syncthreads();
     }
   }
-  for (int e = tid; e < n * n; e += nt) Vout[size_t(e / n + t0) * nfull + (e % n + t0)] = double(V[(e / n) * ld + (e % n)]);
+  for (int i = ty; i < n; i += 32)
+    for (int j = tx; j < n; j += 32) Vout[size_t(i + t0) * nfull + (j + t0)] = double(V[i * ld + j]);
 }
 
 // First index of the sorted (descending) spectrum below tau * lambda_0; n if none.  Also
@@ -333,40 +339,63 @@ __global__ void k_tail_start(int n, const double* __restrict__ lam, double tau, 
   *need = (n - s >= 2) ? 1 : 0;
 }
 
-// One Ogita-Aishima correction, given XtX, S_ = X^T A X (both n x n) and ||A||_F.
-// Writes E (n x n) such that X <- X + X E, and the current eigenvalue estimates lam.
-__global__ void __launch_bounds__(1024) k_oa_update(int n, const double* __restrict__ XtX, const double* __restrict__ SX,
-                                                    const double* __restrict__ anorm_dev, double* __restrict__ E,
-                                                    double* __restrict__ lam, const int* __restrict__ guard) {
+// One Ogita-Aishima correction, given XtX, SX = X^T A X (both n x n) and ||A||_F, in three
+// short kernels spread over OA_BLOCKS blocks: eigenvalue estimates, the two residual norms
+// (partial sums per block, reduced in a fixed order), then E with X <- X + X E.
+constexpr int OA_BLOCKS = 64;
+
+__global__ void k_oa_lambda(int n, const double* __restrict__ XtX, const double* __restrict__ SX,
+                            double* __restrict__ lam, const int* __restrict__ guard) {
+  if (guard && *guard == 0) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    lam[i] = SX[i * n + i] / XtX[i * n + i];
+}
+
+__global__ void __launch_bounds__(256) k_oa_norms(int n, const double* __restrict__ XtX, const double* __restrict__ SX,
+                                                  const double* __restrict__ lam, double* __restrict__ part,
+                                                  const int* __restrict__ guard) {
   if (guard && *guard == 0) return;
   __shared__ double red[32];
-  const double anorm = *anorm_dev;
-  extern __shared__ double sl[];  // lam (n)
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < n; i += nt) sl[i] = SX[i * n + i] / (1.0 - (1.0 - XtX[i * n + i]));
-  __syncthreads();
   double so = 0.0, ro = 0.0;
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, j = e % n;
+  const int64_t nn = int64_t(n) * n;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nn; e += int64_t(gridDim.x) * blockDim.x) {
+    int i = int(e / n), j = int(e % n);
     double r = (i == j ? 1.0 : 0.0) - XtX[e];
-    double sd = SX[e] - (i == j ? sl[i] : 0.0);
-    so += sd * sd; ro += r * r;
+    double sd = SX[e] - (i == j ? lam[i] : 0.0);
+    so += sd * sd;
+    ro += r * r;
   }
-  double s2 = block_sum(so, red);
-  double r2 = block_sum(ro, red);
-  double delta = 2.0 * (sqrt(s2) + anorm * sqrt(r2));
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, j = e % n;
+  so = block_sum(so, red);
+  ro = block_sum(ro, red);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = so;
+    part[OA_BLOCKS + blockIdx.x] = ro;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_oa_E(int n, const double* __restrict__ XtX, const double* __restrict__ SX,
+                                              const double* __restrict__ lam, const double* __restrict__ part,
+                                              const double* __restrict__ anorm_dev, double* __restrict__ E,
+                                              const int* __restrict__ guard) {
+  if (guard && *guard == 0) return;
+  double s2 = 0.0, r2 = 0.0;
+  for (int i = 0; i < OA_BLOCKS; ++i) {
+    s2 += part[i];
+    r2 += part[OA_BLOCKS + i];
+  }
+  const double delta = 2.0 * (sqrt(s2) + (*anorm_dev) * sqrt(r2));
+  const int64_t nn = int64_t(n) * n;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nn; e += int64_t(gridDim.x) * blockDim.x) {
+    int i = int(e / n), j = int(e % n);
     double r = (i == j ? 1.0 : 0.0) - XtX[e];
     double val;
     if (i == j) val = 0.5 * r;
     else {
-      double d = sl[j] - sl[i];
-      val = (fabs(d) > delta) ? (SX[e] + sl[j] * r) / d : 0.5 * r;
+      double d = lam[j] - lam[i];
+      val = (fabs(d) > delta) ? (SX[e] + lam[j] * r) / d : 0.5 * r;
     }
     E[e] = val;
   }
-  for (int i = tid; i < n; i += nt) lam[i] = sl[i];
 }
 
 // Order eigenpairs by decreasing eigenvalue: w[k] = lam[order[k]], V[:, k] = X[:, order[k]].
@@ -444,14 +473,23 @@ void svd_small(Ctx& c, int m, int n, const double* G, double* U, double* s, doub
   after_launch(c, "svd_jacobi");
 }
 
+static void oa_update(Ctx& c, int n, const double* XtX, const double* SX, const double* an, double* E, double* lam,
+                      double* part, const int* guard) {
+  k_oa_lambda<<<1, 256, 0, c.stream>>>(n, XtX, SX, lam, guard);
+  after_launch(c, "oa_lambda");
+  k_oa_norms<<<OA_BLOCKS, 256, 0, c.stream>>>(n, XtX, SX, lam, part, guard);
+  after_launch(c, "oa_norms");
+  k_oa_E<<<OA_BLOCKS, 256, 0, c.stream>>>(n, XtX, SX, lam, part, an, E, guard);
+  after_launch(c, "oa_E");
+}
+
 // One Ogita-Aishima iteration on X (n x n) for the symmetric S.
 static void oa_iteration(Ctx& c, int n, const double* S, double* X, double* XtX, double* AX, double* SX, double* E,
-                         double* lam, const double* an) {
+                         double* lam, const double* an, double* part) {
   gemm(c, 1, n, n, n, 1.0, X, 0, 1, n, X, 0, n, 1, 0.0, XtX, 0, n, 1);   // X^T X
   gemm(c, 1, n, n, n, 1.0, S, 0, n, 1, X, 0, n, 1, 0.0, AX, 0, n, 1);    // S X
   gemm(c, 1, n, n, n, 1.0, X, 0, 1, n, AX, 0, n, 1, 0.0, SX, 0, n, 1);   // X^T S X
-  k_oa_update<<<1, 1024, n * sizeof(double), c.stream>>>(n, XtX, SX, an, E, lam, c.guard);
-  after_launch(c, "oa_update");
+  oa_update(c, n, XtX, SX, an, E, lam, part, c.guard);
   gemm(c, 1, n, n, n, 1.0, X, 0, n, 1, E, 0, n, 1, 0.0, AX, 0, n, 1);    // X E
   axpby(c, int64_t(n) * n, 1.0, AX, 1.0, X);
 }
@@ -473,12 +511,12 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
   }
   const size_t nn = size_t(n) * n;
   DBuf X(&c, nn), Xs(&c, nn), XtX(&c, nn), AX(&c, nn), SX(&c, nn), E(&c, nn), Y(&c, nn), lam(&c, size_t(n)),
-      an(&c, 1), flags(&c, 2);
+      an(&c, 1), flags(&c, 2), part(&c, 2 * OA_BLOCKS);
   int* t0 = reinterpret_cast<int*>(flags.p);
   int* need = t0 + 1;
   {
     ProfScope ps(c, KC_EIG);
-    k_jacobi_f32<<<1, 1024, smf, c.stream>>>(n, S, X.p, 12, nullptr);
+    k_jacobi_f32<<<1, dim3(32, 32), smf, c.stream>>>(n, S, X.p, 10, nullptr);
     after_launch(c, "jacobi_f32");
   }
   k_frob<<<1, 1024, 0, c.stream>>>(int64_t(n) * n, S, an.p);
@@ -494,21 +532,21 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
       c.guard = nullptr;
       {
         ProfScope ps(c, KC_EIG);
-        k_jacobi_f32<<<1, 1024, smf, c.stream>>>(n, SX.p, Y.p, 12, t0);
+        k_jacobi_f32<<<1, dim3(32, 32), smf, c.stream>>>(n, SX.p, Y.p, 8, t0);
         after_launch(c, "jacobi_f32_tail");
       }
       c.guard = need;
       gemm(c, 1, n, n, n, 1.0, X.p, 0, n, 1, Y.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
       copy_guarded(c, X.p, AX.p, int64_t(nn), need);
     }
-    for (int it = 0; it < 3; ++it) oa_iteration(c, n, S, X.p, XtX.p, AX.p, SX.p, E.p, lam.p, an.p);
+    for (int it = 0; it < (level == 0 ? 4 : 3); ++it)
+      oa_iteration(c, n, S, X.p, XtX.p, AX.p, SX.p, E.p, lam.p, an.p, part.p);
     c.guard = nullptr;
     // eigenvalue estimates of the refined vectors, then sort (descending)
     gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, X.p, 0, n, 1, 0.0, XtX.p, 0, n, 1);
     gemm(c, 1, n, n, n, 1.0, S, 0, n, 1, X.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
     gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, AX.p, 0, n, 1, 0.0, SX.p, 0, n, 1);
-    k_oa_update<<<1, 1024, n * sizeof(double), c.stream>>>(n, XtX.p, SX.p, an.p, E.p, lam.p, nullptr);
-    after_launch(c, "oa_update");
+    oa_update(c, n, XtX.p, SX.p, an.p, E.p, lam.p, part.p, nullptr);
     k_sort_eig<<<1, 1024, n * sizeof(int), c.stream>>>(n, lam.p, X.p, w, Xs.p);
     after_launch(c, "sort_eig");
     copy(c, X.p, Xs.p, int64_t(nn));

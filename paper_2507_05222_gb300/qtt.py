@@ -76,6 +76,7 @@ _SIGS = {
     "qtt_ctx_kernel_launches": (L, [P]),
     "qtt_ctx_pool_bytes": (S, [P]),
     "qtt_ctx_profile": (I, [P, I, DP, DP, C.POINTER(C.c_int64)]),
+    "qtt_profiler_range": (I, [I]),
     "qtt_mps_create": (I, [P, I, I, IP, DP, I, C.POINTER(P)]),
     "qtt_mps_free": (I, [P]),
     "qtt_mps_n": (I, [P]),
@@ -186,11 +187,13 @@ class Context:
     def pool_bytes(self) -> int:
         return int(lib().qtt_ctx_pool_bytes(self.h))
 
-    PROFILE_CLASSES = ("gemm_f64", "qr_f64", "eig_jacobi", "cg_update", "other")
+    PROFILE_CLASSES = ("gemm_f64", "qr_f64", "eig_jacobi", "cg_update", "other",
+                       "phase_apply", "phase_rhs_fit", "phase_momentum", "phase_poisson", "phase_projection")
 
     def profile(self, on: bool):
         """Read and reset the per-class kernel timing; switch recording on/off."""
-        ms = np.zeros(5); fl = np.zeros(5); n = np.zeros(5, dtype=np.int64)
+        k = len(self.PROFILE_CLASSES)
+        ms = np.zeros(k); fl = np.zeros(k); n = np.zeros(k, dtype=np.int64)
         _check(lib().qtt_ctx_profile(self.h, 1 if on else 0, _dp(ms), _dp(fl),
                                      n.ctypes.data_as(C.POINTER(C.c_int64))))
         return {k: dict(ms=float(ms[i]), flops=float(fl[i]), launches=int(n[i]))
@@ -379,6 +382,11 @@ def mps_hadamard_round(ctx: Context, a: MPS, b: MPS, chi: int, sweeps: int = 2, 
     _check(lib().mps_hadamard_round(ctx.h, a.h, b.h, _trunc(chi, 0.0), init.h if init is not None else None,
                                     sweeps, C.byref(h), None))
     return MPS(ctx, h)
+
+
+def profiler_range(start: bool):
+    """cudaProfilerStart / Stop (to bracket the launches an external profiler captures)."""
+    _check(lib().qtt_profiler_range(1 if start else 0))
 
 
 def mps_dot_noalloc(n: int, d: int, a_bonds, a_cores_dev: int, b_bonds, b_cores_dev: int, out_dev: int,

