@@ -147,6 +147,16 @@ def run_ours(args, cfg):
     gv = qtt.qtt_encode(ctx, qtt.qtt_field_to_vector(ctx, v0, cfg["ordering"]), ne + nx, chi)
     gp = qtt.MPS.from_cores(ctx, pad)
     case.set_state(gu, gv, gp)
+    if args.kernel_probe:
+        Dx = case.operator(0)
+        u, _, _ = case.get_state()
+        qtt.mpo_apply_round(ctx, Dx, u, chi)
+        ctx.sync()
+        qtt.profiler_range(True)
+        qtt.mpo_apply_round(ctx, Dx, u, chi)
+        ctx.sync()
+        qtt.profiler_range(False)
+        return
     if args.profile_one_step:
         qtt.fractional_step(ctx, case, 1, info=False)
         ctx.sync()
@@ -183,12 +193,15 @@ def run_ours(args, cfg):
         t = torch.tensor([step_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         step_ms = float(t.item())
-    # ---- per-class kernel timing over the same number of steps (roofline of the dominant class)
+    # ---- per-class kernel timing (roofline of the dominant class): the same kernels launched one
+    # by one (timing events cannot sit inside the captured graph), L2 flushed between steps
+    case.use_graph(False)
     ctx.profile(True)
     for k in range(min(args.steps, 2)):
         flush.fill_(float(k))
         qtt.fractional_step(ctx, case, 1, info=False)
     prof = ctx.profile(False)
+    case.use_graph(True)
     nprof = min(args.steps, 2)
     g = prof["gemm_f64"]
     achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else 0.0
@@ -249,6 +262,8 @@ def main():
     ap.add_argument("--chi", type=int, default=None)
     ap.add_argument("--profile-one-step", action="store_true",
                     help="set up, one warm-up step, then one step between cudaProfilerStart/Stop (for ncu)")
+    ap.add_argument("--kernel-probe", action="store_true",
+                    help="set up, then one D_x u product with rounding between cudaProfilerStart/Stop (for ncu)")
     args = ap.parse_args()
     cfg = dict(WORKLOAD)
     if args.n is not None:

@@ -112,8 +112,8 @@ int64_t qtt_ctx_kernel_launches(qtt_ctx* ctx);
 size_t qtt_ctx_pool_bytes(qtt_ctx* ctx);
 /* Per-kernel-class timing.  Synchronises the stream, then writes, for classes 0 FP64 GEMM,
  * 1 Householder QR, 2 Jacobi eigensolver, 3 CG update, 4 other, and the phases of
- * fractional_step 5 MPO-MPS products, 6 right-hand-side fits, 7 momentum solves, 8 Poisson
- * solve, 9 projection fits, the summed CUDA-event time (ms), the algorithmic flops and the
+ * fractional_step 5 MPO-MPS products, 6 right-hand-side fits with the momentum solves (they
+ * overlap on worker streams), 7 unused, 8 Poisson solve, 9 projection fits, the summed CUDA-event time (ms), the algorithmic flops and the
  * launch count recorded since the previous call (each array of 10, any may be NULL), resets
  * them, and turns event recording on (on != 0) or off.  Events are recorded on the context
  * stream around each launch (or phase) of a timed class. */
@@ -249,6 +249,11 @@ int qtt_case_get_vector(qtt_case* c, int which, qtt_mps** out);
  * records, valid after qtt_ctx_sync.  Forces are evaluated when with_forces != 0. */
 int fractional_step(qtt_ctx* ctx, qtt_case* c, int nsteps, int with_forces,
                     qtt_step_info* per_step);
+/* Replay mode of fractional_step.  enable != 0 (the default): the first call captures one
+ * step as a CUDA graph on an internal stream (ordered after the context stream by events)
+ * and every step replays it; the graph is dropped when the state is set again.  enable = 0:
+ * every step is launched kernel by kernel (same kernels, same results). */
+int qtt_case_use_graph(qtt_case* c, int enable);
 /* Drag and lift of the current state (App. F; synchronous). */
 int qtt_case_forces(qtt_ctx* ctx, qtt_case* c, double* cd, double* cl);
 /* Strouhal number from upward zero crossings of C_L(t) (eq:st); host-only arithmetic on a

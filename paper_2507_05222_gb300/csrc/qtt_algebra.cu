@@ -519,13 +519,25 @@ qtt_mps* round_gram(Ctx& c, const qtt_mps* y, int chi, double eps) {
 
 // Gram rounding of y = M x without forming y: the left Gram of y at bond k is kept in the
 // factored index (w, a, w', a'), and Z = (M x)[k] P is contracted from M[k], X[k] directly.
-qtt_mps* apply_round_gram(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, double eps) {
+std::vector<int> apply_bonds(const qtt_mpo* M, const qtt_mps* x, int chi) {
+  const int n = x->n, d = x->d;
+  std::vector<int> R(n + 1);
+  for (int k = 0; k <= n; ++k) R[k] = M->bonds[k] * x->bonds[k];
+  std::vector<int> m = left_struct(R, d);
+  std::vector<int> ob(n + 1, 1);
+  for (int k = n - 1; k >= 1; --k) ob[k] = std::max(1, std::min(std::min(chi, m[k]), d * ob[k + 1]));
+  if (n == 1) ob = R;
+  return ob;
+}
+
+qtt_mps* apply_round_gram(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, double eps, qtt_mps* into) {
   const int n = x->n, d = x->d;
   QTT_CHECK_ARG(M->n == n && M->d == d, "apply: shape mismatch");
   std::vector<int> R(n + 1);
   for (int k = 0; k <= n; ++k) R[k] = M->bonds[k] * x->bonds[k];
   std::vector<int> mstruct = left_struct(R, d);
   if (n == 1) {
+    QTT_CHECK_ARG(!into, "apply into: single-core operands are not supported");
     qtt_mps* y = mpo_mps_exact(c, M, x);
     return y;
   }
@@ -579,7 +591,9 @@ qtt_mps* apply_round_gram(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, d
     P = std::move(Pn);
     ob[k] = bk;
   }
-  qtt_mps* z = new_mps(&c, n, d, ob);
+  qtt_mps* z = into;
+  if (z) QTT_CHECK_ARG(z->n == n && z->d == d && z->bonds == ob, "apply into: output bonds differ");
+  else z = new_mps(&c, n, d, ob);
   for (int k = 0; k < n; ++k) copy(c, z->core(k), out[k].p, int64_t(ob[k]) * d * ob[k + 1]);
   return z;
 }

@@ -42,7 +42,9 @@ qtt_mpo* mps_as_mpo(Ctx& c, const qtt_mps* x, int d);
 qtt_mps* round_svd(Ctx& c, const qtt_mps* x, int chi, double eps);    // QR + Jacobi SVD, FP64
 qtt_mps* round_gram(Ctx& c, const qtt_mps* y, int chi, double eps);   // Gram / density matrix
 qtt_mps* round_any(Ctx& c, const qtt_mps* y, int chi, double eps);
-qtt_mps* apply_round_gram(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, double eps);
+// y = round(M x) by Gram rounding; written into `into` (bonds apply_bonds(M, x, chi)) if given.
+qtt_mps* apply_round_gram(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, double eps, qtt_mps* into = nullptr);
+std::vector<int> apply_bonds(const qtt_mpo* M, const qtt_mps* x, int chi);
 
 void right_orthonormalize(Ctx& c, qtt_mps* x);
 // Variational fit of sum(terms) in place on x (fixed bonds), `sweeps` full sweeps.

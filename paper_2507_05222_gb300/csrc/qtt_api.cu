@@ -120,6 +120,10 @@ int qtt_ctx_create(qtt_ctx** out, int device, void* cuda_stream, qtt_alloc_fn al
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   QTT_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
   c->pool = new Pool(alloc, free_fn, user);
+  c->root = c.get();
+  c->alloc_fn = alloc;
+  c->free_fn = free_fn;
+  c->alloc_user = user;
   *out = reinterpret_cast<qtt_ctx*>(c.release());
   API_END
 }
@@ -128,6 +132,7 @@ void qtt_ctx_destroy(qtt_ctx* ctx) {
   if (!ctx) return;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   cudaStreamSynchronize(c->stream);
+  destroy_workers(*c);
   for (auto e : c->prof.free_events) cudaEventDestroy(e);
   for (int k = 0; k < KC_N; ++k)
     for (auto& pr : c->prof.pending[k]) {
@@ -548,18 +553,32 @@ int qtt_case_set_state(qtt_case* h, const qtt_mps* u, const qtt_mps* v, const qt
       QTT_CHECK_ARG(x->bonds[k] <= 2 * x->bonds[k + 1] && x->bonds[k] <= 2 * x->bonds[k - 1],
                     "case_set_state: bonds must satisfy r_k <= 2 r_{k+-1}");
   }
-  qtt_mps* nu = mps_copy(c, u);
-  qtt_mps* nv = mps_copy(c, v);
-  qtt_mps* np = mps_copy(c, p);
-  right_orthonormalize(c, nu);
-  right_orthonormalize(c, nv);
-  right_orthonormalize(c, np);
-  if (cs.u) free_mps(cs.u);
-  if (cs.v) free_mps(cs.v);
-  if (cs.p) free_mps(cs.p);
-  cs.u = nu;
-  cs.v = nv;
-  cs.p = np;
+  // Same bond profile as the current state: copy into the existing buffers (a captured step
+  // graph, which refers to these addresses, stays valid).  Otherwise new buffers.
+  const bool same = cs.u && cs.v && cs.p && cs.u->bonds == u->bonds && cs.v->bonds == v->bonds &&
+                    cs.p->bonds == p->bonds;
+  if (same) {
+    copy(c, cs.u->buf.p, u->buf.p, u->off[n]);
+    copy(c, cs.v->buf.p, v->buf.p, v->off[n]);
+    copy(c, cs.p->buf.p, p->buf.p, p->off[n]);
+    right_orthonormalize(c, cs.u);
+    right_orthonormalize(c, cs.v);
+    right_orthonormalize(c, cs.p);
+  } else {
+    cs.drop_graph();   // the captured step refers to the old state buffers
+    qtt_mps* nu = mps_copy(c, u);
+    qtt_mps* nv = mps_copy(c, v);
+    qtt_mps* np = mps_copy(c, p);
+    right_orthonormalize(c, nu);
+    right_orthonormalize(c, nv);
+    right_orthonormalize(c, np);
+    if (cs.u) free_mps(cs.u);
+    if (cs.v) free_mps(cs.v);
+    if (cs.p) free_mps(cs.p);
+    cs.u = nu;
+    cs.v = nv;
+    cs.p = np;
+  }
   API_END
 }
 
@@ -606,10 +625,7 @@ int fractional_step(qtt_ctx* ctx, qtt_case* h, int nsteps, int with_forces, qtt_
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   DBuf rec(&c, size_t(std::max(nsteps, 1)) * 4);
   fill(c, rec.p, int64_t(std::max(nsteps, 1)) * 4, 0.0);
-  for (int s = 0; s < nsteps; ++s) {
-    double* r = rec.p + 4 * s;
-    step(c, cs, per_step ? reinterpret_cast<int*>(r) : nullptr, (with_forces && per_step) ? r + 2 : nullptr);
-  }
+  run_steps(c, cs, nsteps, with_forces && per_step, per_step ? rec.p : nullptr);
   if (per_step && nsteps > 0) {
     std::vector<double> hrec(size_t(nsteps) * 4);
     QTT_CUDA(cudaMemcpyAsync(hrec.data(), rec.p, hrec.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
@@ -624,6 +640,14 @@ int fractional_step(qtt_ctx* ctx, qtt_case* h, int nsteps, int with_forces, qtt_
       per_step[s].cl = with_forces ? hrec[4 * s + 3] : 0.0;
     }
   }
+  API_END
+}
+
+int qtt_case_use_graph(qtt_case* h, int enable) {
+  API_BEGIN
+  QTT_CHECK_ARG(h, "case_use_graph: null case");
+  h->cs->drop_graph();
+  h->cs->use_graph = enable != 0;
   API_END
 }
 

@@ -317,7 +317,26 @@ qtt_mps* add_round(Ctx& c, const qtt_mps* a, const qtt_mps* b) {
 
 // ------------------------------------------------------------------ case
 
+void Case::drop_graph() {
+  if (gexec || graph) {
+    if (gstream) cudaStreamSynchronize(gstream);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    gexec = nullptr;
+    graph = nullptr;
+    if (ctx) {
+      ctx->pool->release_capture();
+      for (Ctx* w : ctx->workers) w->pool->release_capture();
+    }
+  }
+}
+
 Case::~Case() {
+  drop_graph();
+  if (gstream) cudaStreamDestroy(gstream);
+  if (ev_in) cudaEventDestroy(ev_in);
+  if (ev_out) cudaEventDestroy(ev_out);
+  if (rec) cudaFree(rec);
   for (qtt_mpo* m : {Dx, Dz, Dxp, Dzp, H, Ap, Px, Pz, Jdiag})
     if (m) free_mpo(m);
   for (qtt_mps* x : {bcx_u, bcz_u, bcx_v, bcz_v, JbcLap_u, JbcLap_v, bcdiv_w, absJ, u, v, p})
@@ -435,6 +454,7 @@ Case* build_case(Ctx& c, const qtt_case_params& P) {
       cs->bcdiv_w = had_round(c, jw.get(), bd.get());
     }
   }
+  cs->ctx = &c;
   QTT_CUDA(cudaStreamSynchronize(c.stream));
   return cs.release();
 }
@@ -537,18 +557,30 @@ void case_forces(Ctx& c, Case& cs, double* out_dev) {
 
 // ------------------------------------------------------------------ the fractional step
 
+// Independent parts run on worker streams: the four MPO-MPS products (4 workers), the
+// right-hand side and momentum solve of each velocity component (2 workers), the two
+// projection fits (2 workers).  The Poisson solve couples u* and v* and runs on the caller's
+// stream.  Results that cross streams are allocated before the fork.
 void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
   const qtt_case_params& P = cs.P;
   const int chi = P.chi;
   const double dt = P.dt;
+  const int n = cs.u->n;
   // (i) convective derivatives (MPO-MPS products rounded to chi, Sec. II.A.2)
   std::unique_ptr<ProfScope> ph(new ProfScope(c, KC_PH_APPLY));
-  MpsP dxu = mk(apply_round_gram(c, cs.Dx, cs.u, chi, 0.0));
-  MpsP dzu = mk(apply_round_gram(c, cs.Dz, cs.u, chi, 0.0));
-  MpsP dxv = mk(apply_round_gram(c, cs.Dx, cs.v, chi, 0.0));
-  MpsP dzv = mk(apply_round_gram(c, cs.Dz, cs.v, chi, 0.0));
+  MpsP dxu = mk(new_mps(&c, n, 2, apply_bonds(cs.Dx, cs.u, chi)));
+  MpsP dzu = mk(new_mps(&c, n, 2, apply_bonds(cs.Dz, cs.u, chi)));
+  MpsP dxv = mk(new_mps(&c, n, 2, apply_bonds(cs.Dx, cs.v, chi)));
+  MpsP dzv = mk(new_mps(&c, n, 2, apply_bonds(cs.Dz, cs.v, chi)));
+  fork(c, 4);
+  apply_round_gram(worker(c, 0), cs.Dx, cs.u, chi, 0.0, dxu.get());
+  apply_round_gram(worker(c, 1), cs.Dz, cs.u, chi, 0.0, dzu.get());
+  apply_round_gram(worker(c, 2), cs.Dx, cs.v, chi, 0.0, dxv.get());
+  apply_round_gram(worker(c, 3), cs.Dz, cs.v, chi, 0.0, dzv.get());
+  join(c, 4);
+  // explicit right-hand sides (eq:intermediate_vel_eq), one fit each, warm start u (v), then
+  // (ii) implicit momentum H v* = |J| (.) rhs + dt/Re |J| bcLap (ALS, warm start v^m)
   ph.reset(new ProfScope(c, KC_PH_RHS));
-  // explicit right-hand sides (eq:intermediate_vel_eq), one fit each, warm start u (v)
   std::vector<Term> tu = {Term::vec(1.0, cs.u), Term::had(-dt, cs.u, dxu.get()), Term::had(-dt, cs.v, dzu.get())};
   if (cs.bcx_u) tu.push_back(Term::had(-dt, cs.u, cs.bcx_u));
   if (cs.bcz_u) tu.push_back(Term::had(-dt, cs.v, cs.bcz_u));
@@ -556,37 +588,100 @@ void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
   if (cs.bcx_v) tv_.push_back(Term::had(-dt, cs.u, cs.bcx_v));
   if (cs.bcz_v) tv_.push_back(Term::had(-dt, cs.v, cs.bcz_v));
   MpsP rhs_u = mk(mps_copy(c, cs.u));
-  fit(c, tu, rhs_u.get(), P.fit_sweeps, true);
   MpsP rhs_v = mk(mps_copy(c, cs.v));
-  fit(c, tv_, rhs_v.get(), P.fit_sweeps, true);
-  ph.reset(new ProfScope(c, KC_PH_MOM));
-  // (ii) implicit momentum: H v* = |J| (.) rhs + dt/Re |J| bcLap  (ALS, warm start v^m)
+  MpsP us = mk(mps_copy(c, cs.u));
+  MpsP vs = mk(mps_copy(c, cs.v));
   const double kk = dt / P.Re;
   std::vector<Term> mu = {Term::mpo(1.0, cs.Jdiag, rhs_u.get())};
   if (cs.JbcLap_u) mu.push_back(Term::vec(kk, cs.JbcLap_u));
   std::vector<Term> mv = {Term::mpo(1.0, cs.Jdiag, rhs_v.get())};
   if (cs.JbcLap_v) mv.push_back(Term::vec(kk, cs.JbcLap_v));
-  MpsP us = mk(mps_copy(c, cs.u));
-  als(c, cs.H, mu, us.get(), P.mom.sweeps, P.mom.cg_iters, P.mom.cg_tol, true, cg_dev ? cg_dev + 0 : nullptr);
-  MpsP vs = mk(mps_copy(c, cs.v));
-  als(c, cs.H, mv, vs.get(), P.mom.sweeps, P.mom.cg_iters, P.mom.cg_tol, true, cg_dev ? cg_dev + 1 : nullptr);
-  ph.reset(new ProfScope(c, KC_PH_POI));
+  fork(c, 2);
+  fit(worker(c, 0), tu, rhs_u.get(), P.fit_sweeps, true);
+  fit(worker(c, 1), tv_, rhs_v.get(), P.fit_sweeps, true);
+  als(worker(c, 0), cs.H, mu, us.get(), P.mom.sweeps, P.mom.cg_iters, P.mom.cg_tol, true, cg_dev ? cg_dev + 0 : nullptr);
+  als(worker(c, 1), cs.H, mv, vs.get(), P.mom.sweeps, P.mom.cg_iters, P.mom.cg_tol, true, cg_dev ? cg_dev + 1 : nullptr);
+  join(c, 2);
   // (iii) pressure Poisson, J-weighted (Sec. III.C): (-|J| Lap_h^p) p = -|J| (.) div(v*) / dt
+  ph.reset(new ProfScope(c, KC_PH_POI));
   std::vector<Term> pr = {Term::mpo(1.0, cs.Px, us.get()), Term::mpo(1.0, cs.Pz, vs.get())};
   if (cs.bcdiv_w) pr.push_back(Term::vec(1.0, cs.bcdiv_w));
   als(c, cs.Ap, pr, cs.p, P.poi.sweeps, P.poi.cg_iters, P.poi.cg_tol, true, cg_dev ? cg_dev + 2 : nullptr);
-  ph.reset(new ProfScope(c, KC_PH_PROJ));
   // projection v = v* - dt grad_h p (one fit each, warm start v*)
+  ph.reset(new ProfScope(c, KC_PH_PROJ));
   MpsP un = mk(mps_copy(c, us.get()));
-  fit(c, {Term::vec(1.0, us.get()), Term::mpo(-dt, cs.Dxp, cs.p)}, un.get(), P.fit_sweeps, true);
   MpsP vn = mk(mps_copy(c, vs.get()));
-  fit(c, {Term::vec(1.0, vs.get()), Term::mpo(-dt, cs.Dzp, cs.p)}, vn.get(), P.fit_sweeps, true);
+  fork(c, 2);
+  fit(worker(c, 0), {Term::vec(1.0, us.get()), Term::mpo(-dt, cs.Dxp, cs.p)}, un.get(), P.fit_sweeps, true);
+  fit(worker(c, 1), {Term::vec(1.0, vs.get()), Term::mpo(-dt, cs.Dzp, cs.p)}, vn.get(), P.fit_sweeps, true);
+  join(c, 2);
   ph.reset();
-  free_mps(cs.u);
-  cs.u = un.release();
-  free_mps(cs.v);
-  cs.v = vn.release();
+  // new state into the same buffers (the captured graph reads and writes these addresses)
+  copy(c, cs.u->buf.p, un->buf.p, cs.u->off[n]);
+  copy(c, cs.v->buf.p, vn->buf.p, cs.v->off[n]);
   if (forces_dev) case_forces(c, cs, forces_dev);
+}
+
+static void capture(Ctx& c, Case& cs, bool with_forces) {
+  cs.drop_graph();
+  init_kernel_attributes();
+  for (int i = 0; i < 4; ++i) worker(c, i);
+  if (!cs.gstream) QTT_CUDA(cudaStreamCreateWithFlags(&cs.gstream, cudaStreamNonBlocking));
+  if (!cs.ev_in) QTT_CUDA(cudaEventCreateWithFlags(&cs.ev_in, cudaEventDisableTiming));
+  if (!cs.ev_out) QTT_CUDA(cudaEventCreateWithFlags(&cs.ev_out, cudaEventDisableTiming));
+  if (!cs.rec) QTT_CUDA(cudaMalloc(&cs.rec, 4 * sizeof(double)));
+  cudaStream_t saved = c.stream;
+  const bool prof_on = c.root->prof.on;
+  c.root->prof.on = false;   // no timing events inside a graph
+  c.pool->begin_capture();
+  for (Ctx* w : c.workers) w->pool->begin_capture();
+  c.stream = cs.gstream;
+  const int64_t n0 = c.root->launches;
+  cudaError_t err = cudaStreamBeginCapture(cs.gstream, cudaStreamCaptureModeRelaxed);
+  try {
+    if (err != cudaSuccess) throw Error(QTT_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(err));
+    step(c, cs, reinterpret_cast<int*>(cs.rec), with_forces ? cs.rec + 2 : nullptr);
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(cs.gstream, &g);
+    if (g) cudaGraphDestroy(g);
+    c.stream = saved;
+    c.pool->end_capture();
+    for (Ctx* w : c.workers) w->pool->end_capture();
+    c.root->prof.on = prof_on;
+    c.root->launches = n0;
+    throw;
+  }
+  err = cudaStreamEndCapture(cs.gstream, &cs.graph);
+  c.stream = saved;
+  c.pool->end_capture();
+  for (Ctx* w : c.workers) w->pool->end_capture();
+  c.root->prof.on = prof_on;
+  cs.graph_launches = c.root->launches - n0;
+  c.root->launches = n0;
+  if (err != cudaSuccess) throw Error(QTT_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(err));
+  QTT_CUDA(cudaGraphInstantiate(&cs.gexec, cs.graph, 0));
+  cs.graph_forces = with_forces;
+}
+
+void run_steps(Ctx& c, Case& cs, int nsteps, bool with_forces, double* rec_all) {
+  if (!cs.use_graph) {
+    for (int s = 0; s < nsteps; ++s) {
+      double* r = rec_all ? rec_all + 4 * s : nullptr;
+      step(c, cs, r ? reinterpret_cast<int*>(r) : nullptr, (with_forces && r) ? r + 2 : nullptr);
+    }
+    return;
+  }
+  if (!cs.gexec || cs.graph_forces != with_forces) capture(c, cs, with_forces);
+  for (int s = 0; s < nsteps; ++s) {
+    QTT_CUDA(cudaEventRecord(cs.ev_in, c.stream));
+    QTT_CUDA(cudaStreamWaitEvent(cs.gstream, cs.ev_in, 0));
+    QTT_CUDA(cudaGraphLaunch(cs.gexec, cs.gstream));
+    QTT_CUDA(cudaEventRecord(cs.ev_out, cs.gstream));
+    QTT_CUDA(cudaStreamWaitEvent(c.stream, cs.ev_out, 0));
+    c.root->launches += cs.graph_launches;
+    if (rec_all) copy(c, rec_all + 4 * s, cs.rec, 4);
+  }
 }
 
 }  // namespace qtt

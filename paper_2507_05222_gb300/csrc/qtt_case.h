@@ -20,11 +20,26 @@ struct Case {
           *JbcLap_v = nullptr, *bcdiv_w = nullptr, *absJ = nullptr;
   // state
   qtt_mps *u = nullptr, *v = nullptr, *p = nullptr;
+  // CUDA graph of one step (captured on first use, replayed afterwards; invalidated when the
+  // state buffers change).  The graph writes its per-step record (3 CG counts, C_D, C_L) to rec.
+  bool use_graph = true;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  bool graph_forces = false;
+  int64_t graph_launches = 0;
+  double* rec = nullptr;        // 4 doubles of device memory (allocated with cudaMalloc once)
+  Ctx* ctx = nullptr;
+  void drop_graph();
   ~Case();
 };
 
 Case* build_case(Ctx& c, const qtt_case_params& P);
 void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev);
+// nsteps steps, replaying the captured graph when cs.use_graph; records (4 doubles per step:
+// three CG counts packed as ints in the first 16 bytes, then C_D, C_L) into rec_all (device).
+void run_steps(Ctx& c, Case& cs, int nsteps, bool with_forces, double* rec_all);
 void case_forces(Ctx& c, Case& cs, double* out_dev);
 void read_row(Ctx& c, const Case& cs, const qtt_mps* x, int64_t I, double* row_dev);
 

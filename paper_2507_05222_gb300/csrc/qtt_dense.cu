@@ -44,6 +44,26 @@ void* Pool::raw_alloc(size_t bytes) {
 
 void* Pool::get(size_t bytes) {
   size_t cls = size_class(bytes);
+  if (capturing_) {
+    auto ci = cap_free_.find(cls);
+    if (ci != cap_free_.end()) {
+      void* p = ci->second;
+      cap_free_.erase(ci);
+      live_[p] = cls;
+      return p;
+    }
+    if (cls > cur_left_) {
+      size_t chunk = std::max<size_t>(cls, size_t(64) << 20);
+      cur_ = static_cast<char*>(raw_alloc(chunk));
+      cur_left_ = chunk;
+    }
+    void* p = cur_;
+    cur_ += cls;
+    cur_left_ -= cls;
+    live_[p] = cls;
+    cap_owned_[p] = cls;
+    return p;
+  }
   auto it = free_blocks_.lower_bound(cls);
   if (it != free_blocks_.end() && it->first == cls) {
     void* p = it->second;
@@ -67,8 +87,45 @@ void Pool::put(void* p) {
   if (!p) return;
   auto it = live_.find(p);
   if (it == live_.end()) return;
-  free_blocks_.insert({it->second, p});
+  size_t cls = it->second;
   live_.erase(it);
+  if (cap_owned_.count(p)) {
+    cap_free_.insert({cls, p});   // reserved for the graph: reused only by a capture
+    return;
+  }
+  if (capturing_) {
+    deferred_.push_back(p);
+    live_[p] = cls;                               // keep its size until the capture ends
+    return;
+  }
+  free_blocks_.insert({cls, p});
+}
+
+void Pool::begin_capture() {
+  capturing_ = true;
+}
+
+void Pool::end_capture() {
+  capturing_ = false;
+  for (void* p : deferred_) {
+    auto it = live_.find(p);
+    if (it != live_.end()) {
+      free_blocks_.insert({it->second, p});
+      live_.erase(it);
+    }
+  }
+  deferred_.clear();
+}
+
+void Pool::release_capture() {
+  for (auto& kv : cap_free_) free_blocks_.insert(kv);
+  cap_free_.clear();
+  // arena blocks still live (held by objects created during the capture) stay with their owners
+  for (auto it = cap_owned_.begin(); it != cap_owned_.end();) {
+    if (!live_.count(it->first)) it = cap_owned_.erase(it);
+    else ++it;
+  }
+  cap_owned_.clear();
 }
 
 DBuf::DBuf(Ctx* c, size_t count) { reset(c, count); }
@@ -91,15 +148,16 @@ void DBuf::reset(Ctx* c, size_t count) {
 }
 
 void after_launch(Ctx& c, const char* what) {
-  c.launches += 1;
+  c.root->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw Error(QTT_ERR_CUDA, std::string("launch of ") + what + ": " + cudaGetErrorString(e));
 }
 
 static cudaEvent_t take_event(Ctx& c) {
-  if (!c.prof.free_events.empty()) {
-    cudaEvent_t e = c.prof.free_events.back();
-    c.prof.free_events.pop_back();
+  Profiler& pr = c.root->prof;
+  if (!pr.free_events.empty()) {
+    cudaEvent_t e = pr.free_events.back();
+    pr.free_events.pop_back();
     return e;
   }
   cudaEvent_t e;
@@ -108,9 +166,10 @@ static cudaEvent_t take_event(Ctx& c) {
 }
 
 ProfScope::ProfScope(Ctx& ctx, int kclass, double flops) : c(ctx), k(kclass) {
-  if (!c.prof.on) return;
-  c.prof.flops[k] += flops;
-  c.prof.launches[k] += 1;
+  Profiler& pr = c.root->prof;
+  if (!pr.on) return;
+  pr.flops[k] += flops;
+  pr.launches[k] += 1;
   e0 = take_event(c);
   cudaEventRecord(e0, c.stream);
 }
@@ -119,7 +178,58 @@ ProfScope::~ProfScope() {
   if (!e0) return;
   cudaEvent_t e1 = take_event(c);
   cudaEventRecord(e1, c.stream);
-  c.prof.pending[k].push_back({e0, e1});
+  c.root->prof.pending[k].push_back({e0, e1});
+}
+
+Ctx& worker(Ctx& c, int i) {
+  while (int(c.workers.size()) <= i) {
+    Ctx* w = new Ctx;
+    w->device = c.device;
+    w->num_sms = c.num_sms;
+    w->root = c.root;
+    w->alloc_fn = c.alloc_fn;
+    w->free_fn = c.free_fn;
+    w->alloc_user = c.alloc_user;
+    cudaError_t e = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete w;
+      throw Error(QTT_ERR_CUDA, std::string("worker stream: ") + cudaGetErrorString(e));
+    }
+    w->pool = new Pool(c.alloc_fn, c.free_fn, c.alloc_user);
+    cudaEvent_t j;
+    QTT_CUDA(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
+    c.ev_join.push_back(j);
+    c.workers.push_back(w);
+  }
+  return *c.workers[i];
+}
+
+void fork(Ctx& c, int n) {
+  for (int i = 0; i < n; ++i) worker(c, i);
+  if (!c.ev_fork) QTT_CUDA(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
+  QTT_CUDA(cudaEventRecord(c.ev_fork, c.stream));
+  for (int i = 0; i < n; ++i) QTT_CUDA(cudaStreamWaitEvent(c.workers[i]->stream, c.ev_fork, 0));
+}
+
+void join(Ctx& c, int n) {
+  for (int i = 0; i < n; ++i) {
+    QTT_CUDA(cudaEventRecord(c.ev_join[i], c.workers[i]->stream));
+    QTT_CUDA(cudaStreamWaitEvent(c.stream, c.ev_join[i], 0));
+  }
+}
+
+void destroy_workers(Ctx& c) {
+  for (Ctx* w : c.workers) {
+    cudaStreamSynchronize(w->stream);
+    delete w->pool;
+    cudaStreamDestroy(w->stream);
+    delete w;
+  }
+  c.workers.clear();
+  for (cudaEvent_t e : c.ev_join) cudaEventDestroy(e);
+  c.ev_join.clear();
+  if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+  c.ev_fork = nullptr;
 }
 
 TV tv(double* p, std::initializer_list<int64_t> dims) {

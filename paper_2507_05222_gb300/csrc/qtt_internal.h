@@ -46,6 +46,14 @@ class Pool {
   void* get(size_t bytes);
   void put(void* p);
   size_t held() const { return held_; }
+  // CUDA-graph capture: blocks handed out while capturing form an arena owned by the graph
+  // (they are reused among themselves during the capture and never handed to anyone else
+  // afterwards); blocks from before the capture that are freed during it return to the
+  // ordinary free list only when the capture ends.  release_capture() gives the arena back
+  // once the graph is destroyed and its last replay has finished.
+  void begin_capture();
+  void end_capture();
+  void release_capture();
 
  private:
   static size_t size_class(size_t bytes);
@@ -55,6 +63,10 @@ class Pool {
   void* user_;
   std::multimap<size_t, void*> free_blocks_;  // class size -> block
   std::map<void*, size_t> live_;              // block -> class size
+  bool capturing_ = false;
+  std::multimap<size_t, void*> cap_free_;     // free blocks of the graph arena
+  std::map<void*, size_t> cap_owned_;         // every block of the graph arena
+  std::vector<void*> deferred_;
   std::vector<std::pair<void*, size_t>> chunks_;
   char* cur_ = nullptr;
   size_t cur_left_ = 0;
@@ -82,7 +94,7 @@ struct DBuf {
 enum KClass {
   KC_GEMM = 0, KC_QR = 1, KC_EIG = 2, KC_CG = 3, KC_OTHER = 4,
   // phases of the fractional step (nested around the kernels above)
-  KC_PH_APPLY = 5, KC_PH_RHS = 6, KC_PH_MOM = 7, KC_PH_POI = 8, KC_PH_PROJ = 9,
+  KC_PH_APPLY = 5, KC_PH_RHS = 6 /* with the momentum solves */, KC_PH_MOM = 7, KC_PH_POI = 8, KC_PH_PROJ = 9,
   KC_N = 10
 };
 
@@ -100,6 +112,17 @@ struct Ctx {
   Pool* pool = nullptr;
   int64_t launches = 0;
   int num_sms = 152;
+  // Worker contexts run independent parts of a step concurrently: each has its own stream
+  // and its own stream-ordered pool; `root` is the context the caller created (launch count
+  // and profiler live there).  Outputs that cross streams are allocated from the parent
+  // before fork(), so the fork event orders any earlier use of that memory.
+  Ctx* root = nullptr;
+  std::vector<Ctx*> workers;
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
+  qtt_alloc_fn alloc_fn = nullptr;
+  qtt_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
   // When non-null, GEMM / permute / reduction kernels read *guard first and return at once
   // if it is 0.  Set around the matrix-vector products of a CG solve so that iterations past
   // convergence cost only their launches (the iteration budget is fixed on the host).
@@ -108,6 +131,11 @@ struct Ctx {
 };
 
 void after_launch(Ctx& c, const char* what);
+
+Ctx& worker(Ctx& c, int i);     // i-th worker of c (created on first use)
+void fork(Ctx& c, int n);       // workers 0..n-1 wait for the work enqueued on c so far
+void join(Ctx& c, int n);       // c waits for everything enqueued on workers 0..n-1
+void destroy_workers(Ctx& c);
 
 // RAII bracket of one launch (or launch group) of class k when profiling is on.
 struct ProfScope {
@@ -195,5 +223,6 @@ void svd_small(Ctx& c, int m, int n, const double* G, double* U, double* s, doub
 // into w (n), eigenvectors as columns of V (n x n, row-major).  FP32 Jacobi in one CTA, then
 // FP64 Ogita-Aishima refinement sweeps on the tensor-free GEMM path.
 void eigh(Ctx& c, int n, const double* S, double* w, double* V);
+void init_kernel_attributes();
 
 }  // namespace qtt

@@ -434,6 +434,24 @@ __global__ void k_frob(int64_t n, const double* __restrict__ x, double* out) {
 
 }  // namespace
 
+// Set the dynamic shared-memory limits of the one-CTA kernels up front (before any stream
+// capture; they are otherwise set on first use).
+static bool g_attr_qr = false, g_attr_svd = false, g_attr_jac = false;
+void init_kernel_attributes() {
+  if (!g_attr_qr) {
+    QTT_CUDA(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    g_attr_qr = true;
+  }
+  if (!g_attr_svd) {
+    QTT_CUDA(cudaFuncSetAttribute(k_svd_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    g_attr_svd = true;
+  }
+  if (!g_attr_jac) {
+    QTT_CUDA(cudaFuncSetAttribute(k_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    g_attr_jac = true;
+  }
+}
+
 static void copy_guarded(Ctx& c, double* dst, const double* src, int64_t n, const int* guard) {
   int g = int(std::min<int64_t>((n + 255) / 256, 4096));
   k_copy_guarded<<<g, 256, 0, c.stream>>>(dst, src, n, guard);
@@ -448,11 +466,7 @@ void qr(Ctx& c, int count, int m, int n, int trans, const double* A, int64_t in_
   size_t sm = qr_smem(m, n);
   if (sm > 220 * 1024)
     throw Error(QTT_ERR_UNSUPPORTED, "qr: matrix " + std::to_string(m) + "x" + std::to_string(n) + " too large for one CTA");
-  static bool attr = false;
-  if (!attr) {
-    QTT_CUDA(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    attr = true;
-  }
+  init_kernel_attributes();
   int kk = std::min(m, n);
   ProfScope ps(c, KC_QR, double(count) * 8.0 * (double(m) * n * kk - 0.5 * (double(m) + n) * kk * kk + kk * kk * kk / 3.0));
   k_qr<<<count, 256, sm, c.stream>>>(m, n, trans, A, Q, R, in_stride, q_stride, r_stride);
@@ -464,11 +478,7 @@ void svd_small(Ctx& c, int m, int n, const double* G, double* U, double* s, doub
   QTT_CHECK_ARG(m >= n, "svd: needs m >= n");
   size_t sm = (size_t(m) * n + size_t(n) * n + n) * sizeof(double) + n * sizeof(int);
   if (sm > 220 * 1024) throw Error(QTT_ERR_UNSUPPORTED, "svd: matrix too large for one CTA");
-  static bool attr = false;
-  if (!attr) {
-    QTT_CUDA(cudaFuncSetAttribute(k_svd_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    attr = true;
-  }
+  init_kernel_attributes();
   k_svd_jacobi<<<1, 256, sm, c.stream>>>(m, n, G, U, s, V, 60);
   after_launch(c, "svd_jacobi");
 }
@@ -504,11 +514,7 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
   QTT_CHECK_ARG(n >= 1, "eigh: n >= 1");
   if (n > 160) throw Error(QTT_ERR_UNSUPPORTED, "eigh: n > 160 not supported");
   size_t smf = (size_t(n) * (n + 1) * 2 + 2 * ((n + 2) / 2)) * sizeof(float) + 2 * ((n + 2) / 2) * sizeof(int);
-  static bool attr = false;
-  if (!attr) {
-    QTT_CUDA(cudaFuncSetAttribute(k_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    attr = true;
-  }
+  init_kernel_attributes();
   const size_t nn = size_t(n) * n;
   DBuf X(&c, nn), Xs(&c, nn), XtX(&c, nn), AX(&c, nn), SX(&c, nn), E(&c, nn), Y(&c, nn), lam(&c, size_t(n)),
       an(&c, 1), flags(&c, 2), part(&c, 2 * OA_BLOCKS);

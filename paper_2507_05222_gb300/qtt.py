@@ -109,6 +109,7 @@ _SIGS = {
     "qtt_case_get_vector": (I, [P, I, C.POINTER(P)]),
     "fractional_step": (I, [P, P, I, I, C.POINTER(qtt_step_info)]),
     "qtt_case_forces": (I, [P, P, DP, DP]),
+    "qtt_case_use_graph": (I, [P, I]),
     "qtt_strouhal": (I, [DP, DP, I, DP]),
 }
 
@@ -188,7 +189,7 @@ class Context:
         return int(lib().qtt_ctx_pool_bytes(self.h))
 
     PROFILE_CLASSES = ("gemm_f64", "qr_f64", "eig_jacobi", "cg_update", "other",
-                       "phase_apply", "phase_rhs_fit", "phase_momentum", "phase_poisson", "phase_projection")
+                       "phase_apply", "phase_rhs_and_momentum", "phase_unused", "phase_poisson", "phase_projection")
 
     def profile(self, on: bool):
         """Read and reset the per-class kernel timing; switch recording on/off."""
@@ -457,6 +458,9 @@ class Case:
 
     def fractional_step(self, nsteps: int = 1, with_forces: bool = False):
         return fractional_step(self.ctx, self, nsteps, with_forces)
+
+    def use_graph(self, enable: bool):
+        _check(lib().qtt_case_use_graph(self.h, 1 if enable else 0))
 
     def forces(self):
         cd, cl = C.c_double(), C.c_double()

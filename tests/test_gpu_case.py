@@ -138,3 +138,25 @@ def test_multi_step_truncated_parity(ctx):
     print("per-step max rel diff:", errs)
     assert errs[0] < 1e-8
     assert max(errs) < 1e-6
+
+
+def test_graph_replay_equals_eager(ctx):
+    """The captured-graph step (default) and kernel-by-kernel launching give identical states
+    (same kernels, deterministic reductions), also after set_state re-captures."""
+    from paper_2507_05222_gb300 import qtt
+    ne = nx = 5
+    R, Re, dt, chi = 40.0, 100.0, 2e-3, 16
+    ops = Q.Ops(ne, nx, R, Re, dt, "interleaved")
+    _, (gu, gv, gp), _ = make_state(ctx, ops, ne, nx, chi)
+    out = []
+    for graph in (True, False, True):
+        case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=1, mom=(1, 8, 1e-12),
+                        poi=(2, 20, 1e-12))
+        case.use_graph(graph)
+        case.set_state(gu, gv, gp)
+        info = case.fractional_step(3, with_forces=True)
+        out.append(([qtt.qtt_decode(ctx, x) for x in case.get_state()], info))
+    for (a, ia), (b, ib) in ((out[0], out[1]), (out[2], out[1])):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+        assert ia == ib
