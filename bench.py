@@ -186,6 +186,7 @@ def run_ours(args, cfg):
             ev[k][1].record(stream)
     torch.cuda.synchronize()
     launches = ctx.kernel_launches() - n0
+    phases = case.phase_ms()
     ms = [a.elapsed_time(b) for a, b in ev]
     clk = clocks.stop()
     step_ms = sum(ms) / len(ms)
@@ -243,7 +244,8 @@ def run_ours(args, cfg):
                              "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                              "kernel": "k_gemm (FP64 core contractions)",
                              "share_of_step": g["ms"] / nprof / step_ms if step_ms > 0 else None},
-                "kernel_classes_ms_per_step": {k: v["ms"] / nprof for k, v in prof.items()},
+                "kernel_classes_ms_per_step": {k: v["ms"] / nprof for k, v in prof.items() if not k.startswith("phase")},
+                "phase_ms_last_timed_step": phases,
                 "clocks": clk, "cpu_baseline": cpu,
                 "last_step": {"cd": info[0]["cd"], "cl": info[0]["cl"]}}
         print(json.dumps(line))

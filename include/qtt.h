@@ -254,6 +254,9 @@ int fractional_step(qtt_ctx* ctx, qtt_case* c, int nsteps, int with_forces,
  * and every step replays it; the graph is dropped when the state is set again.  enable = 0:
  * every step is launched kernel by kernel (same kernels, same results). */
 int qtt_case_use_graph(qtt_case* c, int enable);
+/* Wall time (ms) of the phases of the last step, in order: MPO-MPS products, right-hand
+ * sides with the momentum solves, Poisson solve, projection.  Synchronous. */
+int qtt_case_phase_ms(qtt_case* c, double* ms4);
 /* Drag and lift of the current state (App. F; synchronous). */
 int qtt_case_forces(qtt_ctx* ctx, qtt_case* c, double* cd, double* cl);
 /* Strouhal number from upward zero crossings of C_L(t) (eq:st); host-only arithmetic on a

@@ -643,6 +643,20 @@ int fractional_step(qtt_ctx* ctx, qtt_case* h, int nsteps, int with_forces, qtt_
   API_END
 }
 
+int qtt_case_phase_ms(qtt_case* h, double* ms4) {
+  API_BEGIN
+  QTT_CHECK_ARG(h && ms4, "case_phase_ms: null argument");
+  Case& cs = *h->cs;
+  QTT_CHECK_ARG(cs.ph_ev[4] != nullptr, "case_phase_ms: no step has run");
+  QTT_CUDA(cudaEventSynchronize(cs.ph_ev[4]));
+  for (int i = 0; i < 4; ++i) {
+    float t = 0.f;
+    QTT_CUDA(cudaEventElapsedTime(&t, cs.ph_ev[i], cs.ph_ev[i + 1]));
+    ms4[i] = t;
+  }
+  API_END
+}
+
 int qtt_case_use_graph(qtt_case* h, int enable) {
   API_BEGIN
   QTT_CHECK_ARG(h, "case_use_graph: null case");

@@ -317,6 +317,12 @@ qtt_mps* add_round(Ctx& c, const qtt_mps* a, const qtt_mps* b) {
 
 // ------------------------------------------------------------------ case
 
+void Case::mark(Ctx& c, int i) {
+  if (!ph_ev[i]) QTT_CUDA(cudaEventCreate(&ph_ev[i]));
+  if (capturing) QTT_CUDA(cudaEventRecordWithFlags(ph_ev[i], c.stream, cudaEventRecordExternal));
+  else QTT_CUDA(cudaEventRecord(ph_ev[i], c.stream));
+}
+
 void Case::drop_graph() {
   if (gexec || graph) {
     if (gstream) cudaStreamSynchronize(gstream);
@@ -336,6 +342,8 @@ Case::~Case() {
   if (gstream) cudaStreamDestroy(gstream);
   if (ev_in) cudaEventDestroy(ev_in);
   if (ev_out) cudaEventDestroy(ev_out);
+  for (auto& e : ph_ev)
+    if (e) cudaEventDestroy(e);
   if (rec) cudaFree(rec);
   for (qtt_mpo* m : {Dx, Dz, Dxp, Dzp, H, Ap, Px, Pz, Jdiag})
     if (m) free_mpo(m);
@@ -567,6 +575,7 @@ void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
   const double dt = P.dt;
   const int n = cs.u->n;
   // (i) convective derivatives (MPO-MPS products rounded to chi, Sec. II.A.2)
+  cs.mark(c, 0);
   std::unique_ptr<ProfScope> ph(new ProfScope(c, KC_PH_APPLY));
   MpsP dxu = mk(new_mps(&c, n, 2, apply_bonds(cs.Dx, cs.u, chi)));
   MpsP dzu = mk(new_mps(&c, n, 2, apply_bonds(cs.Dz, cs.u, chi)));
@@ -578,6 +587,7 @@ void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
   apply_round_gram(worker(c, 2), cs.Dx, cs.v, chi, 0.0, dxv.get());
   apply_round_gram(worker(c, 3), cs.Dz, cs.v, chi, 0.0, dzv.get());
   join(c, 4);
+  cs.mark(c, 1);
   // explicit right-hand sides (eq:intermediate_vel_eq), one fit each, warm start u (v), then
   // (ii) implicit momentum H v* = |J| (.) rhs + dt/Re |J| bcLap (ALS, warm start v^m)
   ph.reset(new ProfScope(c, KC_PH_RHS));
@@ -602,12 +612,14 @@ void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
   als(worker(c, 0), cs.H, mu, us.get(), P.mom.sweeps, P.mom.cg_iters, P.mom.cg_tol, true, cg_dev ? cg_dev + 0 : nullptr);
   als(worker(c, 1), cs.H, mv, vs.get(), P.mom.sweeps, P.mom.cg_iters, P.mom.cg_tol, true, cg_dev ? cg_dev + 1 : nullptr);
   join(c, 2);
+  cs.mark(c, 2);
   // (iii) pressure Poisson, J-weighted (Sec. III.C): (-|J| Lap_h^p) p = -|J| (.) div(v*) / dt
   ph.reset(new ProfScope(c, KC_PH_POI));
   std::vector<Term> pr = {Term::mpo(1.0, cs.Px, us.get()), Term::mpo(1.0, cs.Pz, vs.get())};
   if (cs.bcdiv_w) pr.push_back(Term::vec(1.0, cs.bcdiv_w));
   als(c, cs.Ap, pr, cs.p, P.poi.sweeps, P.poi.cg_iters, P.poi.cg_tol, true, cg_dev ? cg_dev + 2 : nullptr);
   // projection v = v* - dt grad_h p (one fit each, warm start v*)
+  cs.mark(c, 3);
   ph.reset(new ProfScope(c, KC_PH_PROJ));
   MpsP un = mk(mps_copy(c, us.get()));
   MpsP vn = mk(mps_copy(c, vs.get()));
@@ -616,6 +628,7 @@ void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
   fit(worker(c, 1), {Term::vec(1.0, vs.get()), Term::mpo(-dt, cs.Dzp, cs.p)}, vn.get(), P.fit_sweeps, true);
   join(c, 2);
   ph.reset();
+  cs.mark(c, 4);
   // new state into the same buffers (the captured graph reads and writes these addresses)
   copy(c, cs.u->buf.p, un->buf.p, cs.u->off[n]);
   copy(c, cs.v->buf.p, vn->buf.p, cs.v->off[n]);
@@ -637,11 +650,15 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
   for (Ctx* w : c.workers) w->pool->begin_capture();
   c.stream = cs.gstream;
   const int64_t n0 = c.root->launches;
+  for (int i = 0; i < 5; ++i)
+    if (!cs.ph_ev[i]) QTT_CUDA(cudaEventCreate(&cs.ph_ev[i]));
+  cs.capturing = true;
   cudaError_t err = cudaStreamBeginCapture(cs.gstream, cudaStreamCaptureModeRelaxed);
   try {
     if (err != cudaSuccess) throw Error(QTT_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(err));
     step(c, cs, reinterpret_cast<int*>(cs.rec), with_forces ? cs.rec + 2 : nullptr);
   } catch (...) {
+    cs.capturing = false;
     cudaGraph_t g = nullptr;
     cudaStreamEndCapture(cs.gstream, &g);
     if (g) cudaGraphDestroy(g);
@@ -653,6 +670,7 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
     throw;
   }
   err = cudaStreamEndCapture(cs.gstream, &cs.graph);
+  cs.capturing = false;
   c.stream = saved;
   c.pool->end_capture();
   for (Ctx* w : c.workers) w->pool->end_capture();

@@ -30,6 +30,12 @@ struct Case {
   bool graph_forces = false;
   int64_t graph_launches = 0;
   double* rec = nullptr;        // 4 doubles of device memory (allocated with cudaMalloc once)
+  // Phase boundaries of the last step (timing events; external event nodes inside the graph):
+  // start, after the MPO-MPS products, after the right sides + momentum, after the Poisson
+  // solve, after the projection.
+  cudaEvent_t ph_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool capturing = false;
+  void mark(Ctx& c, int i);
   Ctx* ctx = nullptr;
   void drop_graph();
   ~Case();

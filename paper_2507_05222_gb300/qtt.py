@@ -110,6 +110,7 @@ _SIGS = {
     "fractional_step": (I, [P, P, I, I, C.POINTER(qtt_step_info)]),
     "qtt_case_forces": (I, [P, P, DP, DP]),
     "qtt_case_use_graph": (I, [P, I]),
+    "qtt_case_phase_ms": (I, [P, DP]),
     "qtt_strouhal": (I, [DP, DP, I, DP]),
 }
 
@@ -458,6 +459,12 @@ class Case:
 
     def fractional_step(self, nsteps: int = 1, with_forces: bool = False):
         return fractional_step(self.ctx, self, nsteps, with_forces)
+
+    def phase_ms(self):
+        """Wall time (ms) of the last step's phases: apply, rhs+momentum, Poisson, projection."""
+        out = np.zeros(4)
+        _check(lib().qtt_case_phase_ms(self.h, _dp(out)))
+        return dict(zip(("apply", "rhs_and_momentum", "poisson", "projection"), out.tolist()))
 
     def use_graph(self, enable: bool):
         _check(lib().qtt_case_use_graph(self.h, 1 if enable else 0))
