@@ -157,6 +157,22 @@ def run_ours(args, cfg):
         ctx.sync()
         qtt.profiler_range(False)
         return
+    if args.phase_breakdown:
+        # kernel-class time by step phase, kernels launched one by one (eager), next to the
+        # phase wall times of a replayed graph step
+        for _ in range(2):
+            qtt.fractional_step(ctx, case, 1, info=False)
+        ctx.sync()
+        graph_phases = case.phase_ms()
+        case.use_graph(False)
+        qtt.fractional_step(ctx, case, 1, info=False)
+        ctx.sync()
+        ctx.profile(True)
+        qtt.fractional_step(ctx, case, 1, info=False)
+        ctx.profile(False)
+        print(json.dumps({"graph_phase_ms": graph_phases, "eager_phase_ms": case.phase_ms(),
+                          "eager_kernel_ms_by_phase": ctx.profile_phases()}))
+        return
     if args.profile_one_step:
         qtt.fractional_step(ctx, case, 1, info=False)
         ctx.sync()
@@ -264,6 +280,8 @@ def main():
     ap.add_argument("--chi", type=int, default=None)
     ap.add_argument("--profile-one-step", action="store_true",
                     help="set up, one warm-up step, then one step between cudaProfilerStart/Stop (for ncu)")
+    ap.add_argument("--phase-breakdown", action="store_true",
+                    help="print kernel-class time by step phase (diagnostic; no bench line)")
     ap.add_argument("--kernel-probe", action="store_true",
                     help="set up, then one D_x u product with rounding between cudaProfilerStart/Stop (for ncu)")
     args = ap.parse_args()

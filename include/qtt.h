@@ -118,6 +118,11 @@ size_t qtt_ctx_pool_bytes(qtt_ctx* ctx);
  * them, and turns event recording on (on != 0) or off.  Events are recorded on the context
  * stream around each launch (or phase) of a timed class. */
 int qtt_ctx_profile(qtt_ctx* ctx, int on, double* ms_out, double* flops_out, int64_t* launches_out);
+/* The kernel-class times of the last qtt_ctx_profile read-out split by step phase:
+ * ms_out[6 * 5] (row i = phase i of the fractional step -- MPO-MPS products, right-hand sides
+ * with momentum, unused, Poisson, projection -- row 5 = outside any phase; column k = kernel
+ * class k), and launches_out[6] (kernel launches enqueued in each row).  Either may be NULL. */
+int qtt_ctx_profile_phases(qtt_ctx* ctx, double* ms_out, int64_t* launches_out);
 
 /* ------------------------------------------------------------------------ MPS and MPO */
 
@@ -200,6 +205,15 @@ int mps_dot_noalloc(int n, int d, const int* a_bonds, const double* a_cores, con
  * symmetric), w (n, descending) and V (n x n row-major, eigenvectors as columns) are host
  * buffers owned by the caller; synchronous. */
 int qtt_sym_eig(qtt_ctx* ctx, int n, const double* S, double* w, double* V);
+/* Householder QR of a small dense matrix, the gauge move of every fit and ALS sweep (the QR
+ * of a core's unfolding, Sec. II.A.4): A (m x n) = Q (m x kk) R (kk x n), kk = min(m, n),
+ * R upper triangular with R_jj = -sign(alpha_j) ||x_j|| (the LAPACK convention).  trans = 0:
+ * A is row-major m x n and Q is returned row-major m x kk; trans = 1: the buffer holds A^T
+ * (row-major n x m) and Q^T (kk x m) is returned.  path 0 picks the kernel (cluster QR over up
+ * to 16 CTAs for m >= n >= 16, else one CTA), 1 forces one CTA, 2 forces the cluster kernel
+ * (QTT_ERR_UNSUPPORTED if the shape does not allow it).  Host buffers; R may be NULL;
+ * synchronous. */
+int qtt_qr(qtt_ctx* ctx, int m, int n, int trans, const double* A, double* Q, double* R, int path);
 /* <a, b> into *out_host (synchronous). */
 int mps_dot(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, double* out_host);
 

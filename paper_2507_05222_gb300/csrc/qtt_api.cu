@@ -1,5 +1,6 @@
 // extern "C" entry points of include/qtt.h: argument checks, error translation, handle
 // management.  No C++ exception crosses this file's functions.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -136,8 +137,8 @@ void qtt_ctx_destroy(qtt_ctx* ctx) {
   for (auto e : c->prof.free_events) cudaEventDestroy(e);
   for (int k = 0; k < KC_N; ++k)
     for (auto& pr : c->prof.pending[k]) {
-      cudaEventDestroy(pr.first);
-      cudaEventDestroy(pr.second);
+      cudaEventDestroy(pr.e0);
+      cudaEventDestroy(pr.e1);
     }
   delete c->pool;
   delete c;
@@ -168,23 +169,44 @@ int qtt_ctx_profile(qtt_ctx* ctx, int on, double* ms_out, double* flops_out, int
   QTT_CHECK_ARG(ctx, "ctx is null");
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   QTT_CUDA(cudaStreamSynchronize(c.stream));
+  Profiler& P = c.prof;
+  for (auto& row : P.phase_ms)
+    for (double& v : row) v = 0.0;
   for (int k = 0; k < KC_N; ++k) {
     double ms = 0.0;
-    for (auto& pr : c.prof.pending[k]) {
+    for (auto& sp : P.pending[k]) {
       float t = 0.f;
-      QTT_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+      QTT_CUDA(cudaEventElapsedTime(&t, sp.e0, sp.e1));
       ms += t;
-      c.prof.free_events.push_back(pr.first);
-      c.prof.free_events.push_back(pr.second);
+      if (k < KC_KERNEL_CLASSES) P.phase_ms[sp.phase < 0 ? KC_PHASES : sp.phase][k] += t;
+      P.free_events.push_back(sp.e0);
+      P.free_events.push_back(sp.e1);
     }
-    c.prof.pending[k].clear();
+    P.pending[k].clear();
     if (ms_out) ms_out[k] = ms;
-    if (flops_out) flops_out[k] = c.prof.flops[k];
-    if (launches_out) launches_out[k] = c.prof.launches[k];
-    c.prof.flops[k] = 0.0;
-    c.prof.launches[k] = 0;
+    if (flops_out) flops_out[k] = P.flops[k];
+    if (launches_out) launches_out[k] = P.launches[k];
+    P.flops[k] = 0.0;
+    P.launches[k] = 0;
   }
-  c.prof.on = on != 0;
+  for (int i = 0; i <= KC_PHASES; ++i) {
+    P.phase_launches[i] = P.acc_phase_launches[i];
+    P.acc_phase_launches[i] = 0;
+  }
+  P.phase = -1;
+  P.on = on != 0;
+  API_END
+}
+
+int qtt_ctx_profile_phases(qtt_ctx* ctx, double* ms_out, int64_t* launches_out) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx, "ctx is null");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  for (int i = 0; i <= KC_PHASES; ++i) {
+    for (int k = 0; k < KC_KERNEL_CLASSES; ++k)
+      if (ms_out) ms_out[i * KC_KERNEL_CLASSES + k] = c.prof.phase_ms[i][k];
+    if (launches_out) launches_out[i] = c.prof.phase_launches[i];
+  }
   API_END
 }
 
@@ -461,6 +483,23 @@ int qtt_sym_eig(qtt_ctx* ctx, int n, const double* S, double* w, double* V) {
   eigh(c, n, dS.p, dw.p, dV.p);
   QTT_CUDA(cudaMemcpyAsync(w, dw.p, n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   QTT_CUDA(cudaMemcpyAsync(V, dV.p, nn * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  API_END
+}
+
+int qtt_qr(qtt_ctx* ctx, int m, int n, int trans, const double* A, double* Q, double* R, int path) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && A && Q, "qr: null argument");
+  QTT_CHECK_ARG(m >= 1 && n >= 1 && int64_t(m) * n <= (int64_t(1) << 22), "qr: m, n >= 1 and m n <= 2^22");
+  QTT_CHECK_ARG(path >= 0 && path <= 2, "qr: path must be 0, 1 or 2");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  const int kk = std::min(m, n);
+  const size_t mn = size_t(m) * n;
+  DBuf dA(&c, mn), dQ(&c, size_t(m) * kk), dR(&c, size_t(kk) * n);
+  QTT_CUDA(cudaMemcpyAsync(dA.p, A, mn * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  qr(c, 1, m, n, trans, dA.p, 0, dQ.p, 0, R ? dR.p : nullptr, 0, path);
+  QTT_CUDA(cudaMemcpyAsync(Q, dQ.p, size_t(m) * kk * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  if (R) QTT_CUDA(cudaMemcpyAsync(R, dR.p, size_t(kk) * n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   QTT_CUDA(cudaStreamSynchronize(c.stream));
   API_END
 }

@@ -149,6 +149,8 @@ void DBuf::reset(Ctx* c, size_t count) {
 
 void after_launch(Ctx& c, const char* what) {
   c.root->launches += 1;
+  Profiler& pr = c.root->prof;
+  if (pr.on) pr.acc_phase_launches[pr.phase < 0 ? KC_PHASES : pr.phase] += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw Error(QTT_ERR_CUDA, std::string("launch of ") + what + ": " + cudaGetErrorString(e));
 }
@@ -170,15 +172,19 @@ ProfScope::ProfScope(Ctx& ctx, int kclass, double flops) : c(ctx), k(kclass) {
   if (!pr.on) return;
   pr.flops[k] += flops;
   pr.launches[k] += 1;
+  if (k >= KC_PH_APPLY) pr.phase = k - KC_PH_APPLY;
   e0 = take_event(c);
   cudaEventRecord(e0, c.stream);
 }
 
 ProfScope::~ProfScope() {
   if (!e0) return;
+  Profiler& pr = c.root->prof;
   cudaEvent_t e1 = take_event(c);
   cudaEventRecord(e1, c.stream);
-  c.root->prof.pending[k].push_back({e0, e1});
+  pr.pending[k].push_back({e0, e1, pr.phase});
+  // phase scopes are replaced by constructing the next one first: close only our own phase
+  if (k >= KC_PH_APPLY && pr.phase == k - KC_PH_APPLY) pr.phase = -1;
 }
 
 Ctx& worker(Ctx& c, int i) {

@@ -98,12 +98,25 @@ enum KClass {
   KC_N = 10
 };
 
+constexpr int KC_KERNEL_CLASSES = KC_PH_APPLY;       // classes 0..4 are kernel classes
+constexpr int KC_PHASES = KC_N - KC_PH_APPLY;         // classes 5..9 are step phases
+
 struct Profiler {
+  struct Span {
+    cudaEvent_t e0, e1;
+    int phase;  // step phase open when the span was enqueued (-1: none)
+  };
   bool on = false;
+  int phase = -1;
   std::vector<cudaEvent_t> free_events;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[KC_N];
+  std::vector<Span> pending[KC_N];
   double flops[KC_N] = {0};
   int64_t launches[KC_N] = {0};
+  // Kernel-class time (ms) and launch counts split by step phase, filled by the last
+  // read-out; row KC_PHASES collects what ran outside any phase.
+  double phase_ms[KC_PHASES + 1][KC_KERNEL_CLASSES] = {};
+  int64_t phase_launches[KC_PHASES + 1] = {0};
+  int64_t acc_phase_launches[KC_PHASES + 1] = {0};
 };
 
 struct Ctx {
@@ -214,8 +227,9 @@ void dot(Ctx& c, int64_t n, const double* x, const double* y, double* out_dev);
 
 // Householder QR of `count` matrices (strided): A (m x n) = Q (m x kk) R (kk x n), kk = min(m,n).
 // trans = 1: the buffer holds A^T (n x m row-major) and Q^T (kk x m) is written.
+// path: 0 = cluster QR when the shape allows it, else one CTA; 1 = one CTA; 2 = cluster only.
 void qr(Ctx& c, int count, int m, int n, int trans, const double* A, int64_t in_stride, double* Q, int64_t q_stride,
-        double* R, int64_t r_stride);
+        double* R, int64_t r_stride, int path = 0);
 // Accurate (one-sided Jacobi, FP64) SVD of a small m x n matrix, m >= n: U (m x n), s, V (n x n).
 void svd_small(Ctx& c, int m, int n, const double* G, double* U, double* s, double* V);
 

@@ -1,7 +1,10 @@
 // Small dense factorisations for the QTT sweeps, one CTA per matrix, operands in shared
 // memory:
 //   * Householder QR in FP64 (gauge moves of the fit and ALS sweeps; the orthogonalisation
-//     sweep of the accurate rounding);
+//     sweep of the accurate rounding), blocked and spread over a thread-block cluster of up
+//     to 16 CTAs (one SM of GB300 retires only 2 FP64 FMAs per cycle, so a one-CTA QR of a
+//     128 x 64 unfolding is bound at ~0.2 ms by that SM's FP64 pipe), one CTA for small or
+//     wide matrices;
 //   * one-sided (Hestenes) Jacobi SVD in FP64 for small accurate roundings (operator set-up,
 //     rel_tol > 0);
 //   * symmetric eigendecomposition: cyclic parallel Jacobi in FP32 (the FP32 pipe of GB300 is
@@ -9,10 +12,14 @@
 //     Ogita-Aishima iteration (Ogita & Aishima, Japan J. Indust. Appl. Math. 35, 2018), whose
 //     matrix products run on the FP64 GEMM path across many SMs.
 // Every loop has a fixed upper bound; no kernel waits on another.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 
 #include "qtt_internal.h"
+
+namespace cgrp = cooperative_groups;
 
 namespace qtt {
 
@@ -124,6 +131,217 @@ __global__ void __launch_bounds__(256) k_qr(int m, int n, int trans, const doubl
     if (trans) Q[e] = S[e];                      // Q^T row-major (kk x m)
     else Q[e] = S[(e % kk) * m + e / kk];        // Q row-major (m x kk)
   }
+}
+
+// ------------------------------------------------------------------ cluster Householder QR (FP64)
+// Same factorisation and conventions as k_qr (beta = -sign(alpha) ||x||, unit-diagonal
+// reflectors, thin Q), for m >= n, organised as a blocked right-looking QR over a cluster of
+// cs CTAs.  CTA q owns columns [q nb, q nb + nb) and holds them in shared memory for the
+// whole factorisation; panel p is CTA p's column block.
+//   R phase, for p = 0 .. cs-1: CTA p factors its (already updated) panel with one warp and
+//     forms the compact-WY factor T_p (H_{j0} ... H_{j0+w-1} = I - V_p T_p V_p^T); after a
+//     cluster barrier every CTA q > p reads V_p and T_p from CTA p's shared memory (DSMEM)
+//     and updates its columns, A_q <- (I - V_p T_p^T V_p^T) A_q.
+//   Q phase: column block q of Q = H_0 ... H_{n-1} [I; 0] only sees panels p <= q, so each CTA
+//     accumulates its own columns of Q backwards from the final V_p, T_p with no further
+//     synchronisation; a last cluster barrier keeps every CTA's shared memory alive until the
+//     others have read it.
+// Shared layout (doubles): Acol | Qcol | Vb (m x nb each, column-major) | T | Tb | W | W2
+// (nb x nb each) | tau (nb).
+constexpr int QRC_THREADS = 256;
+
+__host__ __device__ constexpr size_t qrc_smem_doubles(int m, int nb) {
+  return size_t(3) * m * nb + 4 * size_t(nb) * nb + nb;
+}
+
+// X(i, c) (i >= j0, c < ncols, column-major with leading dimension m) <- (I - V op(T) V^T) X,
+// op(T) = T^T when transT, else T.  V: m x wp (rows >= j0 valid), T: wp x wp upper triangular
+// with leading dimension nb.  Called by every thread of the CTA; ends with a CTA barrier.
+__device__ void qrc_apply_block(int m, int nb, int j0, int wp, int ncols, const double* V, const double* T, bool transT,
+                                double* X, double* W, double* W2) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nd = wp * ncols;
+  int g = 32;
+  while (g > 1 && g * nd > nt) g >>= 1;
+  {
+    const int dd = tid / g, gl = tid % g;
+    double s = 0.0;
+    if (dd < nd) {
+      const int l = dd / ncols, c = dd % ncols;
+      const double* vl = V + size_t(l) * m;
+      const double* xc = X + size_t(c) * m;
+      for (int i = j0 + gl; i < m; i += g) s += vl[i] * xc[i];
+    }
+    for (int o = g >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (dd < nd && gl == 0) W[dd] = s;
+  }
+  __syncthreads();
+  if (tid < nd) {
+    const int l = tid / ncols, c = tid % ncols;
+    double s = 0.0;
+    if (transT) {
+      for (int l2 = 0; l2 <= l; ++l2) s += T[l2 * nb + l] * W[l2 * ncols + c];
+    } else {
+      for (int l2 = l; l2 < wp; ++l2) s += T[l * nb + l2] * W[l2 * ncols + c];
+    }
+    W2[tid] = s;
+  }
+  __syncthreads();
+  const int mr = m - j0;
+  for (int e = tid; e < mr * ncols; e += nt) {
+    const int c = e / mr, i = j0 + e % mr;
+    double s = 0.0;
+    for (int l = 0; l < wp; ++l) s += V[size_t(l) * m + i] * W2[l * ncols + c];
+    X[size_t(c) * m + i] -= s;
+  }
+  __syncthreads();
+}
+
+// Copy panel p's reflectors (unit diagonal, zeros above, from the factored columns src) and
+// its T into the local buffers Vb, Tb.  Ends with a CTA barrier.
+__device__ void qrc_fetch_panel(int m, int nb, int j0, int wp, const double* src, const double* srcT, double* Vb,
+                                double* Tb) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int mr = m - j0;
+  for (int e = tid; e < mr * wp; e += nt) {
+    const int l = e / mr, i = j0 + e % mr;
+    const int diag = j0 + l;
+    Vb[size_t(l) * m + i] = (i < diag) ? 0.0 : (i == diag ? 1.0 : src[size_t(l) * m + i]);
+  }
+  for (int e = tid; e < wp * nb; e += nt) Tb[e] = srcT[e];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(int m, int n, int nb, int trans, const double* __restrict__ Ain,
+                                                           double* Qall, double* __restrict__ Rall, int64_t in_stride,
+                                                           int64_t q_stride, int64_t r_stride) {
+  cgrp::cluster_group cl = cgrp::this_cluster();
+  const int cs = int(cl.num_blocks());
+  const int q = int(cl.block_rank());
+  const int mat = blockIdx.x / cs;
+  extern __shared__ double sm[];
+  double* Acol = sm;
+  double* Qcol = Acol + size_t(m) * nb;
+  double* Vb = Qcol + size_t(m) * nb;
+  double* T = Vb + size_t(m) * nb;
+  double* Tb = T + nb * nb;
+  double* W = Tb + nb * nb;
+  double* W2 = W + nb * nb;
+  double* tau = W2 + nb * nb;
+  const double* A = Ain + mat * in_stride;
+  double* Q = Qall + mat * q_stride;
+  double* R = Rall ? Rall + mat * r_stride : nullptr;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = q * nb;
+  const int w = max(0, min(nb, n - c0));
+  for (int e = tid; e < m * w; e += nt) {
+    if (trans) {
+      const int c = e / m, i = e % m;
+      Acol[size_t(c) * m + i] = A[int64_t(c0 + c) * m + i];
+    } else {
+      const int i = e / w, c = e % w;
+      Acol[size_t(c) * m + i] = A[int64_t(i) * n + c0 + c];
+    }
+  }
+  for (int e = tid; e < nb * nb; e += nt) T[e] = 0.0;
+  __syncthreads();
+
+  // ---- R phase
+  for (int p = 0; p < cs; ++p) {
+    const int j0 = p * nb;
+    const int wp = max(0, min(nb, n - j0));
+    if (p == q && warp == 0) {
+      for (int j = 0; j < w; ++j) {
+        const int r = j0 + j;
+        double* x = Acol + size_t(j) * m;
+        double part = 0.0;
+        for (int i = r + 1 + lane; i < m; i += 32) part += x[i] * x[i];
+        const double sigma = warp_sum(part);
+        const double alpha = x[r];
+        double beta, t, scale;
+        if (sigma == 0.0) {
+          t = 0.0; beta = alpha; scale = 0.0;
+        } else {
+          const double nrm = sqrt(alpha * alpha + sigma);
+          beta = alpha >= 0.0 ? -nrm : nrm;
+          t = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+        __syncwarp();
+        for (int i = r + 1 + lane; i < m; i += 32) x[i] *= scale;
+        if (lane == 0) {
+          x[r] = beta;
+          tau[j] = t;
+        }
+        __syncwarp();
+        for (int jj = j + 1; jj < w; ++jj) {
+          double* y = Acol + size_t(jj) * m;
+          double sdot = 0.0;
+          for (int i = r + 1 + lane; i < m; i += 32) sdot += x[i] * y[i];
+          sdot = (warp_sum(sdot) + y[r]) * t;
+          __syncwarp();
+          if (lane == 0) y[r] -= sdot;
+          for (int i = r + 1 + lane; i < m; i += 32) y[i] -= sdot * x[i];
+          __syncwarp();
+        }
+      }
+      // T: T_ii = tau_i, T_{0:i, i} = -tau_i T_{0:i, 0:i} (V_{:, 0:i}^T v_i)
+      for (int i = 0; i < w; ++i) {
+        const double* vi = Acol + size_t(i) * m;
+        for (int l = 0; l < i; ++l) {
+          const double* vl = Acol + size_t(l) * m;
+          double sdot = 0.0;
+          for (int row = j0 + i + 1 + lane; row < m; row += 32) sdot += vl[row] * vi[row];
+          sdot = warp_sum(sdot) + vl[j0 + i];
+          if (lane == 0) W[l] = sdot;
+        }
+        __syncwarp();
+        if (lane < i) {
+          double sacc = 0.0;
+          for (int l2 = lane; l2 < i; ++l2) sacc += T[lane * nb + l2] * W[l2];
+          T[lane * nb + i] = -tau[i] * sacc;
+        }
+        if (lane == 0) T[i * nb + i] = tau[i];
+        __syncwarp();
+      }
+    }
+    cl.sync();
+    if (q > p) {
+      qrc_fetch_panel(m, nb, j0, wp, cl.map_shared_rank(Acol, p), cl.map_shared_rank(T, p), Vb, Tb);
+      qrc_apply_block(m, nb, j0, wp, w, Vb, Tb, true, Acol, W, W2);
+    }
+  }
+  if (R) {
+    for (int e = tid; e < n * w; e += nt) {
+      const int r = e / w, c = e % w;
+      R[int64_t(r) * n + c0 + c] = (r <= c0 + c) ? Acol[size_t(c) * m + r] : 0.0;
+    }
+  }
+
+  // ---- Q phase: own columns of H_0 ... H_{n-1} [I; 0], panels q, q-1, ..., 0
+  for (int e = tid; e < m * w; e += nt) {
+    const int c = e / m, i = e % m;
+    Qcol[size_t(c) * m + i] = (i == c0 + c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int p = q; p >= 0; --p) {
+    const int j0 = p * nb;
+    const int wp = max(0, min(nb, n - j0));
+    const double* srcA = (p == q) ? Acol : cl.map_shared_rank(Acol, p);
+    const double* srcT = (p == q) ? T : cl.map_shared_rank(T, p);
+    qrc_fetch_panel(m, nb, j0, wp, srcA, srcT, Vb, Tb);
+    qrc_apply_block(m, nb, j0, wp, w, Vb, Tb, false, Qcol, W, W2);
+  }
+  for (int e = tid; e < m * w; e += nt) {
+    if (trans) {
+      const int c = e / m, i = e % m;
+      Q[int64_t(c0 + c) * m + i] = Qcol[size_t(c) * m + i];   // Q^T row-major (n x m)
+    } else {
+      const int i = e / w, c = e % w;
+      Q[int64_t(i) * n + c0 + c] = Qcol[size_t(c) * m + i];   // Q row-major (m x n)
+    }
+  }
+  cl.sync();
 }
 
 // ------------------------------------------------------------------ one-sided Jacobi SVD (FP64)
@@ -437,9 +655,32 @@ __global__ void k_frob(int64_t n, const double* __restrict__ x, double* out) {
 // Set the dynamic shared-memory limits of the one-CTA kernels up front (before any stream
 // capture; they are otherwise set on first use).
 static bool g_attr_qr = false, g_attr_svd = false, g_attr_jac = false;
+static int g_qr_max_cluster = 0;  // largest cluster the cluster QR may use (0: none)
+constexpr size_t QRC_SMEM_LIMIT = 200 * 1024;
 void init_kernel_attributes() {
   if (!g_attr_qr) {
     QTT_CUDA(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    QTT_CUDA(cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, int(QRC_SMEM_LIMIT)));
+    // 16-CTA clusters are beyond the portable size 8: ask for them, keep them only if a
+    // 16-CTA cluster of the largest shared-memory footprint can be resident.
+    g_qr_max_cluster = 8;
+    if (cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(QRC_THREADS);
+      cfg.dynamicSmemBytes = QRC_SMEM_LIMIT;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 16;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k_qr_cluster, &cfg) == cudaSuccess && nclusters >= 1)
+        g_qr_max_cluster = 16;
+    }
+    cudaGetLastError();
     g_attr_qr = true;
   }
   if (!g_attr_svd) {
@@ -460,15 +701,49 @@ static void copy_guarded(Ctx& c, double* dst, const double* src, int64_t n, cons
 
 static size_t qr_smem(int m, int n) { return (size_t(m) * n + m + std::min(m, n) + 32) * sizeof(double); }
 
+// Column block width and cluster size of the cluster QR for an m x n matrix (cs = 0: use the
+// one-CTA kernel).  Panels of at least 4 columns; at most g_qr_max_cluster CTAs.
+static void qr_cluster_shape(int m, int n, int& nb, int& cs) {
+  nb = 0;
+  cs = 0;
+  if (m < n || n < 16 || g_qr_max_cluster < 2) return;
+  int b = std::max(4, (n + g_qr_max_cluster - 1) / g_qr_max_cluster);
+  int k = (n + b - 1) / b;
+  if (k < 2 || b > 16 || qrc_smem_doubles(m, b) * sizeof(double) > QRC_SMEM_LIMIT) return;
+  nb = b;
+  cs = k;
+}
+
 void qr(Ctx& c, int count, int m, int n, int trans, const double* A, int64_t in_stride, double* Q, int64_t q_stride,
-        double* R, int64_t r_stride) {
+        double* R, int64_t r_stride, int path) {
   if (count <= 0 || n <= 0 || m <= 0) return;
+  init_kernel_attributes();
+  int kk = std::min(m, n);
+  int nb = 0, cs = 0;
+  if (path != 1) qr_cluster_shape(m, n, nb, cs);
+  if (path == 2 && cs == 0)
+    throw Error(QTT_ERR_UNSUPPORTED, "qr: no cluster shape for " + std::to_string(m) + "x" + std::to_string(n));
+  ProfScope ps(c, KC_QR, double(count) * 8.0 * (double(m) * n * kk - 0.5 * (double(m) + n) * kk * kk + kk * kk * kk / 3.0));
+  if (cs > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(count) * unsigned(cs));
+    cfg.blockDim = dim3(QRC_THREADS);
+    cfg.dynamicSmemBytes = qrc_smem_doubles(m, nb) * sizeof(double);
+    cfg.stream = c.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = unsigned(cs);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    QTT_CUDA(cudaLaunchKernelEx(&cfg, k_qr_cluster, m, n, nb, trans, A, Q, R, in_stride, q_stride, r_stride));
+    after_launch(c, "qr_cluster");
+    return;
+  }
   size_t sm = qr_smem(m, n);
   if (sm > 220 * 1024)
     throw Error(QTT_ERR_UNSUPPORTED, "qr: matrix " + std::to_string(m) + "x" + std::to_string(n) + " too large for one CTA");
-  init_kernel_attributes();
-  int kk = std::min(m, n);
-  ProfScope ps(c, KC_QR, double(count) * 8.0 * (double(m) * n * kk - 0.5 * (double(m) + n) * kk * kk + kk * kk * kk / 3.0));
   k_qr<<<count, 256, sm, c.stream>>>(m, n, trans, A, Q, R, in_stride, q_stride, r_stride);
   after_launch(c, "qr");
 }

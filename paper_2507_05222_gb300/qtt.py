@@ -76,6 +76,8 @@ _SIGS = {
     "qtt_ctx_kernel_launches": (L, [P]),
     "qtt_ctx_pool_bytes": (S, [P]),
     "qtt_ctx_profile": (I, [P, I, DP, DP, C.POINTER(C.c_int64)]),
+    "qtt_ctx_profile_phases": (I, [P, DP, C.POINTER(C.c_int64)]),
+    "qtt_qr": (I, [P, I, I, I, DP, DP, DP, I]),
     "qtt_profiler_range": (I, [I]),
     "qtt_mps_create": (I, [P, I, I, IP, DP, I, C.POINTER(P)]),
     "qtt_mps_free": (I, [P]),
@@ -200,6 +202,16 @@ class Context:
                                      n.ctypes.data_as(C.POINTER(C.c_int64))))
         return {k: dict(ms=float(ms[i]), flops=float(fl[i]), launches=int(n[i]))
                 for i, k in enumerate(self.PROFILE_CLASSES)}
+
+    def profile_phases(self):
+        """Kernel-class ms and launch counts of the last profile() read-out, by step phase."""
+        kc = self.PROFILE_CLASSES[:5]
+        rows = ("apply", "rhs_and_momentum", "unused", "poisson", "projection", "outside")
+        ms = np.zeros(len(rows) * len(kc)); n = np.zeros(len(rows), dtype=np.int64)
+        _check(lib().qtt_ctx_profile_phases(self.h, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64))))
+        ms = ms.reshape(len(rows), len(kc))
+        return {r: dict({k: float(ms[i, j]) for j, k in enumerate(kc)}, launches=int(n[i]))
+                for i, r in enumerate(rows) if r != "unused"}
 
     def close(self):
         if getattr(self, "h", None):
@@ -399,6 +411,23 @@ def mps_dot_noalloc(n: int, d: int, a_bonds, a_cores_dev: int, b_bonds, b_cores_
     bb = np.ascontiguousarray(np.asarray(b_bonds, dtype=np.int32))
     _check(lib().mps_dot_noalloc(n, d, ab.ctypes.data_as(IP), a_cores_dev, bb.ctypes.data_as(IP), b_cores_dev,
                                  out_dev, stream))
+
+
+def qtt_qr(ctx: Context, A, trans: bool = False, path: int = 0):
+    """Householder QR of a small dense matrix on the device: A = Q R (LAPACK sign convention).
+
+    With trans=True the argument is A^T (n x m) and Q^T is returned in place of Q.
+    path: 0 automatic, 1 one CTA, 2 cluster kernel."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+    if trans:
+        n, m = A.shape
+    else:
+        m, n = A.shape
+    kk = min(m, n)
+    Q = np.zeros((kk, m) if trans else (m, kk))
+    R = np.zeros((kk, n))
+    _check(lib().qtt_qr(ctx.h, m, n, 1 if trans else 0, _dp(A), _dp(Q), _dp(R), int(path)))
+    return Q, R
 
 
 def qtt_sym_eig(ctx: Context, S):
