@@ -675,6 +675,8 @@ int fractional_step(qtt_ctx* ctx, qtt_case* h, int nsteps, int with_forces, qtt_
       per_step[s].cg_u = cg3[0];
       per_step[s].cg_v = cg3[1];
       per_step[s].cg_p = cg3[2];
+      if (cg3[0] < 0 || cg3[1] < 0 || cg3[2] < 0)
+        throw Error(QTT_ERR_CUDA, "fractional_step: a CG grid barrier timed out (step " + std::to_string(s) + ")");
       per_step[s].cd = with_forces ? hrec[4 * s + 2] : 0.0;
       per_step[s].cl = with_forces ? hrec[4 * s + 3] : 0.0;
     }
@@ -693,6 +695,14 @@ int qtt_case_phase_ms(qtt_case* h, double* ms4) {
     QTT_CUDA(cudaEventElapsedTime(&t, cs.ph_ev[i], cs.ph_ev[i + 1]));
     ms4[i] = t;
   }
+  API_END
+}
+
+int qtt_ctx_set_cg_mode(qtt_ctx* ctx, int mode) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx, "ctx is null");
+  QTT_CHECK_ARG(mode == 0 || mode == 1, "cg mode must be 0 (one kernel per solve) or 1 (one kernel per stage)");
+  reinterpret_cast<Ctx*>(ctx)->cg_mode = mode;
   API_END
 }
 

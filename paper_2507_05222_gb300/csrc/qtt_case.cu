@@ -638,6 +638,7 @@ void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
 static void capture(Ctx& c, Case& cs, bool with_forces) {
   cs.drop_graph();
   init_kernel_attributes();
+  cg_init_attributes();
   for (int i = 0; i < 4; ++i) worker(c, i);
   if (!cs.gstream) QTT_CUDA(cudaStreamCreateWithFlags(&cs.gstream, cudaStreamNonBlocking));
   if (!cs.ev_in) QTT_CUDA(cudaEventCreateWithFlags(&cs.ev_in, cudaEventDisableTiming));

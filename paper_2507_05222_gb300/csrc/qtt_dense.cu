@@ -363,10 +363,20 @@ void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, 
     after_launch(c, "splitk_reduce");
     return;
   }
-  // Tile and split-K choice: enough CTAs to cover every SM twice (the FP64 pipe, not memory,
-  // bounds these kernels), the larger tile when it already gets there.
+  // Tile and split-K choice.  On GB300 an SM retires 2 FP64 FMAs per cycle, so the FP64 pipe,
+  // not shared-memory or L2 traffic, bounds these kernels at any tile size >= 16: the time is
+  // about the FMA load of the busiest SM, ceil(CTAs / SMs) T^2 kchunk / 2 cycles, plus one more
+  // launch when K is split.  Each tile size is planned with split-K up to two CTAs per SM
+  // (at least 2 GK of k per split); the cheapest plan wins, ties going to the larger tile.
   const int64_t target = 2 * int64_t(c.num_sms);
-  auto plan = [&](int T, int64_t& splits_out, int64_t& kchunk_out) {
+  struct Plan {
+    int T;
+    int64_t splits, kchunk;
+    double cost;
+  };
+  auto plan = [&](int T) {
+    Plan p;
+    p.T = T;
     int64_t tiles = ((M + T - 1) / T) * ((N + T - 1) / T) * batch;
     int64_t splits = 1;
     if (tiles < target && K > 2 * GK) {
@@ -377,17 +387,20 @@ void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, 
     int64_t kchunk = (K + splits - 1) / splits;
     kchunk = (kchunk + GK - 1) / GK * GK;
     splits = (K + kchunk - 1) / kchunk;
-    splits_out = splits;
-    kchunk_out = kchunk;
-    return tiles * splits;
+    p.splits = splits;
+    p.kchunk = kchunk;
+    const int64_t per_sm = (tiles * splits + c.num_sms - 1) / c.num_sms;
+    p.cost = double(per_sm) * T * T * double(kchunk) / 2.0 + (splits > 1 ? 3000.0 : 0.0);
+    return p;
   };
-  int64_t s64, kc64, s32, kc32;
-  int64_t ctas64 = plan(64, s64, kc64);
-  int64_t ctas32 = plan(32, s32, kc32);
-  const bool big = ctas64 >= target || ctas64 >= ctas32;
-  const int T = big ? 64 : 32;
-  const int splits = int(big ? s64 : s32);
-  const int64_t kchunk = big ? kc64 : kc32;
+  Plan best = plan(64);
+  for (int T : {32, 16}) {
+    Plan p = plan(T);
+    if (p.cost < best.cost * 0.97) best = p;
+  }
+  const int T = best.T;
+  const int splits = int(best.splits);
+  const int64_t kchunk = best.kchunk;
   ProfScope ps(c, KC_GEMM, 2.0 * double(batch) * double(M) * double(N) * double(K));
   dim3 grid(unsigned((N + T - 1) / T), unsigned((M + T - 1) / T), unsigned(batch * splits));
   QTT_CHECK_ARG(grid.y <= 65535 && grid.z <= 65535, "gemm grid too large");
@@ -395,11 +408,14 @@ void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, 
   DBuf W;
   if (splits > 1) W.reset(&c, size_t(splits) * batch * M * N);
   double* Wp = splits > 1 ? W.p : nullptr;
-  if (big)
+  if (T == 64)
     k_gemm<64><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
                                              sBn, beta, C, sCb, sCm, sCn, Wp, c.guard);
-  else
+  else if (T == 32)
     k_gemm<32><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
+                                             sBn, beta, C, sCb, sCm, sCn, Wp, c.guard);
+  else
+    k_gemm<16><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
                                              sBn, beta, C, sCb, sCm, sCn, Wp, c.guard);
   after_launch(c, "gemm");
   if (splits > 1) {

@@ -140,6 +140,9 @@ struct Ctx {
   // if it is 0.  Set around the matrix-vector products of a CG solve so that iterations past
   // convergence cost only their launches (the iteration budget is fixed on the host).
   const int* guard = nullptr;
+  // ALS local solves: 0 = one cooperative kernel per solve where the shapes allow it,
+  // 1 = one kernel per contraction and CG update (read from the root context).
+  int cg_mode = 0;
   Profiler prof;
 };
 

@@ -78,6 +78,7 @@ _SIGS = {
     "qtt_ctx_profile": (I, [P, I, DP, DP, C.POINTER(C.c_int64)]),
     "qtt_ctx_profile_phases": (I, [P, DP, C.POINTER(C.c_int64)]),
     "qtt_qr": (I, [P, I, I, I, DP, DP, DP, I]),
+    "qtt_ctx_set_cg_mode": (I, [P, I]),
     "qtt_profiler_range": (I, [I]),
     "qtt_mps_create": (I, [P, I, I, IP, DP, I, C.POINTER(P)]),
     "qtt_mps_free": (I, [P]),
@@ -202,6 +203,10 @@ class Context:
                                      n.ctypes.data_as(C.POINTER(C.c_int64))))
         return {k: dict(ms=float(ms[i]), flops=float(fl[i]), launches=int(n[i]))
                 for i, k in enumerate(self.PROFILE_CLASSES)}
+
+    def set_cg_mode(self, mode: int):
+        """0: one cooperative kernel per ALS local CG solve (default); 1: one kernel per stage."""
+        _check(lib().qtt_ctx_set_cg_mode(self.h, int(mode)))
 
     def profile_phases(self):
         """Kernel-class ms and launch counts of the last profile() read-out, by step phase."""

@@ -160,3 +160,33 @@ def test_graph_replay_equals_eager(ctx):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
         assert ia == ib
+
+
+@pytest.mark.parametrize("ne,nx,chi", [(5, 5, 16), (6, 6, 64)])
+def test_cg_one_kernel_equals_per_stage(ctx, ne, nx, chi):
+    """The local CG solves as one cooperative kernel give the per-stage kernels' iterates up to
+    rounding order: CG counts within one per step, states within the oracle parity bar (1e-10)
+    after one step (the step amplifies rounding differences ~1e3-fold: unconverged CG).  At
+    chi = 64 the grid runs several work items per CTA in both contraction stages (the momentum
+    solves run on half the SMs)."""
+    from paper_2507_05222_gb300 import qtt
+    R, Re, dt = 40.0, 100.0, 2e-3
+    ops = Q.Ops(ne, nx, R, Re, dt, "interleaved")
+    _, (gu, gv, gp), _ = make_state(ctx, ops, ne, nx, chi)
+    out = []
+    try:
+        for mode in (0, 1):
+            ctx.set_cg_mode(mode)
+            case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=1, mom=(1, 8, 1e-12),
+                            poi=(2, 20, 1e-12))
+            case.set_state(gu, gv, gp)
+            info = case.fractional_step(1, with_forces=False)
+            out.append(([qtt.qtt_decode(ctx, x) for x in case.get_state()], info))
+    finally:
+        ctx.set_cg_mode(0)
+    (a, ia), (b, ib) = out
+    for x, y in zip(a, b):
+        assert rel(x, y) < TOL
+    for i, j in zip(ia, ib):
+        for k in ("cg_u", "cg_v", "cg_p"):
+            assert abs(i[k] - j[k]) <= 1

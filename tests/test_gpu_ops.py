@@ -150,7 +150,14 @@ def test_dot(ctx):
     assert abs(v - ref) <= 1e-12 * np.linalg.norm(tt.full(a)) * np.linalg.norm(tt.full(b))
 
 
-def test_poisson_solve_matches_oracle_als(ctx):
+@pytest.fixture(params=[0, 1], ids=["cg_one_kernel", "cg_per_stage"])
+def cg_mode(ctx, request):
+    ctx.set_cg_mode(request.param)
+    yield request.param
+    ctx.set_cg_mode(0)
+
+
+def test_poisson_solve_matches_oracle_als(ctx, cg_mode):
     """ALS (Sec. II.A.4) with the same sweeps / CG budget as the oracle."""
     from paper_2507_05222_gb300 import qtt
     ne, nx = 4, 4
@@ -165,7 +172,7 @@ def test_poisson_solve_matches_oracle_als(ctx):
     assert rel(down(ctx, g), tt.full(ref)) < 1e-9
 
 
-def test_poisson_solve_full_rank_exact(ctx):
+def test_poisson_solve_full_rank_exact(ctx, cg_mode):
     """At full bond dimension the ALS solution equals the dense solve (J-weighted Poisson)."""
     from paper_2507_05222_gb300 import qtt
     ne, nx = 3, 4
