@@ -433,11 +433,16 @@ __global__ void __launch_bounds__(256) k_svd_jacobi(int m, int n, const double* 
 // ------------------------------------------------------------------ symmetric Jacobi (FP32)
 // S: n x n FP64 row-major symmetric.  V (FP64 out, row-major n x n): eigenvectors as columns.
 // With t0_dev != null only the trailing block S[t0:, t0:] is diagonalised (t0 read on the
-// device) and Vout is the identity outside that block.  1024 threads as 32 x 32: threadIdx.x
-// walks the matrix index, the warp index walks the rotation pairs, so no integer division by
-// a runtime size appears in the per-round updates.
+// device) and Vout is the identity outside that block.  1024 threads.
+// Parallel cyclic (round-robin) ordering: each round rotates n/2 disjoint pairs (p_k, q_k).
+// The round's two-sided update A <- J^T A J is done in one pass over 2 x 2 blocks: block
+// (k, l) of A (rows p_k, q_k; columns p_l, q_l) becomes R_k B R_l^T, so each element is loaded
+// and stored once per round, and only blocks k <= l are computed (the mirror is stored), which
+// halves the FP32 work of the rotation; V's columns are rotated in the same pass.  Sweeps stop
+// when the off-diagonal mass falls below off_tol2 of the total (squared Frobenius norms) -- the
+// FP64 refinement that follows only needs a start it converges from quadratically.
 __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __restrict__ S, double* __restrict__ Vout,
-                                                     int max_sweeps, const int* __restrict__ t0_dev) {
+                                                     int max_sweeps, const int* __restrict__ t0_dev, float off_tol2) {
   extern __shared__ float smf[];
   const int t0 = t0_dev ? *t0_dev : 0;
   const int n = nfull - t0;
@@ -451,12 +456,16 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
     return;
   }
   const int ld = n + 1;                 // padded rows: column walks are bank-conflict free
+  const int np = (n + 1) & ~1;
+  const int npairs = np / 2;
+  const int nblocks = npairs * (npairs + 1) / 2;
   float* A = smf;                       // n x ld
   float* V = A + size_t(n) * ld;        // n x ld (row i = component i, column = vector)
-  float* cs = V + size_t(n) * ld;       // np/2
-  float* sn = cs + (n + 2) / 2;         // np/2
-  int* pp = reinterpret_cast<int*>(sn + (n + 2) / 2);
-  int* qq = pp + (n + 2) / 2;
+  float* cs = V + size_t(n) * ld;       // npairs
+  float* sn = cs + npairs;              // npairs
+  int* pp = reinterpret_cast<int*>(sn + npairs);
+  int* qq = pp + npairs;
+  unsigned short* blk = reinterpret_cast<unsigned short*>(qq + npairs);   // (k << 8 | l), k <= l
   __shared__ float red[32];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   for (int i = ty; i < n; i += 32)
@@ -464,9 +473,11 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
       A[i * ld + j] = float(S[size_t(i + t0) * nfull + (j + t0)]);
       V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
     }
+  for (int k = tid; k < npairs; k += 1024) {
+    int base = k * npairs - k * (k - 1) / 2;
+    for (int l = k; l < npairs; ++l) blk[base + (l - k)] = (unsigned short)((k << 8) | l);
+  }
   __syncthreads();
-  const int np = (n + 1) & ~1;
-  const int npairs = np / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // convergence test: off-diagonal mass relative to the total
     float off = 0.f, tot = 0.f;
@@ -488,7 +499,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
     float tots = 0.f;
     for (int i = 0; i < 32; ++i) tots += red[i];
     __syncthreads();
-    if (!(offs > 1e-12f * tots)) break;
+    if (!(offs > off_tol2 * tots)) break;
     for (int r = 0; r < np - 1; ++r) {
       if (tid < npairs) {
         const int k = tid;
@@ -505,33 +516,49 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
           if (apq != 0.f) {
             float tau = (A[q * ld + q] - A[p * ld + p]) / (2.f * apq);
             float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = rsqrtf(1.f + t * t);
+            // correctly rounded sqrt and division: c^2 + s^2 - 1 stays at the rounding level
+            // with no bias, so V drifts from orthonormality like a random walk over the
+            // ~n sweeps x n rounds of rotations rather than linearly
+            c = 1.f / sqrtf(1.f + t * t);
             s = t * c;
           }
         }
         pp[k] = p; qq[k] = q; cs[k] = c; sn[k] = s;
       }
       __syncthreads();
-      for (int k = ty; k < npairs; k += 32) {        // rows p, q of A
-        const int p = pp[k], q = qq[k];
-        if (q >= n) continue;
-        const float c = cs[k], s = sn[k];
-        for (int j = tx; j < n; j += 32) {
-          float x = A[p * ld + j], y = A[q * ld + j];
-          A[p * ld + j] = c * x - s * y;
-          A[q * ld + j] = s * x + c * y;
+      // A <- J^T A J: block (k, l) = R_k B R_l^T with R = [c -s; s c] acting on (p, q)
+      for (int e = tid; e < nblocks; e += 1024) {
+        const unsigned short kl = blk[e];
+        const int k = kl >> 8, l = kl & 0xff;
+        const int p1 = pp[k], q1 = qq[k], p2 = pp[l], q2 = qq[l];
+        const float c1 = cs[k], s1 = sn[k], c2 = cs[l], s2 = sn[l];
+        const bool h1 = q1 < n, h2 = q2 < n;   // a pair with q >= n is a lone index (odd n)
+        const float b00 = A[p1 * ld + p2];
+        const float b01 = h2 ? A[p1 * ld + q2] : 0.f;
+        const float b10 = h1 ? A[q1 * ld + p2] : 0.f;
+        const float b11 = (h1 && h2) ? A[q1 * ld + q2] : 0.f;
+        const float t00 = c1 * b00 - s1 * b10, t01 = c1 * b01 - s1 * b11;
+        const float t10 = s1 * b00 + c1 * b10, t11 = s1 * b01 + c1 * b11;
+        const float n00 = c2 * t00 - s2 * t01, n01 = s2 * t00 + c2 * t01;
+        const float n10 = c2 * t10 - s2 * t11, n11 = s2 * t10 + c2 * t11;
+        A[p1 * ld + p2] = n00;
+        if (h2) A[p1 * ld + q2] = n01;
+        if (h1) A[q1 * ld + p2] = n10;
+        if (h1 && h2) A[q1 * ld + q2] = n11;
+        if (k != l) {
+          A[p2 * ld + p1] = n00;
+          if (h2) A[q2 * ld + p1] = n01;
+          if (h1) A[p2 * ld + q1] = n10;
+          if (h1 && h2) A[q2 * ld + q1] = n11;
         }
       }
-      __syncthreads();
-      for (int k = ty; k < npairs; k += 32) {        // columns p, q of A and of V
+      // columns p, q of V (independent of the A update)
+      for (int k = ty; k < npairs; k += 32) {
         const int p = pp[k], q = qq[k];
         if (q >= n) continue;
         const float c = cs[k], s = sn[k];
         for (int i = tx; i < n; i += 32) {
-          float x = A[i * ld + p], y = A[i * ld + q];
-          A[i * ld + p] = c * x - s * y;
-          A[i * ld + q] = s * x + c * y;
-          x = V[i * ld + p]; y = V[i * ld + q];
+          float x = V[i * ld + p], y = V[i * ld + q];
           V[i * ld + p] = c * x - s * y;
           V[i * ld + q] = s * x + c * y;
         }
@@ -768,6 +795,13 @@ static void oa_update(Ctx& c, int n, const double* XtX, const double* SX, const 
   after_launch(c, "oa_E");
 }
 
+// One Newton-Schulz step X <- X (3 I - X^T X) / 2 (squares ||X^T X - I||); honours c.guard.
+static void newton_schulz(Ctx& c, int n, double* X, double* XtX, double* AX) {
+  gemm(c, 1, n, n, n, 1.0, X, 0, 1, n, X, 0, n, 1, 0.0, XtX, 0, n, 1);
+  gemm(c, 1, n, n, n, 1.0, X, 0, n, 1, XtX, 0, n, 1, 0.0, AX, 0, n, 1);
+  axpby(c, int64_t(n) * n, -0.5, AX, 1.5, X);
+}
+
 // One Ogita-Aishima iteration on X (n x n) for the symmetric S.
 static void oa_iteration(Ctx& c, int n, const double* S, double* X, double* XtX, double* AX, double* SX, double* E,
                          double* lam, const double* an, double* part) {
@@ -785,10 +819,23 @@ static void oa_iteration(Ctx& c, int n, const double* S, double* X, double* XtX,
 // levels 2 and 3 re-diagonalise the trailing block of X^T S X (the eigenvalues below
 // 1e-5 and 1e-10 of the largest) on its own scale and refine again.  Levels with fewer than
 // two tail eigenvalues are skipped on the device.
+// FP32 Jacobi stopping thresholds (squared off-diagonal mass over squared total) before the
+// level-0 and the tail-level refinements.
+#ifndef QTT_JAC_TOL2_FULL
+#define QTT_JAC_TOL2_FULL 1e-12f
+#endif
+#ifndef QTT_JAC_TOL2_TAIL
+#define QTT_JAC_TOL2_TAIL 1e-12f
+#endif
+constexpr float JAC_TOL2_FULL = QTT_JAC_TOL2_FULL;
+constexpr float JAC_TOL2_TAIL = QTT_JAC_TOL2_TAIL;
+
 void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
   QTT_CHECK_ARG(n >= 1, "eigh: n >= 1");
   if (n > 160) throw Error(QTT_ERR_UNSUPPORTED, "eigh: n > 160 not supported");
-  size_t smf = (size_t(n) * (n + 1) * 2 + 2 * ((n + 2) / 2)) * sizeof(float) + 2 * ((n + 2) / 2) * sizeof(int);
+  const size_t npairs = size_t((n + 1) & ~1) / 2;
+  size_t smf = (size_t(n) * (n + 1) * 2 + 2 * npairs) * sizeof(float) + 2 * npairs * sizeof(int) +
+               npairs * (npairs + 1) / 2 * sizeof(unsigned short);
   init_kernel_attributes();
   const size_t nn = size_t(n) * n;
   DBuf X(&c, nn), Xs(&c, nn), XtX(&c, nn), AX(&c, nn), SX(&c, nn), E(&c, nn), Y(&c, nn), lam(&c, size_t(n)),
@@ -797,9 +844,10 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
   int* need = t0 + 1;
   {
     ProfScope ps(c, KC_EIG);
-    k_jacobi_f32<<<1, dim3(32, 32), smf, c.stream>>>(n, S, X.p, 10, nullptr);
+    k_jacobi_f32<<<1, dim3(32, 32), smf, c.stream>>>(n, S, X.p, 10, nullptr, JAC_TOL2_FULL);
     after_launch(c, "jacobi_f32");
   }
+
   k_frob<<<1, 1024, 0, c.stream>>>(int64_t(n) * n, S, an.p);
   after_launch(c, "frob");
   const double taus[3] = {0.0, 1e-5, 1e-10};
@@ -813,7 +861,7 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
       c.guard = nullptr;
       {
         ProfScope ps(c, KC_EIG);
-        k_jacobi_f32<<<1, dim3(32, 32), smf, c.stream>>>(n, SX.p, Y.p, 8, t0);
+        k_jacobi_f32<<<1, dim3(32, 32), smf, c.stream>>>(n, SX.p, Y.p, 8, t0, JAC_TOL2_TAIL);
         after_launch(c, "jacobi_f32_tail");
       }
       c.guard = need;
@@ -833,13 +881,9 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
     copy(c, X.p, Xs.p, int64_t(nn));
     copy(c, lam.p, w, n);
   }
-  // Two Newton-Schulz steps X <- X (3 I - X^T X) / 2: the first-order orthonormalisation of
-  // the refinement leaves ~eps ||S|| / gap in X^T X - I for close pairs; each step squares it.
-  for (int it = 0; it < 2; ++it) {
-    gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, X.p, 0, n, 1, 0.0, XtX.p, 0, n, 1);
-    gemm(c, 1, n, n, n, 1.0, X.p, 0, n, 1, XtX.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
-    axpby(c, int64_t(nn), -0.5, AX.p, 1.5, X.p);
-  }
+  // Two Newton-Schulz steps: the first-order orthonormalisation of the refinement leaves
+  // ~eps ||S|| / gap in X^T X - I for close pairs; each step squares it.
+  for (int it = 0; it < 2; ++it) newton_schulz(c, n, X.p, XtX.p, AX.p);
   copy(c, V, X.p, int64_t(nn));
 }
 
