@@ -912,7 +912,7 @@ int als(Ctx& c, const qtt_mpo* A, const std::vector<Term>& rhs, qtt_mps* x, int 
     int r0 = x->bonds[k], r1 = x->bonds[k + 1];
     int64_t nel = int64_t(r0) * d * r1;
     const int w0 = A->bonds[k], w1 = A->bonds[k + 1];
-    if (c.root->cg_mode == 0 && cg_persistent_fits(r0, r1, w0, w1, d)) {
+    if (c.root->cg_mode == 0 && cg_persistent_fits(c, r0, r1, w0, w1, d)) {
       DBuf bvec(&c, nel), xk(&c, nel);
       local_sum(c, rhs, E, x, k, bvec.p);
       copy(c, xk.p, x->core(k), nel);

@@ -58,7 +58,7 @@ int als(Ctx& c, const qtt_mpo* A, const std::vector<Term>& rhs, qtt_mps* x, int 
 // One ALS local CG solve as a single cooperative kernel (qtt_cg.cu): L (r0, w0, r0),
 // W (w0, d, d, w1), R (r1, w1, r1), b and x (r0, d, r1; x in/out); *total_dev += iterations
 // done, or a negative value if a grid barrier timed out.
-bool cg_persistent_fits(int r0, int r1, int w0, int w1, int d);
+bool cg_persistent_fits(const Ctx& c, int r0, int r1, int w0, int w1, int d);
 void cg_init_attributes();   // kernel attributes and occupancy, once (before any stream capture)
 void cg_persistent(Ctx& c, const double* L, const double* W, const double* R, const double* b, double* x, int r0,
                    int r1, int w0, int w1, int d, int iters, double tol, int* total_dev);

@@ -38,7 +38,6 @@ constexpr unsigned long long CGP_TIMEOUT_NS = 2000000000ull;   // 2 s per barrie
 constexpr int CGP_MAX_BOND = 128;
 constexpr int CGP_MAX_W = 16;
 constexpr int CGP_MAX_D = 4;
-constexpr int CGP_ET = 16;                        // outputs per stage-B work item
 
 struct CgBar {
   unsigned int count;   // arrivals so far (monotonic within a launch)
@@ -48,6 +47,7 @@ struct CgBar {
 
 struct CgArgs {
   int r0, r1, w0, w1, d, bt, iters;
+  int eb, ch;     // stage B: e-block width (16, 8, 4, 2 or 1) and T2 row chunks per load
   double tol2;
   const double* L;
   const double* W;
@@ -145,10 +145,15 @@ __device__ void stage_a(const CgArgs& a, const double* P0, const double* Rv, dou
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int c = item / nblk, b0 = (item % nblk) * bt, bw = min(bt, r1 - b0);
     for (int e = tid; e < w0 * r0; e += nt) sL[e] = __ldg(a.L + size_t(c) * w0 * r0 + e);
-    for (int e = tid; e < r0 * d * bw; e += nt) {
-      const int aa = e / (d * bw), rem = e % (d * bw), t = rem / bw, bb = rem % bw;
-      const size_t g = (size_t(aa) * d + t) * r1 + b0 + bb;
-      sP[(aa * d + t) * bt + bb] = Rv ? fma(beta, __ldcg(P0 + g), __ldcg(Rv + g)) : __ldcg(P0 + g);
+    // rows (a, t) of the P block, one warp per row and one lane per b (bt <= 32): coalesced,
+    // no index division
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    if (lane < bw) {
+#pragma unroll 4
+      for (int row = warp; row < r0 * d; row += nwarps) {
+        const size_t g = size_t(row) * r1 + b0 + lane;
+        sP[row * bt + lane] = Rv ? fma(beta, __ldcg(P0 + g), __ldcg(Rv + g)) : __ldcg(P0 + g);
+      }
     }
     __syncthreads();
     for (int e = tid; e < w0 * d * bw; e += nt) {
@@ -172,26 +177,46 @@ __device__ void stage_a(const CgArgs& a, const double* P0, const double* Rv, dou
 }
 
 // Stage B: out = T2 . R^T; returns this block's share of P . out (0 if P is null).
-__device__ double stage_b(const CgArgs& a, const double* P, double* out) {
-  const int r0 = a.r0, r1 = a.r1, w1 = a.w1, d = a.d;
-  const int rows = r0 * d, K = w1 * r1;
-  const int neblk = (r1 + CGP_ET - 1) / CGP_ET;
-  const int items = rows * neblk;
-  const int o = threadIdx.x / 16, l = threadIdx.x % 16;
+// Block j works on the e-block j % NE (EB consecutive e, its rows of R staged in sR once per
+// solve) and on the row chunks (RB rows each) j / NE, j / NE + NRG, ...; the T2 rows of up to
+// CH chunks are loaded together (one L2 latency), then 16 outputs x 16 lanes per pass.
+__device__ double stage_b(const CgArgs& a, const double* P, double* out, const double* sR, double* sT2) {
+  const int r1 = a.r1, EB = a.eb, RB = 16 / a.eb, K = a.w1 * r1, Kp = K + 1;
+  const int rows = a.r0 * a.d;
+  const int NE = (r1 + EB - 1) / EB, NRG = gridDim.x / NE;
+  const int eb = blockIdx.x % NE, rg = blockIdx.x / NE;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int o = tid >> 4, l = tid & 15, i = o / EB, eo = o % EB;
+  const int e = eb * EB + eo;
   double dot = 0.0;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int row = item / neblk, e = (item % neblk) * CGP_ET + o;
-    double s = 0.0;
-    if (e < r1) {
-      const double* t2 = a.T2 + size_t(row) * K;
-      const double* rr = a.R + size_t(e) * K;
-      for (int k = l; k < K; k += 16) s = fma(__ldcg(t2 + k), __ldg(rr + k), s);
+  if (rg >= NRG) return dot;
+  const int nchunks = (rows + RB - 1) / RB;
+  for (int c0 = rg; c0 < nchunks; c0 += NRG * a.ch) {
+    // load the T2 rows of chunks c0, c0 + NRG, ... (at most ch chunks)
+    int nch = 0;
+    for (int cc = c0; cc < nchunks && nch < a.ch; cc += NRG, ++nch) {
+      const int row0 = cc * RB, nr = min(RB, rows - row0);
+      const double* src = a.T2 + size_t(row0) * K;
+      double* dst = sT2 + size_t(nch) * RB * K;
+      for (int x = tid; x < nr * K; x += nt) dst[x] = __ldcg(src + x);
     }
-    for (int off = 8; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (e < r1 && l == 0) {
-      out[size_t(row) * r1 + e] = s;
-      if (P) dot = fma(__ldcg(P + size_t(row) * r1 + e), s, dot);
+    __syncthreads();
+    for (int q = 0; q < nch; ++q) {
+      const int row = (c0 + q * NRG) * RB + i;
+      double s = 0.0;
+      const bool ok = row < rows && e < r1;
+      if (ok) {
+        const double* t2 = sT2 + (size_t(q) * RB + i) * K;
+        const double* rr = sR + size_t(eo) * Kp;
+        for (int k = l; k < K; k += 16) s = fma(t2[k], rr[k], s);
+      }
+      for (int off = 8; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (ok && l == 0) {
+        out[size_t(row) * r1 + e] = s;
+        if (P) dot = fma(__ldcg(P + size_t(row) * r1 + e), s, dot);
+      }
     }
+    __syncthreads();
   }
   return dot;
 }
@@ -204,10 +229,13 @@ __global__ void __launch_bounds__(CGP_THREADS, 2) k_cg_persistent(CgArgs a) {
   const int r0 = a.r0, w0 = a.w0, w1 = a.w1, d = a.d, bt = a.bt;
   const int G = gridDim.x, tid = threadIdx.x, nt = blockDim.x;
   const int64_t nel = int64_t(r0) * d * a.r1;
+  const int K = w1 * a.r1;
   double* sL = sm;                           // w0 x r0
   double* sW = sL + w0 * r0;                 // w0 x d x d x w1
   double* sP = sW + w0 * d * d * w1;         // r0 x d x bt
   double* sT1 = sP + r0 * d * bt;            // w0 x d x bt
+  double* sR = sT1 + w0 * d * bt;            // eb x (K + 1): this block's rows of R
+  double* sT2 = sR + size_t(a.eb) * (K + 1); // ch x (16 / eb) x K
   __shared__ double red[32];
   __shared__ int flag;
   unsigned int target = 0;
@@ -215,6 +243,13 @@ __global__ void __launch_bounds__(CGP_THREADS, 2) k_cg_persistent(CgArgs a) {
   double* part_rr = a.part + G;
   double* part_bb = a.part + 2 * G;
   for (int e = tid; e < w0 * d * d * w1; e += nt) sW[e] = __ldg(a.W + e);
+  {
+    const int NE = (a.r1 + a.eb - 1) / a.eb, e0 = (blockIdx.x % NE) * a.eb;
+    for (int x = tid; x < a.eb * K; x += nt) {
+      const int eo = x / K, k = x - eo * K;
+      sR[size_t(eo) * (K + 1) + k] = (e0 + eo < a.r1) ? __ldg(a.R + size_t(e0 + eo) * K + k) : 0.0;
+    }
+  }
   __syncthreads();
 
   // ---- initial residual: r = b - A x, p_0 = r
@@ -224,7 +259,7 @@ __global__ void __launch_bounds__(CGP_THREADS, 2) k_cg_persistent(CgArgs a) {
   do {
     stage_a(a, a.x, nullptr, 0.0, sL, sW, sP, sT1);
     if (!(ok = grid_sync(a.bar, target, &flag))) break;
-    stage_b(a, nullptr, a.Ap);
+    stage_b(a, nullptr, a.Ap, sR, sT2);
     if (!(ok = grid_sync(a.bar, target, &flag))) break;
     double rr_p = 0.0, bb_p = 0.0;
     for (int64_t e = int64_t(blockIdx.x) * nt + tid; e < nel; e += int64_t(G) * nt) {
@@ -260,7 +295,7 @@ __global__ void __launch_bounds__(CGP_THREADS, 2) k_cg_persistent(CgArgs a) {
         stage_a(a, po, a.r, beta, sL, sW, sP, sT1);
       }
       if (!(ok = grid_sync(a.bar, target, &flag))) break;
-      double pap_p = stage_b(a, pn, a.Ap);
+      double pap_p = stage_b(a, pn, a.Ap, sR, sT2);
       pap_p = block_reduce(pap_p, red);
       if (tid == 0) part_pap[blockIdx.x] = pap_p;
       if (!(ok = grid_sync(a.bar, target, &flag))) break;
@@ -290,10 +325,6 @@ __global__ void __launch_bounds__(CGP_THREADS, 2) k_cg_persistent(CgArgs a) {
   }
 }
 
-size_t cgp_smem_bytes(int r0, int w0, int w1, int d, int bt) {
-  return (size_t(w0) * r0 + size_t(w0) * d * d * w1 + size_t(r0) * d * bt + size_t(w0) * d * bt) * sizeof(double);
-}
-
 // Stage-A block of b.  Per work item the CTA does bt r0 w0 d FP64 FMAs at the SM's 2 per cycle,
 // and never less than one dependent chain of r0 FMAs (~64 cycles each) per pass of its 256
 // threads; items are dealt to the G CTAs round by round.  Larger blocks win ties.
@@ -314,43 +345,77 @@ int choose_bt(int r0, int r1, int w0, int d, int G) {
   return best;
 }
 
+// Shared memory of one block at most 110 KiB, so that two blocks fit an SM.
+constexpr size_t CGP_SMEM_LIMIT = 110 * 1024;
+
+struct CgPlan {
+  int G, bt, eb, ch;
+  size_t smem;
+};
+
+// Grid, stage-A block, stage-B e-block and chunking, shared memory; false if the solve does not
+// fit this kernel (the caller then launches one kernel per stage).
+bool cg_plan(const Ctx& c, int r0, int r1, int w0, int w1, int d, CgPlan& p) {
+  if (!(r0 >= 1 && r1 >= 1 && r0 <= CGP_MAX_BOND && r1 <= CGP_MAX_BOND && w0 >= 1 && w1 >= 1 && w0 <= CGP_MAX_W &&
+        w1 <= CGP_MAX_W && d >= 1 && d <= CGP_MAX_D))
+    return false;
+  // The cooperative launch needs every block resident.  The caller's own stream gets one CTA
+  // per SM; a worker stream (two solves may run concurrently, next to short-lived kernels of
+  // other streams) gets half the SMs, so that two persistent grids never hold more than one of
+  // the two slots per SM that this kernel's register and shared-memory budget leaves.
+  p.G = (&c == c.root) ? c.num_sms : std::max(1, c.num_sms / 2);
+  const int K = w1 * r1;
+  int eb = 16;
+  while (eb > 1 && size_t(eb) * (K + 1) * sizeof(double) > 64 * 1024) eb >>= 1;
+  const int NE = (r1 + eb - 1) / eb;
+  if (NE > p.G) return false;
+  const int NRG = p.G / NE, RB = 16 / eb, rows = r0 * d;
+  const int nchunks = (rows + RB - 1) / RB;
+  p.bt = choose_bt(r0, r1, w0, d, p.G);
+  const size_t base = size_t(w0) * r0 + size_t(w0) * d * d * w1 + size_t(r0) * d * p.bt + size_t(w0) * d * p.bt +
+                      size_t(eb) * (K + 1);
+  const size_t per_ch = size_t(RB) * K;
+  const size_t budget = CGP_SMEM_LIMIT / sizeof(double);
+  if (base + per_ch > budget) return false;
+  p.eb = eb;
+  p.ch = int(std::min<size_t>((nchunks + NRG - 1) / NRG, (budget - base) / per_ch));
+  p.smem = (base + size_t(p.ch) * per_ch) * sizeof(double);
+  return true;
+}
+
 }  // namespace
 
 static int g_cgp_per_sm = -1;
 
 void cg_init_attributes() {
   if (g_cgp_per_sm >= 0) return;
-  const size_t max_smem = cgp_smem_bytes(CGP_MAX_BOND, CGP_MAX_W, CGP_MAX_W, CGP_MAX_D, 32);
-  QTT_CUDA(cudaFuncSetAttribute(k_cg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, int(max_smem)));
+  QTT_CUDA(cudaFuncSetAttribute(k_cg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, int(CGP_SMEM_LIMIT)));
   int per_sm = 0;
-  QTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persistent, CGP_THREADS, max_smem));
+  QTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persistent, CGP_THREADS, CGP_SMEM_LIMIT));
   g_cgp_per_sm = per_sm;
 }
 
-bool cg_persistent_fits(int r0, int r1, int w0, int w1, int d) {
-  return r0 >= 1 && r1 >= 1 && r0 <= CGP_MAX_BOND && r1 <= CGP_MAX_BOND && w0 >= 1 && w1 >= 1 && w0 <= CGP_MAX_W &&
-         w1 <= CGP_MAX_W && d >= 1 && d <= CGP_MAX_D;
+bool cg_persistent_fits(const Ctx& c, int r0, int r1, int w0, int w1, int d) {
+  cg_init_attributes();
+  CgPlan p;
+  return g_cgp_per_sm >= 2 && cg_plan(c, r0, r1, w0, w1, d, p);
 }
 
 void cg_persistent(Ctx& c, const double* L, const double* W, const double* R, const double* b, double* x, int r0,
                    int r1, int w0, int w1, int d, int iters, double tol, int* total_dev) {
-  QTT_CHECK_ARG(cg_persistent_fits(r0, r1, w0, w1, d), "cg_persistent: shape outside the supported range");
-  // The cooperative launch needs every block resident.  The caller's own stream gets one CTA
-  // per SM; a worker stream (two solves may run concurrently, next to short-lived kernels of
-  // other streams) gets half the SMs, so that two persistent grids never hold more than one of
-  // the two slots per SM that this kernel's register budget leaves.
+  CgPlan pl;
+  QTT_CHECK_ARG(cg_plan(c, r0, r1, w0, w1, d, pl), "cg_persistent: shape outside the supported range");
   cg_init_attributes();
-  const int want = (&c == c.root) ? c.num_sms : std::max(1, c.num_sms / 2);
-  const int G = std::min(want, g_cgp_per_sm * c.num_sms);
-  if (G < 1) throw Error(QTT_ERR_UNSUPPORTED, "cg_persistent: kernel does not fit an SM");
-  const int bt = choose_bt(r0, r1, w0, d, G);
-  const size_t smem = cgp_smem_bytes(r0, w0, w1, d, bt);
+  if (g_cgp_per_sm < 2) throw Error(QTT_ERR_UNSUPPORTED, "cg_persistent: fewer than two blocks fit an SM");
+  const int G = pl.G, bt = pl.bt;
+  const size_t smem = pl.smem;
   const int64_t nel = int64_t(r0) * d * r1;
   DBuf r(&c, nel), p(&c, 2 * nel), Ap(&c, nel), T2(&c, size_t(r0) * d * w1 * r1), part(&c, size_t(3) * G),
       bar(&c, (sizeof(CgBar) + 7) / 8);
   QTT_CUDA(cudaMemsetAsync(bar.p, 0, sizeof(CgBar), c.stream));
   CgArgs a;
   a.r0 = r0; a.r1 = r1; a.w0 = w0; a.w1 = w1; a.d = d; a.bt = bt; a.iters = iters;
+  a.eb = pl.eb; a.ch = pl.ch;
   a.tol2 = tol * tol;
   a.L = L; a.W = W; a.R = R; a.b = b; a.x = x;
   a.r = r.p; a.p = p.p; a.Ap = Ap.p; a.T2 = T2.p; a.part = part.p;
