@@ -219,6 +219,10 @@ int qtt_sym_eig(qtt_ctx* ctx, int n, const double* S, double* w, double* V);
  * (QTT_ERR_UNSUPPORTED if the shape does not allow it).  Host buffers; R may be NULL;
  * synchronous. */
 int qtt_qr(qtt_ctx* ctx, int m, int n, int trans, const double* A, double* Q, double* R, int path);
+/* Self-check of the QR's Householder scalars: the maximum relative errors of its Newton-Raphson
+ * reciprocal (err2[0]) and reciprocal square root (err2[1]) against CUDA's correctly rounded
+ * 1/x and 1/sqrt(x) over the n positive host values x.  Synchronous. */
+int qtt_check_recip(qtt_ctx* ctx, int n, const double* x, double* err2);
 /* <a, b> into *out_host (synchronous). */
 int mps_dot(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, double* out_host);
 

@@ -504,6 +504,18 @@ int qtt_qr(qtt_ctx* ctx, int m, int n, int trans, const double* A, double* Q, do
   API_END
 }
 
+int qtt_check_recip(qtt_ctx* ctx, int n, const double* x, double* err2) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && x && err2 && n >= 1 && n <= (1 << 24), "check_recip: arguments");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  DBuf dx(&c, size_t(n)), de(&c, 2);
+  QTT_CUDA(cudaMemcpyAsync(dx.p, x, size_t(n) * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  check_recip(c, n, dx.p, de.p);
+  QTT_CUDA(cudaMemcpyAsync(err2, de.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  API_END
+}
+
 int mps_dot(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, double* out_host) {
   API_BEGIN
   QTT_CHECK_ARG(ctx && out_host, "dot: null argument");

@@ -230,6 +230,9 @@ void dot(Ctx& c, int64_t n, const double* x, const double* y, double* out_dev);
 
 // Householder QR of `count` matrices (strided): A (m x n) = Q (m x kk) R (kk x n), kk = min(m,n).
 // trans = 1: the buffer holds A^T (n x m row-major) and Q^T (kk x m) is written.
+// Max relative errors of the QR's Newton reciprocal / reciprocal square root against CUDA's
+// correctly rounded 1/x and 1/sqrt(x) over x_dev[0..n): err_dev[0], err_dev[1].
+void check_recip(Ctx& c, int n, const double* x_dev, double* err_dev);
 // path: 0 = cluster QR when the shape allows it, else one CTA; 1 = one CTA; 2 = cluster only.
 void qr(Ctx& c, int count, int m, int n, int trans, const double* A, int64_t in_stride, double* Q, int64_t q_stride,
         double* R, int64_t r_stride, int path = 0);

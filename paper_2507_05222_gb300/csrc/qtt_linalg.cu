@@ -150,6 +150,79 @@ __global__ void __launch_bounds__(256) k_qr(int m, int n, int trans, const doubl
 // (nb x nb each) | tau (nb).
 constexpr int QRC_THREADS = 256;
 
+// 1/sqrt(q) and 1/x by Newton-Raphson from the hardware's approximate FP64 reciprocal (square
+// root), two quadratically convergent steps each (~20 correct bits -> beyond 53).  An FP64
+// division or square root is a sequence of ~10 dependent FP64 operations, ~650 cycles on this
+// part; these take 3 x 64 (reciprocal) and 6 x 64 (reciprocal square root) cycles.  Results are
+// within a few ulp of the correctly rounded ones (checked against CUDA's by qtt_check_recip).
+__device__ __forceinline__ double rcp_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double r = fma(-x * y, y, 1.0);
+  y = fma(0.5 * y, r, y);
+  r = fma(-x * y, y, 1.0);
+  return fma(0.5 * y, r, y);
+}
+
+// Householder scalars of a column with pivot alpha and sum of squares sigma below it (LAPACK
+// convention): beta = -sign(alpha) ||x||, t = (beta - alpha) / beta = 1 + |alpha| / ||x||,
+// scale = 1 / (alpha - beta) = sign(alpha) / (|alpha| + ||x||).  sigma = 0: identity reflector.
+__device__ __forceinline__ void householder_scalars(double alpha, double sigma, double& beta, double& t,
+                                                    double& scale) {
+  if (sigma == 0.0) {
+    t = 0.0;
+    beta = alpha;
+    scale = 0.0;
+    return;
+  }
+  const double q = fma(alpha, alpha, sigma);
+  const double g = rsqrt_nr(q);
+  const double nrm = q * g;
+  const double aa = fabs(alpha);
+  beta = alpha >= 0.0 ? -nrm : nrm;
+  t = fma(aa, g, 1.0);
+  const double rd = rcp_nr(aa + nrm);
+  scale = alpha >= 0.0 ? rd : -rd;
+}
+
+__global__ void k_check_recip(int n, const double* __restrict__ x, double* __restrict__ err) {
+  // err[0] = max relative error of rcp_nr, err[1] of rsqrt_nr, against CUDA's 1/x, 1/sqrt(x)
+  __shared__ double red[2][32];
+  double e0 = 0.0, e1 = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = x[i];
+    const double a = 1.0 / v, b = 1.0 / sqrt(v);
+    e0 = fmax(e0, fabs(rcp_nr(v) - a) / fabs(a));
+    e1 = fmax(e1, fabs(rsqrt_nr(v) - b) / fabs(b));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    e0 = fmax(e0, __shfl_xor_sync(0xffffffffu, e0, o));
+    e1 = fmax(e1, __shfl_xor_sync(0xffffffffu, e1, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = e0;
+    red[1][threadIdx.x >> 5] = e1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m0 = 0.0, m1 = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      m0 = fmax(m0, red[0][w]);
+      m1 = fmax(m1, red[1][w]);
+    }
+    err[0] = m0;
+    err[1] = m1;
+  }
+}
+
 __host__ __device__ constexpr size_t qrc_smem_doubles(int m, int nb) {
   return size_t(3) * m * nb + 4 * size_t(nb) * nb + nb;
 }
@@ -231,7 +304,7 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(int m, int n, int nb
   const double* A = Ain + mat * in_stride;
   double* Q = Qall + mat * q_stride;
   double* R = Rall ? Rall + mat * r_stride : nullptr;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps_all = nt >> 5;
   const int c0 = q * nb;
   const int w = max(0, min(nb, n - c0));
   for (int e = tid; e < m * w; e += nt) {
@@ -250,59 +323,73 @@ __global__ void __launch_bounds__(QRC_THREADS) k_qr_cluster(int m, int n, int nb
   for (int p = 0; p < cs; ++p) {
     const int j0 = p * nb;
     const int wp = max(0, min(nb, n - j0));
-    if (p == q && warp == 0) {
+    if (p == q) {
+      // Panel factorisation.  Warp 0 forms reflector j; the other panel columns are then updated
+      // by one warp each (every warp sits on its own SM sub-partition and FP64 unit: one warp
+      // issues at most one FP64 instruction per ~64 cycles on this part).
       for (int j = 0; j < w; ++j) {
         const int r = j0 + j;
-        double* x = Acol + size_t(j) * m;
-        double part = 0.0;
-        for (int i = r + 1 + lane; i < m; i += 32) part += x[i] * x[i];
-        const double sigma = warp_sum(part);
-        const double alpha = x[r];
-        double beta, t, scale;
-        if (sigma == 0.0) {
-          t = 0.0; beta = alpha; scale = 0.0;
-        } else {
-          const double nrm = sqrt(alpha * alpha + sigma);
-          beta = alpha >= 0.0 ? -nrm : nrm;
-          t = (beta - alpha) / beta;
-          scale = 1.0 / (alpha - beta);
+        if (warp == 0) {
+          double* x = Acol + size_t(j) * m;
+          double part0 = 0.0, part1 = 0.0;
+          int i = r + 1 + lane;
+          for (; i + 32 < m; i += 64) {
+            part0 = fma(x[i], x[i], part0);
+            part1 = fma(x[i + 32], x[i + 32], part1);
+          }
+          if (i < m) part0 = fma(x[i], x[i], part0);
+          const double sigma = warp_sum(part0 + part1);
+          const double alpha = x[r];
+          double beta, t, scale;
+          householder_scalars(alpha, sigma, beta, t, scale);
+          __syncwarp();
+          for (int i2 = r + 1 + lane; i2 < m; i2 += 32) x[i2] *= scale;
+          if (lane == 0) {
+            x[r] = beta;
+            tau[j] = t;
+          }
         }
-        __syncwarp();
-        for (int i = r + 1 + lane; i < m; i += 32) x[i] *= scale;
-        if (lane == 0) {
-          x[r] = beta;
-          tau[j] = t;
-        }
-        __syncwarp();
-        for (int jj = j + 1; jj < w; ++jj) {
+        __syncthreads();
+        for (int jj = j + 1 + warp; jj < w; jj += nwarps_all) {
+          const double* x = Acol + size_t(j) * m;
           double* y = Acol + size_t(jj) * m;
           double sdot = 0.0;
-          for (int i = r + 1 + lane; i < m; i += 32) sdot += x[i] * y[i];
-          sdot = (warp_sum(sdot) + y[r]) * t;
+          for (int i = r + 1 + lane; i < m; i += 32) sdot = fma(x[i], y[i], sdot);
+          sdot = (warp_sum(sdot) + y[r]) * tau[j];
           __syncwarp();
           if (lane == 0) y[r] -= sdot;
           for (int i = r + 1 + lane; i < m; i += 32) y[i] -= sdot * x[i];
+        }
+        __syncthreads();
+      }
+      // T: T_ii = tau_i, T_{0:i, i} = -tau_i T_{0:i, 0:i} z_{0:i, i} with z_{l,i} = v_l . v_i,
+      // the w (w - 1) / 2 products one warp each, then the triangular recurrence in warp 0
+      const int npair = w * (w - 1) / 2;
+      for (int pidx = warp; pidx < npair; pidx += nwarps_all) {
+        int i = 1, base = 0;
+        while (base + i <= pidx) {
+          base += i;
+          ++i;
+        }
+        const int l = pidx - base;
+        const double* vi = Acol + size_t(i) * m;
+        const double* vl = Acol + size_t(l) * m;
+        double sdot = 0.0;
+        for (int row = j0 + i + 1 + lane; row < m; row += 32) sdot = fma(vl[row], vi[row], sdot);
+        sdot = warp_sum(sdot) + vl[j0 + i];
+        if (lane == 0) W[l * nb + i] = sdot;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        for (int i = 0; i < w; ++i) {
+          if (lane < i) {
+            double sacc = 0.0;
+            for (int l2 = lane; l2 < i; ++l2) sacc = fma(T[lane * nb + l2], W[l2 * nb + i], sacc);
+            T[lane * nb + i] = -tau[i] * sacc;
+          }
+          if (lane == 0) T[i * nb + i] = tau[i];
           __syncwarp();
         }
-      }
-      // T: T_ii = tau_i, T_{0:i, i} = -tau_i T_{0:i, 0:i} (V_{:, 0:i}^T v_i)
-      for (int i = 0; i < w; ++i) {
-        const double* vi = Acol + size_t(i) * m;
-        for (int l = 0; l < i; ++l) {
-          const double* vl = Acol + size_t(l) * m;
-          double sdot = 0.0;
-          for (int row = j0 + i + 1 + lane; row < m; row += 32) sdot += vl[row] * vi[row];
-          sdot = warp_sum(sdot) + vl[j0 + i];
-          if (lane == 0) W[l] = sdot;
-        }
-        __syncwarp();
-        if (lane < i) {
-          double sacc = 0.0;
-          for (int l2 = lane; l2 < i; ++l2) sacc += T[lane * nb + l2] * W[l2];
-          T[lane * nb + i] = -tau[i] * sacc;
-        }
-        if (lane == 0) T[i * nb + i] = tau[i];
-        __syncwarp();
       }
     }
     cl.sync();
@@ -773,6 +860,11 @@ void qr(Ctx& c, int count, int m, int n, int trans, const double* A, int64_t in_
     throw Error(QTT_ERR_UNSUPPORTED, "qr: matrix " + std::to_string(m) + "x" + std::to_string(n) + " too large for one CTA");
   k_qr<<<count, 256, sm, c.stream>>>(m, n, trans, A, Q, R, in_stride, q_stride, r_stride);
   after_launch(c, "qr");
+}
+
+void check_recip(Ctx& c, int n, const double* x_dev, double* err_dev) {
+  k_check_recip<<<1, 256, 0, c.stream>>>(n, x_dev, err_dev);
+  after_launch(c, "check_recip");
 }
 
 // Accurate SVD of small matrices: G (m x n, m >= n) = U diag(s) V^T.

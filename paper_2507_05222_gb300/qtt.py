@@ -79,6 +79,7 @@ _SIGS = {
     "qtt_ctx_profile_phases": (I, [P, DP, C.POINTER(C.c_int64)]),
     "qtt_qr": (I, [P, I, I, I, DP, DP, DP, I]),
     "qtt_ctx_set_cg_mode": (I, [P, I]),
+    "qtt_check_recip": (I, [P, I, DP, DP]),
     "qtt_profiler_range": (I, [I]),
     "qtt_mps_create": (I, [P, I, I, IP, DP, I, C.POINTER(P)]),
     "qtt_mps_free": (I, [P]),
@@ -416,6 +417,14 @@ def mps_dot_noalloc(n: int, d: int, a_bonds, a_cores_dev: int, b_bonds, b_cores_
     bb = np.ascontiguousarray(np.asarray(b_bonds, dtype=np.int32))
     _check(lib().mps_dot_noalloc(n, d, ab.ctypes.data_as(IP), a_cores_dev, bb.ctypes.data_as(IP), b_cores_dev,
                                  out_dev, stream))
+
+
+def qtt_check_recip(ctx: Context, x):
+    """Max relative errors (reciprocal, reciprocal square root) of the QR's Newton iterations."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    err = np.zeros(2)
+    _check(lib().qtt_check_recip(ctx.h, x.size, _dp(x), _dp(err)))
+    return float(err[0]), float(err[1])
 
 
 def qtt_qr(ctx: Context, A, trans: bool = False, path: int = 0):

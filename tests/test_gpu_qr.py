@@ -92,3 +92,15 @@ def test_qr_cluster_rejects_wide(ctx):
     from paper_2507_05222_gb300 import qtt
     with pytest.raises(qtt.QttError):
         qtt.qtt_qr(ctx, np.ones((8, 32)), path=2)
+
+
+def test_householder_scalar_reciprocals(ctx):
+    """The QR's Householder scalars use Newton-Raphson reciprocal and reciprocal square root
+    instead of FP64 division and square root: within ~2 ulp of CUDA's correctly rounded 1/x and
+    1/sqrt(x) over the whole normal range and near 1 (where column norms live)."""
+    from paper_2507_05222_gb300 import qtt
+    g = inputs.rng(4242)
+    x = np.concatenate([10.0 ** g.uniform(-300, 300, 20000), g.uniform(0.5, 2.0, 20000),
+                        1.0 + g.uniform(-1e-12, 1e-12, 1000), [1.0, 2.0, 4.0, 0.25, 1e-300, 1e300]])
+    e_rcp, e_rsqrt = qtt.qtt_check_recip(ctx, x)
+    assert e_rcp <= 4.5e-16 and e_rsqrt <= 4.5e-16
