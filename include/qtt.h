@@ -219,6 +219,17 @@ int qtt_sym_eig(qtt_ctx* ctx, int n, const double* S, double* w, double* V);
  * (QTT_ERR_UNSUPPORTED if the shape does not allow it).  Host buffers; R may be NULL;
  * synchronous. */
 int qtt_qr(qtt_ctx* ctx, int m, int n, int trans, const double* A, double* Q, double* R, int path);
+/* C = A B for row-major host matrices A (m x k), B (k x n), C (m x n); synchronous.  The product
+ * behind every core contraction of the sweeps (Sec. II.A).  path 0 uses the context's mode (see
+ * qtt_ctx_set_gemm_mode), 1 forces the FP64 pipe, 2 forces the tensor-core product: every row
+ * of A and column of B is split into seven 8-bit digits scaled by a power of two, digit products
+ * are summed exactly in FP32 on the bf16 tensor cores and combined in FP64 (Ozaki scheme; error
+ * ~2^-53 max_k|A_ik| sum_k|B_kj|). */
+int qtt_dgemm(qtt_ctx* ctx, int m, int n, int k, const double* A, const double* B, double* C, int path);
+/* Matrix products of the whole library: mode 0 sends products of at least 2^23 multiply-adds to
+ * the tensor cores (digit-split FP64), mode 1 (default) keeps every product on the FP64 pipe.
+ * Takes effect for work enqueued afterwards (a captured step keeps its kernels). */
+int qtt_ctx_set_gemm_mode(qtt_ctx* ctx, int mode);
 /* Self-check of the QR's Householder scalars: the maximum relative errors of its Newton-Raphson
  * reciprocal (err2[0]) and reciprocal square root (err2[1]) against CUDA's correctly rounded
  * 1/x and 1/sqrt(x) over the n positive host values x.  Synchronous. */

@@ -639,6 +639,7 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
   cs.drop_graph();
   init_kernel_attributes();
   cg_init_attributes();
+  init_ozaki_attributes();
   for (int i = 0; i < 4; ++i) worker(c, i);
   if (!cs.gstream) QTT_CUDA(cudaStreamCreateWithFlags(&cs.gstream, cudaStreamNonBlocking));
   if (!cs.ev_in) QTT_CUDA(cudaEventCreateWithFlags(&cs.ev_in, cudaEventDisableTiming));

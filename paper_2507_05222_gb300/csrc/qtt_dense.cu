@@ -363,6 +363,10 @@ void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, 
     after_launch(c, "splitk_reduce");
     return;
   }
+  if (c.root->gemm_mode == 0 && batch * M * N * K >= (int64_t(1) << 23) && M >= 16 && N >= 16 && K >= 16) {
+    gemm_ozaki(c, batch, M, N, K, alpha, A, sAb, sAm, sAk, B, sBb, sBk, sBn, beta, C, sCb, sCm, sCn);
+    return;
+  }
   // Tile and split-K choice.  On GB300 an SM retires 2 FP64 FMAs per cycle, so the FP64 pipe,
   // not shared-memory or L2 traffic, bounds these kernels at any tile size >= 16: the time is
   // about the FMA load of the busiest SM, ceil(CTAs / SMs) T^2 kchunk / 2 cycles, plus one more

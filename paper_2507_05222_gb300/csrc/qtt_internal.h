@@ -143,6 +143,9 @@ struct Ctx {
   // ALS local solves: 0 = one cooperative kernel per solve where the shapes allow it,
   // 1 = one kernel per contraction and CG update (read from the root context).
   int cg_mode = 0;
+  // Matrix products: 0 = products of >= 2^23 multiply-adds on the tensor cores (digit
+  // splitting, see qtt_ozaki.cu), the rest on the FP64 pipe; 1 = everything on the FP64 pipe.
+  int gemm_mode = 1;
   Profiler prof;
 };
 
@@ -221,6 +224,11 @@ void permute(Ctx& c, const double* in, int nd, const int64_t* in_dim, const int*
 
 // Elementwise helpers (device pointers, count n).
 void fill(Ctx& c, double* x, int64_t n, double v);
+// FP64-accurate product on the bf16 tensor cores (qtt_ozaki.cu); same arguments as gemm.
+void gemm_ozaki(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sAb,
+                int64_t sAm, int64_t sAk, const double* B, int64_t sBb, int64_t sBk, int64_t sBn, double beta,
+                double* C, int64_t sCb, int64_t sCm, int64_t sCn);
+void init_ozaki_attributes();   // kernel attributes, once (before any stream capture)
 void copy(Ctx& c, double* dst, const double* src, int64_t n);
 void axpby(Ctx& c, int64_t n, double a, const double* x, double b, double* y);  // y = a x + b y
 // Deterministic dot product into a device scalar.

@@ -80,6 +80,8 @@ _SIGS = {
     "qtt_qr": (I, [P, I, I, I, DP, DP, DP, I]),
     "qtt_ctx_set_cg_mode": (I, [P, I]),
     "qtt_check_recip": (I, [P, I, DP, DP]),
+    "qtt_dgemm": (I, [P, I, I, I, DP, DP, DP, I]),
+    "qtt_ctx_set_gemm_mode": (I, [P, I]),
     "qtt_profiler_range": (I, [I]),
     "qtt_mps_create": (I, [P, I, I, IP, DP, I, C.POINTER(P)]),
     "qtt_mps_free": (I, [P]),
@@ -204,6 +206,10 @@ class Context:
                                      n.ctypes.data_as(C.POINTER(C.c_int64))))
         return {k: dict(ms=float(ms[i]), flops=float(fl[i]), launches=int(n[i]))
                 for i, k in enumerate(self.PROFILE_CLASSES)}
+
+    def set_gemm_mode(self, mode: int):
+        """0: large products on the tensor cores (digit-split FP64); 1: FP64 pipe only."""
+        _check(lib().qtt_ctx_set_gemm_mode(self.h, int(mode)))
 
     def set_cg_mode(self, mode: int):
         """0: one cooperative kernel per ALS local CG solve (default); 1: one kernel per stage."""
@@ -417,6 +423,19 @@ def mps_dot_noalloc(n: int, d: int, a_bonds, a_cores_dev: int, b_bonds, b_cores_
     bb = np.ascontiguousarray(np.asarray(b_bonds, dtype=np.int32))
     _check(lib().mps_dot_noalloc(n, d, ab.ctypes.data_as(IP), a_cores_dev, bb.ctypes.data_as(IP), b_cores_dev,
                                  out_dev, stream))
+
+
+def qtt_dgemm(ctx: Context, A, B, path: int = 0):
+    """A @ B on the device (row-major FP64); path 0 context mode, 1 FP64 pipe, 2 tensor cores."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.float64))
+    m, k = A.shape
+    k2, n = B.shape
+    if k2 != k:
+        raise ValueError("inner dimensions differ")
+    Cm = np.zeros((m, n))
+    _check(lib().qtt_dgemm(ctx.h, m, n, k, _dp(A), _dp(B), _dp(Cm), int(path)))
+    return Cm
 
 
 def qtt_check_recip(ctx: Context, x):

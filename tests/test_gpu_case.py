@@ -190,3 +190,31 @@ def test_cg_one_kernel_equals_per_stage(ctx, ne, nx, chi):
     for i, j in zip(ia, ib):
         for k in ("cg_u", "cg_v", "cg_p"):
             assert abs(i[k] - j[k]) <= 1
+
+
+def test_tensor_core_products_equal_fp64_pipe(ctx):
+    """A step whose large contractions (chi = 64: 4096 x 128 x 64 environment products) run on
+    the tensor cores by digit splitting equals the same step with every product on the FP64
+    pipe, within the oracle parity bar after one step (plus the ~1e3-fold amplification of
+    rounding differences by unconverged CG that the one-kernel CG test measures)."""
+    from paper_2507_05222_gb300 import qtt
+    ne = nx = 6
+    R, Re, dt, chi = 40.0, 100.0, 2e-3, 64
+    ops = Q.Ops(ne, nx, R, Re, dt, "interleaved")
+    _, (gu, gv, gp), _ = make_state(ctx, ops, ne, nx, chi)
+    out = []
+    try:
+        for mode in (0, 1):
+            ctx.set_gemm_mode(mode)
+            case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=1, mom=(1, 8, 1e-12),
+                            poi=(2, 20, 1e-12))
+            case.set_state(gu, gv, gp)
+            info = case.fractional_step(1, with_forces=False)
+            out.append(([qtt.qtt_decode(ctx, x) for x in case.get_state()], info))
+    finally:
+        ctx.set_gemm_mode(1)
+    (a, ia), (b, ib) = out
+    for x, y in zip(a, b):
+        assert rel(x, y) < 1e-9
+    for k in ("cg_u", "cg_v", "cg_p"):
+        assert abs(ia[0][k] - ib[0][k]) <= 2
