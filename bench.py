@@ -139,6 +139,8 @@ def run_ours(args, cfg):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     ctx = qtt.Context(local)
+    if args.gemm_mode is not None:
+        ctx.set_gemm_mode(args.gemm_mode)
     ne, nx, chi = cfg["n_eta"], cfg["n_xi"], cfg["chi"]
     case = qtt.Case(ctx, ne, nx, cfg["R"], cfg["Re"], cfg["dt"], chi, cfg["ordering"], fit_sweeps=cfg["fit_sweeps"],
                     mom=cfg["mom"], poi=cfg["poi"])
@@ -258,7 +260,7 @@ def run_ours(args, cfg):
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                             "kernel": "k_gemm (FP64 core contractions)",
+                             "kernel": "core contractions: k_gemm (FP64 pipe) + k_oz_gemm (digit-split FP64 on the tensor cores), FP64-equivalent flops",
                              "share_of_step": g["ms"] / nprof / step_ms if step_ms > 0 else None},
                 "kernel_classes_ms_per_step": {k: v["ms"] / nprof for k, v in prof.items() if not k.startswith("phase")},
                 "phase_ms_last_timed_step": phases,
@@ -280,6 +282,8 @@ def main():
     ap.add_argument("--chi", type=int, default=None)
     ap.add_argument("--profile-one-step", action="store_true",
                     help="set up, one warm-up step, then one step between cudaProfilerStart/Stop (for ncu)")
+    ap.add_argument("--gemm-mode", type=int, default=None, choices=(0, 1),
+                    help="0: large products on the tensor cores (digit-split FP64); 1: FP64 pipe")
     ap.add_argument("--phase-breakdown", action="store_true",
                     help="print kernel-class time by step phase (diagnostic; no bench line)")
     ap.add_argument("--kernel-probe", action="store_true",

@@ -226,8 +226,8 @@ int qtt_qr(qtt_ctx* ctx, int m, int n, int trans, const double* A, double* Q, do
  * are summed exactly in FP32 on the bf16 tensor cores and combined in FP64 (Ozaki scheme; error
  * ~2^-53 max_k|A_ik| sum_k|B_kj|). */
 int qtt_dgemm(qtt_ctx* ctx, int m, int n, int k, const double* A, const double* B, double* C, int path);
-/* Matrix products of the whole library: mode 0 sends products of at least 2^23 multiply-adds to
- * the tensor cores (digit-split FP64), mode 1 (default) keeps every product on the FP64 pipe.
+/* Matrix products of the whole library: mode 0 (default) sends products of at least 2^23
+ * multiply-adds to the tensor cores (digit-split FP64), mode 1 keeps every product on the FP64 pipe.
  * Takes effect for work enqueued afterwards (a captured step keeps its kernels). */
 int qtt_ctx_set_gemm_mode(qtt_ctx* ctx, int mode);
 /* Self-check of the QR's Householder scalars: the maximum relative errors of its Newton-Raphson

@@ -145,7 +145,7 @@ struct Ctx {
   int cg_mode = 0;
   // Matrix products: 0 = products of >= 2^23 multiply-adds on the tensor cores (digit
   // splitting, see qtt_ozaki.cu), the rest on the FP64 pipe; 1 = everything on the FP64 pipe.
-  int gemm_mode = 1;
+  int gemm_mode = 0;
   Profiler prof;
 };
 

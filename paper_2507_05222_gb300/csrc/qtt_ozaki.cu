@@ -8,9 +8,10 @@
 //     balanced base-256 digits, A_ik = 2^e_i sum_s a_s 2^-8s + r, |a_s| <= 128,
 //     |r| <= 2^-57 2^e_i; columns of B likewise (exponents f_j, digits b_u);
 //   * digits are integers of at most 8 bits, exact in bf16; a digit product is exact in FP32, and
-//     every sum of (t - 1) <= 7 digit products over at most 128 k stays below 2^24, so the tensor
+//     every sum of (t - 1) <= 7 digit products over at most 64 k stays below 2^24, so the tensor
 //     core's FP32 accumulation of G_t = sum_{s+u=t} sum_k a_s b_u is exact for t <= 8;
-//   * C_ij = 2^(e_i + f_j) sum_{t=2}^{S+1} 2^-8t G_t, combined in FP64, chunk by chunk.
+//   * C_ij = 2^(e_i + f_j) sum_{t=2}^{S+1} 2^-8t G_t, accumulated exactly as a 128-bit integer
+//     (integer adds only) and converted to FP64 once per output.
 // Dropped digit products (s + u > S + 1) and the splitting remainders bound the error by
 // ~2^-53 max_k |A_ik| sum_k |B_kj| (the FP64 GEMM bound is k eps sum_k |A_ik||B_kj|): the two
 // agree to rounding for operands whose rows (columns) do not span many orders of magnitude.
@@ -25,10 +26,10 @@ namespace qtt {
 namespace {
 
 constexpr int OZ_S = 7;            // digits per operand
-constexpr int OZ_KC = 128;         // k per chunk of exact FP32 accumulation
-constexpr int OZ_BM = 64;          // rows of A per CTA (4 warps x 16)
+constexpr int OZ_KC = 64;          // k per chunk of exact FP32 accumulation
+constexpr int OZ_BM = 128;         // rows of A per CTA (8 warps x 16)
 constexpr int OZ_BN = 32;          // columns of B per CTA (4 n8 tiles)
-constexpr int OZ_THREADS = 128;
+constexpr int OZ_THREADS = 256;
 
 // Exponent of each row r of X (R rows of K values, strides sR, sK; batch stride sB):
 // ex[b R + r] = e with max_k |X_rk| 2^-e < 1/2 (0 for a zero row).  One warp per row.
@@ -105,6 +106,45 @@ __global__ void k_oz_digits(int64_t batch, int64_t R, int64_t K, int64_t Kp, con
   }
 }
 
+// (hi 2^64 + lo) 2^E as a double, rounded to nearest even, by integer operations on the bit
+// pattern (the FP64 unit of this part is ~64x slower than its integer units).  |value| < 2^127.
+__device__ __forceinline__ double fixed_to_double(long long hi, unsigned long long lo, int E) {
+  const bool neg = hi < 0;
+  unsigned long long h = static_cast<unsigned long long>(hi), l = lo;
+  if (neg) {
+    l = ~l + 1ull;
+    h = ~h + (l == 0ull ? 1ull : 0ull);
+  }
+  if (h == 0ull && l == 0ull) return 0.0;
+  // normalise so that bit 127 is set
+  const int lz = h ? __clzll(static_cast<long long>(h)) : 64 + __clzll(static_cast<long long>(l));
+  if (lz >= 64) {
+    h = l << (lz - 64);
+    l = 0ull;
+  } else if (lz > 0) {
+    h = (h << lz) | (l >> (64 - lz));
+    l <<= lz;
+  }
+  unsigned long long m = h >> 11;                                  // 53 bits
+  const bool guard = (h >> 10) & 1ull;
+  const bool sticky = ((h & 0x3ffull) != 0ull) || (l != 0ull);
+  int X = 127 - lz + E;                                           // exponent of the leading bit
+  if (guard && (sticky || (m & 1ull))) {
+    ++m;
+    if (m == (1ull << 53)) {
+      m >>= 1;
+      ++X;
+    }
+  }
+  if (X < -1022 || X > 1023) {                                    // outside the normal range
+    const double r = scalbn(static_cast<double>(m), X - 52);
+    return neg ? -r : r;
+  }
+  const unsigned long long bits = (neg ? (1ull << 63) : 0ull) | (static_cast<unsigned long long>(X + 1023) << 52) |
+                                  (m & 0xfffffffffffffull);
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
 // 16-byte global -> shared copy that does not stall the thread; full = false writes zeros.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool full) {
   const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
@@ -127,7 +167,7 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 }
 
 // C = alpha A B + beta C from the digit slices of A (rows) and of B (columns).  CTA tile
-// 64 x 32, warp w owns rows 16w..16w+15 and all 32 columns (four m16n8k16 tiles).  Shared
+// 128 x 32, warp w owns rows 16w..16w+15 and all 32 columns (four m16n8k16 tiles).  Shared
 // memory holds the S digit slices of the tile for one k chunk, rows padded by 8 bf16 (16 bytes)
 // so that ldmatrix rows fall on distinct banks.  Split K: blockIdx.z = b splits + sp covers
 // k in [sp ksplit, (sp + 1) ksplit); with splits > 1 the (alpha-scaled) partial products go to
@@ -147,11 +187,18 @@ __global__ void __launch_bounds__(OZ_THREADS)
   const int sp = blockIdx.z % splits;
   const int64_t kbeg = sp * ksplit, kend = min(Kp, kbeg + ksplit);
   const int64_t m0 = int64_t(blockIdx.y) * OZ_BM, n0 = int64_t(blockIdx.x) * OZ_BN;
-  double acc[4][4];
+  // Exact fixed-point accumulators (value = hi 2^64 + lo, in units of 2^-64 2^(e_i + f_j)):
+  // each group sum G_t (an integer below 2^24 per chunk) enters shifted left by 8 (8 - t) bits,
+  // with integer adds only -- the FP64 pipe is touched once per output, at the end.
+  unsigned long long lo[4][4];
+  long long hi[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[i][q] = 0.0;
+    for (int q = 0; q < 4; ++q) {
+      lo[i][q] = 0ull;
+      hi[i][q] = 0ll;
+    }
   for (int64_t k0 = kbeg; k0 < kend; k0 += kc) {
     const int kw = int(kend - k0 < int64_t(kc) ? kend - k0 : int64_t(kc));   // multiple of 16
     const int v8 = kw / 8;                                                    // 16-byte vectors per row
@@ -196,11 +243,28 @@ __global__ void __launch_bounds__(OZ_THREADS)
           mma_bf16(c32[3], a, b23[2], b23[3]);
         }
       }
-      const double sc = scalbn(1.0, -8 * t);
+      const int shift = 8 * (OZ_S + 1 - t);   // 0 .. 48
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[i][q] = fma(double(c32[i][q]), sc, acc[i][q]);
+        for (int q = 0; q < 4; ++q) {
+          // exact integer, |G| < 2^24; the 32-bit conversion stays off the FP64 unit
+          const long long G = static_cast<long long>(__float2int_rz(c32[i][q]));
+          unsigned long long add_lo;
+          long long add_hi;
+          if (shift >= 32) {
+            const long long v = G << (shift - 32);            // |v| < 2^40: value v 2^32
+            add_lo = static_cast<unsigned long long>(v) << 32;
+            add_hi = v >> 32;
+          } else {
+            const long long v = G << shift;                   // |v| < 2^56
+            add_lo = static_cast<unsigned long long>(v);
+            add_hi = v >> 63;                                 // sign extension
+          }
+          const unsigned long long nl = lo[i][q] + add_lo;
+          hi[i][q] += add_hi + (nl < add_lo ? 1 : 0);
+          lo[i][q] = nl;
+        }
     }
   }
   const int g = lane >> 2, tg = lane & 3;
@@ -211,7 +275,8 @@ __global__ void __launch_bounds__(OZ_THREADS)
       const int64_t gm = m0 + warp * 16 + g + (q >= 2 ? 8 : 0);
       const int64_t gn = n0 + i * 8 + 2 * tg + (q & 1);
       if (gm >= M || gn >= N) continue;
-      const double v = alpha * scalbn(acc[i][q], ea[b * M + gm] + eb[b * N + gn]);
+      double v = fixed_to_double(hi[i][q], lo[i][q], ea[b * M + gm] + eb[b * N + gn] - 8 * (OZ_S + 1));
+      if (alpha != 1.0) v *= alpha;
       if (W) {
         W[((int64_t(sp) * batch + b) * M + gm) * N + gn] = v;
       } else {

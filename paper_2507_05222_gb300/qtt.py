@@ -208,7 +208,7 @@ class Context:
                 for i, k in enumerate(self.PROFILE_CLASSES)}
 
     def set_gemm_mode(self, mode: int):
-        """0: large products on the tensor cores (digit-split FP64); 1: FP64 pipe only."""
+        """0 (default): large products on the tensor cores (digit-split FP64); 1: FP64 pipe only."""
         _check(lib().qtt_ctx_set_gemm_mode(self.h, int(mode)))
 
     def set_cg_mode(self, mode: int):

@@ -212,7 +212,7 @@ def test_tensor_core_products_equal_fp64_pipe(ctx):
             info = case.fractional_step(1, with_forces=False)
             out.append(([qtt.qtt_decode(ctx, x) for x in case.get_state()], info))
     finally:
-        ctx.set_gemm_mode(1)
+        ctx.set_gemm_mode(0)
     (a, ia), (b, ib) = out
     for x, y in zip(a, b):
         assert rel(x, y) < 1e-9

@@ -84,5 +84,5 @@ def test_dispatch_of_large_products(ctx):
         try:
             C = qtt.qtt_dgemm(ctx, A, B, path=0)
         finally:
-            ctx.set_gemm_mode(1)
+            ctx.set_gemm_mode(0)
         assert np.all(np.abs(C - ref) <= 2 * fp64_bound(A, B) + 4 * bound(A, B))
