@@ -41,17 +41,14 @@ __global__ void k_oz_rowexp(int64_t batch, int64_t R, int64_t K, const double* _
   if (wid >= batch * R) return;
   const int64_t b = wid / R, r = wid - b * R;
   const double* x = X + b * sB + r * sR;
-  double m = 0.0;
-  for (int64_t k = lane; k < K; k += 32) m = fmax(m, fabs(x[k * sK]));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) {
-    int e = 0;
-    if (m > 0.0) {
-      frexp(m, &e);   // m < 2^e
-      e += 1;         // |x| 2^-e < 1/2
-    }
-    ex[b * R + r] = e;
-  }
+  // largest exponent field of the row (integer operations only: the FP64 unit is slow here)
+  int mx = 0;
+  for (int64_t k = lane; k < K; k += 32)
+    mx = max(mx, int((static_cast<unsigned long long>(__double_as_longlong(x[k * sK])) >> 52) & 0x7ff));
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  // max |x| < 2^(mx - 1022), so e = mx - 1021 gives |x| 2^-e < 1/2 (rows of zeros and subnormals:
+  // e = 0, their digits vanish -- an absolute error below 2^-1021)
+  if (lane == 0) ex[b * R + r] = mx > 0 ? mx - 1021 : 0;
 }
 
 // The S digits of every element, by integer arithmetic on the FP64 bit pattern: the element
