@@ -520,73 +520,80 @@ __global__ void __launch_bounds__(256) k_svd_jacobi(int m, int n, const double* 
 // ------------------------------------------------------------------ symmetric Jacobi (FP32)
 // S: n x n FP64 row-major symmetric.  V (FP64 out, row-major n x n): eigenvectors as columns.
 // With t0_dev != null only the trailing block S[t0:, t0:] is diagonalised (t0 read on the
-// device) and Vout is the identity outside that block.  1024 threads.
+// device) and Vout is the identity outside that block.  1024 threads per CTA.
 // Parallel cyclic (round-robin) ordering: each round rotates n/2 disjoint pairs (p_k, q_k).
 // The round's two-sided update A <- J^T A J is done in one pass over 2 x 2 blocks: block
-// (k, l) of A (rows p_k, q_k; columns p_l, q_l) becomes R_k B R_l^T, so each element is loaded
-// and stored once per round, and only blocks k <= l are computed (the mirror is stored), which
-// halves the FP32 work of the rotation; V's columns are rotated in the same pass.  Sweeps stop
-// when the off-diagonal mass falls below off_tol2 of the total (squared Frobenius norms) -- the
-// FP64 refinement that follows only needs a start it converges from quadratically.
+// (k, l) of A (rows p_k, q_k; columns p_l, q_l) becomes R_k B R_l^T.  Only the upper triangle
+// of A is kept: element (i, j) lives at (min, max), blocks k <= l cover every upper element
+// once, so each is loaded and stored once per round with no mirror store.
+// The eigenvector rows are independent under column rotations, so the grid's CTAs each keep a
+// full copy of A and a slab of V's rows: every CTA runs the same rotations in the same order
+// (no atomics, fixed reduction orders, so their A copies and decisions are bitwise equal) and
+// rotates only its own slab, with no communication between CTAs.  Sweeps stop when the
+// off-diagonal mass falls below off_tol2 of the total (squared Frobenius norms) -- the FP64
+// refinement that follows only needs a start it converges from quadratically.
+constexpr int JAC_MAX_BLOCKS_PER_THREAD = 4;   // n <= 160: 80 pairs, 3240 blocks <= 4 x 1024
 __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __restrict__ S, double* __restrict__ Vout,
                                                      int max_sweeps, const int* __restrict__ t0_dev, float off_tol2) {
   extern __shared__ float smf[];
   const int t0 = t0_dev ? *t0_dev : 0;
   const int n = nfull - t0;
+  const int G = gridDim.x, g = blockIdx.x;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   if (t0_dev) {
-    for (int i = threadIdx.y; i < nfull; i += 32)
-      for (int j = threadIdx.x; j < nfull; j += 32)
+    for (int i = g + G * ty; i < nfull; i += 32 * G)
+      for (int j = tx; j < nfull; j += 32)
         if (i < t0 || j < t0) Vout[size_t(i) * nfull + j] = (i == j) ? 1.0 : 0.0;
   }
   if (n <= 1) {
-    if (n == 1 && threadIdx.x == 0 && threadIdx.y == 0) Vout[size_t(t0) * nfull + t0] = 1.0;
+    if (n == 1 && g == 0 && tid == 0) Vout[size_t(t0) * nfull + t0] = 1.0;
     return;
   }
   const int ld = n + 1;                 // padded rows: column walks are bank-conflict free
   const int np = (n + 1) & ~1;
   const int npairs = np / 2;
   const int nblocks = npairs * (npairs + 1) / 2;
-  float* A = smf;                       // n x ld
-  float* V = A + size_t(n) * ld;        // n x ld (row i = component i, column = vector)
-  float* cs = V + size_t(n) * ld;       // npairs
-  float* sn = cs + npairs;              // npairs
-  int* pp = reinterpret_cast<int*>(sn + npairs);
-  int* qq = pp + npairs;
-  unsigned short* blk = reinterpret_cast<unsigned short*>(qq + npairs);   // (k << 8 | l), k <= l
-  __shared__ float red[32];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int r0 = (g * n) / G, r1 = ((g + 1) * n) / G;   // this CTA's rows of V
+  float* A = smf;                       // n x ld, upper triangle used
+  float* V = A + size_t(n) * ld;        // (r1 - r0) x ld: row i = component r0 + i
+  const size_t poff = (size_t(n) * ld + size_t(n / G + 1) * ld + 1) & ~size_t(1);   // 8-byte aligned
+  float2* cs = reinterpret_cast<float2*>(smf + poff);
+  int2* pq = reinterpret_cast<int2*>(cs + npairs);
+  __shared__ float red[2][32];
   for (int i = ty; i < n; i += 32)
-    for (int j = tx; j < n; j += 32) {
-      A[i * ld + j] = float(S[size_t(i + t0) * nfull + (j + t0)]);
-      V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+    for (int j = i + tx; j < n; j += 32) A[i * ld + j] = float(S[size_t(i + t0) * nfull + (j + t0)]);
+  for (int i = ty; i < r1 - r0; i += 32)
+    for (int j = tx; j < n; j += 32) V[i * ld + j] = (r0 + i == j) ? 1.0f : 0.0f;
+  // this thread's blocks (k, l), k <= l, for blocks e = tid + 1024 b
+  int bk[JAC_MAX_BLOCKS_PER_THREAD], bl[JAC_MAX_BLOCKS_PER_THREAD];
+#pragma unroll
+  for (int b = 0; b < JAC_MAX_BLOCKS_PER_THREAD; ++b) {
+    int e = tid + 1024 * b, k = 0;
+    bk[b] = -1; bl[b] = -1;
+    if (e < nblocks) {
+      while (e >= npairs - k) { e -= npairs - k; ++k; }
+      bk[b] = k; bl[b] = k + e;
     }
-  for (int k = tid; k < npairs; k += 1024) {
-    int base = k * npairs - k * (k - 1) / 2;
-    for (int l = k; l < npairs; ++l) blk[base + (l - k)] = (unsigned short)((k << 8) | l);
   }
   __syncthreads();
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // convergence test: off-diagonal mass relative to the total
-    float off = 0.f, tot = 0.f;
-    for (int i = ty; i < n; i += 32)
-      for (int j = tx; j < n; j += 32) {
+    // convergence test: off-diagonal mass relative to the total (upper triangle counted twice)
+    float off = 0.f, dia = 0.f;
+    for (int i = ty; i < n; i += 32) {
+      for (int j = i + tx; j < n; j += 32) {
         float a = A[i * ld + j];
-        tot += a * a;
-        if (i != j) off += a * a;
+        if (j == i) dia += a * a; else off += a * a;
       }
+    }
     off = warp_sumf(off);
-    tot = warp_sumf(tot);
-    if (tx == 0) red[ty] = off;
+    dia = warp_sumf(dia);
+    if (tx == 0) { red[0][ty] = off; red[1][ty] = dia; }
     __syncthreads();
-    float offs = 0.f;
-    for (int i = 0; i < 32; ++i) offs += red[i];
+    float offs = 0.f, dias = 0.f;
+    for (int i = 0; i < 32; ++i) { offs += red[0][i]; dias += red[1][i]; }
     __syncthreads();
-    if (tx == 0) red[ty] = tot;
-    __syncthreads();
-    float tots = 0.f;
-    for (int i = 0; i < 32; ++i) tots += red[i];
-    __syncthreads();
-    if (!(offs > off_tol2 * tots)) break;
+    offs *= 2.f;
+    if (!(offs > off_tol2 * (offs + dias))) break;
     for (int r = 0; r < np - 1; ++r) {
       if (tid < npairs) {
         const int k = tid;
@@ -610,51 +617,55 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
             s = t * c;
           }
         }
-        pp[k] = p; qq[k] = q; cs[k] = c; sn[k] = s;
+        pq[k] = make_int2(p, q);
+        cs[k] = make_float2(c, s);
       }
       __syncthreads();
       // A <- J^T A J: block (k, l) = R_k B R_l^T with R = [c -s; s c] acting on (p, q)
-      for (int e = tid; e < nblocks; e += 1024) {
-        const unsigned short kl = blk[e];
-        const int k = kl >> 8, l = kl & 0xff;
-        const int p1 = pp[k], q1 = qq[k], p2 = pp[l], q2 = qq[l];
-        const float c1 = cs[k], s1 = sn[k], c2 = cs[l], s2 = sn[l];
+#pragma unroll
+      for (int b = 0; b < JAC_MAX_BLOCKS_PER_THREAD; ++b) {
+        if (bk[b] < 0) break;
+        const int k = bk[b], l = bl[b];
+        const int2 pq1 = pq[k], pq2 = pq[l];
+        const float2 r1v = cs[k], r2v = cs[l];
+        const int p1 = pq1.x, q1 = pq1.y, p2 = pq2.x, q2 = pq2.y;
+        const float c1 = r1v.x, s1 = r1v.y, c2 = r2v.x, s2 = r2v.y;
         const bool h1 = q1 < n, h2 = q2 < n;   // a pair with q >= n is a lone index (odd n)
-        const float b00 = A[p1 * ld + p2];
-        const float b01 = h2 ? A[p1 * ld + q2] : 0.f;
-        const float b10 = h1 ? A[q1 * ld + p2] : 0.f;
-        const float b11 = (h1 && h2) ? A[q1 * ld + q2] : 0.f;
+        // upper-triangle addresses of (p1, p2), (p1, q2), (q1, p2), (q1, q2); for k == l the
+        // two off-diagonal entries are the same element
+        const int a00 = p1 <= p2 ? p1 * ld + p2 : p2 * ld + p1;
+        const int a01 = p1 <= q2 ? p1 * ld + q2 : q2 * ld + p1;
+        const int a10 = q1 <= p2 ? q1 * ld + p2 : p2 * ld + q1;
+        const int a11 = q1 <= q2 ? q1 * ld + q2 : q2 * ld + q1;
+        const float b00 = A[a00];
+        const float b01 = h2 ? A[a01] : 0.f;
+        const float b10 = h1 ? A[a10] : 0.f;
+        const float b11 = (h1 && h2) ? A[a11] : 0.f;
         const float t00 = c1 * b00 - s1 * b10, t01 = c1 * b01 - s1 * b11;
         const float t10 = s1 * b00 + c1 * b10, t11 = s1 * b01 + c1 * b11;
         const float n00 = c2 * t00 - s2 * t01, n01 = s2 * t00 + c2 * t01;
         const float n10 = c2 * t10 - s2 * t11, n11 = s2 * t10 + c2 * t11;
-        A[p1 * ld + p2] = n00;
-        if (h2) A[p1 * ld + q2] = n01;
-        if (h1) A[q1 * ld + p2] = n10;
-        if (h1 && h2) A[q1 * ld + q2] = n11;
-        if (k != l) {
-          A[p2 * ld + p1] = n00;
-          if (h2) A[q2 * ld + p1] = n01;
-          if (h1) A[p2 * ld + q1] = n10;
-          if (h1 && h2) A[q2 * ld + q1] = n11;
-        }
+        A[a00] = n00;
+        if (h2) A[a01] = n01;
+        if (h1 && k != l) A[a10] = n10;
+        if (h1 && h2) A[a11] = n11;
       }
-      // columns p, q of V (independent of the A update)
+      // columns p, q of this CTA's rows of V (independent of the A update)
       for (int k = ty; k < npairs; k += 32) {
-        const int p = pp[k], q = qq[k];
-        if (q >= n) continue;
-        const float c = cs[k], s = sn[k];
-        for (int i = tx; i < n; i += 32) {
-          float x = V[i * ld + p], y = V[i * ld + q];
-          V[i * ld + p] = c * x - s * y;
-          V[i * ld + q] = s * x + c * y;
+        const int2 pqk = pq[k];
+        if (pqk.y >= n) continue;
+        const float2 r = cs[k];
+        for (int i = tx; i < r1 - r0; i += 32) {
+          float x = V[i * ld + pqk.x], y = V[i * ld + pqk.y];
+          V[i * ld + pqk.x] = r.x * x - r.y * y;
+          V[i * ld + pqk.y] = r.y * x + r.x * y;
         }
       }
       __syncthreads();
     }
   }
-  for (int i = ty; i < n; i += 32)
-    for (int j = tx; j < n; j += 32) Vout[size_t(i + t0) * nfull + (j + t0)] = double(V[i * ld + j]);
+  for (int i = ty; i < r1 - r0; i += 32)
+    for (int j = tx; j < n; j += 32) Vout[size_t(r0 + i + t0) * nfull + (j + t0)] = double(V[i * ld + j]);
 }
 
 // First index of the sorted (descending) spectrum below tau * lambda_0; n if none.  Also
@@ -911,6 +922,13 @@ static void oa_iteration(Ctx& c, int n, const double* S, double* X, double* XtX,
 // levels 2 and 3 re-diagonalise the trailing block of X^T S X (the eigenvalues below
 // 1e-5 and 1e-10 of the largest) on its own scale and refine again.  Levels with fewer than
 // two tail eigenvalues are skipped on the device.
+// Each tail level starts with one Newton-Schulz step on X: the last refinement of a level can
+// take a large first-order step for a tail pair that the level could not yet resolve (its
+// Rayleigh quotients drift apart by more than the threshold while their coupling is still at
+// the previous level's FP32 resolution), which leaves X^T X - I near 1e-3.  The tail block of
+// X^T S X is a Rayleigh-Ritz projection only for an orthonormal X; with X^T X - I at 1e-3 the
+// re-diagonalised tail pairs keep couplings of ~1e-3 of their scale, and the same large step
+// recurs in the next level's last refinement, where nothing repairs it.
 // FP32 Jacobi stopping thresholds (squared off-diagonal mass over squared total) before the
 // level-0 and the tail-level refinements.
 #ifndef QTT_JAC_TOL2_FULL
@@ -919,15 +937,21 @@ static void oa_iteration(Ctx& c, int n, const double* S, double* X, double* XtX,
 #ifndef QTT_JAC_TOL2_TAIL
 #define QTT_JAC_TOL2_TAIL 1e-12f
 #endif
+#ifndef QTT_JAC_CTAS
+#define QTT_JAC_CTAS 4
+#endif
 constexpr float JAC_TOL2_FULL = QTT_JAC_TOL2_FULL;
 constexpr float JAC_TOL2_TAIL = QTT_JAC_TOL2_TAIL;
 
 void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
   QTT_CHECK_ARG(n >= 1, "eigh: n >= 1");
   if (n > 160) throw Error(QTT_ERR_UNSUPPORTED, "eigh: n > 160 not supported");
+  // FP32 Jacobi: QTT_JAC_CTAS CTAs share the eigenvector rows for the larger matrices (each
+  // keeps all of A)
+  const int jac_ctas = n >= 64 ? QTT_JAC_CTAS : 1;
   const size_t npairs = size_t((n + 1) & ~1) / 2;
-  size_t smf = (size_t(n) * (n + 1) * 2 + 2 * npairs) * sizeof(float) + 2 * npairs * sizeof(int) +
-               npairs * (npairs + 1) / 2 * sizeof(unsigned short);
+  const size_t smf = ((size_t(n) * (n + 1) + size_t(n / jac_ctas + 1) * (n + 1) + 1) & ~size_t(1)) * sizeof(float) +
+                     npairs * (sizeof(float2) + sizeof(int2));
   init_kernel_attributes();
   const size_t nn = size_t(n) * n;
   DBuf X(&c, nn), Xs(&c, nn), XtX(&c, nn), AX(&c, nn), SX(&c, nn), E(&c, nn), Y(&c, nn), lam(&c, size_t(n)),
@@ -936,7 +960,7 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
   int* need = t0 + 1;
   {
     ProfScope ps(c, KC_EIG);
-    k_jacobi_f32<<<1, dim3(32, 32), smf, c.stream>>>(n, S, X.p, 10, nullptr, JAC_TOL2_FULL);
+    k_jacobi_f32<<<jac_ctas, dim3(32, 32), smf, c.stream>>>(n, S, X.p, 10, nullptr, JAC_TOL2_FULL);
     after_launch(c, "jacobi_f32");
   }
 
@@ -945,6 +969,7 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
   const double taus[3] = {0.0, 1e-5, 1e-10};
   for (int level = 0; level < 3; ++level) {
     if (level > 0) {
+      newton_schulz(c, n, X.p, XtX.p, AX.p);
       k_tail_start<<<1, 1, 0, c.stream>>>(n, lam.p, taus[level], t0, need);
       after_launch(c, "tail_start");
       c.guard = need;
@@ -953,7 +978,7 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
       c.guard = nullptr;
       {
         ProfScope ps(c, KC_EIG);
-        k_jacobi_f32<<<1, dim3(32, 32), smf, c.stream>>>(n, SX.p, Y.p, 8, t0, JAC_TOL2_TAIL);
+        k_jacobi_f32<<<jac_ctas, dim3(32, 32), smf, c.stream>>>(n, SX.p, Y.p, 8, t0, JAC_TOL2_TAIL);
         after_launch(c, "jacobi_f32_tail");
       }
       c.guard = need;

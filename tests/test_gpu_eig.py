@@ -61,3 +61,24 @@ def test_sym_eig(ctx, kind, n):
         assert np.abs(P - Pr).max() < 1e-12
     else:
         assert np.abs(S @ V - V * w).max() <= 1e-11 * scale
+
+
+@pytest.mark.parametrize("kind", ["zeros", "dominant_flat_tail", "geometric"])
+def test_sym_eig_many_seeds(ctx, kind):
+    """Multi-level spectra (a dominant group, a group ~1e-6 below it, an exact null space) over
+    many seeds: every level's refinement must leave X orthonormal whatever rounding the FP32
+    start carries, so orthogonality, eigenvalues and residuals hold for each seed."""
+    from paper_2507_05222_gb300 import qtt
+    n = 128
+    for seed in range(16):
+        g = inputs.rng(5000 + 17 * seed + len(kind))
+        Qm, _ = np.linalg.qr(g.standard_normal((n, n)))
+        lam = spectrum(kind, n, g)
+        S = (Qm * lam) @ Qm.T
+        S = 0.5 * (S + S.T)
+        w, V = qtt.qtt_sym_eig(ctx, S)
+        wr = np.linalg.eigvalsh(S)[::-1]
+        scale = np.abs(wr).max()
+        assert np.abs(V.T @ V - np.eye(n)).max() < 1e-12, seed
+        assert np.abs(w - wr).max() <= 1e-12 * scale, seed
+        assert np.abs(S @ V - V * w).max() <= 1e-11 * scale, seed
