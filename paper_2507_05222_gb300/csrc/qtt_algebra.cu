@@ -502,7 +502,7 @@ qtt_mps* round_gram(Ctx& c, const qtt_mps* y, int chi, double eps) {
     DBuf T(&c, size_t(a0) * nv), rho(&c, size_t(nv) * nv), w(&c, size_t(nv)), V(&c, size_t(nv) * nv);
     einsum(c, "aA,asc->Asc", 1.0, tv(G[k].p, {a0, a0}), tv(Z.p, {a0, d, c1}), 0.0, tv(T.p, {a0, d, c1}));
     einsum(c, "Asc,AtD->sctD", 1.0, tv(T.p, {a0, d, c1}), tv(Z.p, {a0, d, c1}), 0.0, tv(rho.p, {d, c1, d, c1}));
-    eigh(c, nv, rho.p, w.p, V.p);
+    eigh(c, nv, rho.p, w.p, V.p, std::min(std::min(chi, m[k]), nv));
     int bk = choose_rank(c, w.p, nv, chi, eps, std::min(m[k], nv));
     out[k].reset(&c, size_t(bk) * nv);
     top_vectors_as_core(c, V.p, nv, bk, out[k].p);
@@ -582,7 +582,7 @@ qtt_mps* apply_round_gram(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, d
            tv(T2.p, {w0, a0, d, c1}));
     einsum(c, "WAsc,WASC->scSC", 1.0, tv(T2.p, {w0, a0, d, c1}), tv(Z.p, {w0, a0, d, c1}), 0.0,
            tv(rho.p, {d, c1, d, c1}));
-    eigh(c, nv, rho.p, wv.p, V.p);
+    eigh(c, nv, rho.p, wv.p, V.p, std::min(std::min(chi, mstruct[k]), nv));
     int bk = choose_rank(c, wv.p, nv, chi, eps, std::min(mstruct[k], nv));
     out[k].reset(&c, size_t(bk) * nv);
     top_vectors_as_core(c, V.p, nv, bk, out[k].p);
@@ -861,8 +861,8 @@ qtt_mps* zipup_hadamard(Ctx& c, const qtt_mps* a, const qtt_mps* b, int chi) {
     const int nv = d * c1;
     DBuf rho(&c, size_t(nv) * nv), w(&c, size_t(nv)), V(&c, size_t(nv) * nv);
     gemm(c, 1, nv, nv, int64_t(a0) * b0, 1.0, T.p, 0, 1, nv, T.p, 0, nv, 1, 0.0, rho.p, 0, nv, 1);
-    eigh(c, nv, rho.p, w.p, V.p);
     int bk = std::max(1, std::min(std::min(chi, ms[k]), nv));
+    eigh(c, nv, rho.p, w.p, V.p, bk);
     out[k].reset(&c, size_t(bk) * nv);
     top_vectors_as_core(c, V.p, nv, bk, out[k].p);
     // C_new(beta, a, b) = sum_{s,c} T(a, b, s, c) V(sc, beta)
@@ -1077,8 +1077,8 @@ qtt_mps* encode_dense(Ctx& c, const double* dense_dev, int n, int d, int chi, do
     int64_t rows = powd(k);
     DBuf rho(&c, size_t(nv) * nv), w(&c, size_t(nv)), V(&c, size_t(nv) * nv);
     gemm(c, 1, nv, nv, rows, 1.0, cur.p, 0, 1, nv, cur.p, 0, nv, 1, 0.0, rho.p, 0, nv, 1);
-    eigh(c, nv, rho.p, w.p, V.p);
     int strct = int(std::min<int64_t>(rows, nv));
+    eigh(c, nv, rho.p, w.p, V.p, std::min(chi, strct));
     int bk = choose_rank(c, w.p, nv, chi, eps, strct);
     out[k].reset(&c, size_t(bk) * nv);
     top_vectors_as_core(c, V.p, nv, bk, out[k].p);

@@ -248,9 +248,11 @@ void qr(Ctx& c, int count, int m, int n, int trans, const double* A, int64_t in_
 void svd_small(Ctx& c, int m, int n, const double* G, double* U, double* s, double* V);
 
 // Symmetric eigendecomposition of an n x n FP64 matrix S (row-major): eigenvalues descending
-// into w (n), eigenvectors as columns of V (n x n, row-major).  FP32 Jacobi in one CTA, then
-// FP64 Ogita-Aishima refinement sweeps on the tensor-free GEMM path.
-void eigh(Ctx& c, int n, const double* S, double* w, double* V);
+// into w (n), eigenvectors as columns of V (n x n, row-major).  FP32 Jacobi, then FP64
+// Ogita-Aishima refinement levels.  keep (0: n) bounds how many leading eigenvectors the
+// caller uses: refinement levels whose tail starts at or after keep are skipped, so the
+// trailing (discarded) vectors span the right subspace but are not resolved among themselves.
+void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep = 0);
 void init_kernel_attributes();
 
 }  // namespace qtt

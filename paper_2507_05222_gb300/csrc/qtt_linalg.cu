@@ -520,7 +520,8 @@ __global__ void __launch_bounds__(256) k_svd_jacobi(int m, int n, const double* 
 // ------------------------------------------------------------------ symmetric Jacobi (FP32)
 // S: n x n FP64 row-major symmetric.  V (FP64 out, row-major n x n): eigenvectors as columns.
 // With t0_dev != null only the trailing block S[t0:, t0:] is diagonalised (t0 read on the
-// device) and Vout is the identity outside that block.  1024 threads per CTA.
+// device) and Vout is the identity outside that block.  With guard != null and *guard == 0
+// the kernel returns at once and leaves Vout untouched.  1024 threads per CTA.
 // Parallel cyclic (round-robin) ordering: each round rotates n/2 disjoint pairs (p_k, q_k).
 // The round's two-sided update A <- J^T A J is done in one pass over 2 x 2 blocks: block
 // (k, l) of A (rows p_k, q_k; columns p_l, q_l) becomes R_k B R_l^T.  Only the upper triangle
@@ -534,8 +535,10 @@ __global__ void __launch_bounds__(256) k_svd_jacobi(int m, int n, const double* 
 // refinement that follows only needs a start it converges from quadratically.
 constexpr int JAC_MAX_BLOCKS_PER_THREAD = 4;   // n <= 160: 80 pairs, 3240 blocks <= 4 x 1024
 __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __restrict__ S, double* __restrict__ Vout,
-                                                     int max_sweeps, const int* __restrict__ t0_dev, float off_tol2) {
+                                                     int max_sweeps, const int* __restrict__ t0_dev, float off_tol2,
+                                                     const int* __restrict__ guard) {
   extern __shared__ float smf[];
+  if (guard && *guard == 0) return;
   const int t0 = t0_dev ? *t0_dev : 0;
   const int n = nfull - t0;
   const int G = gridDim.x, g = blockIdx.x;
@@ -669,8 +672,10 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
 }
 
 // First index of the sorted (descending) spectrum below tau * lambda_0; n if none.  Also
-// raises a flag when the tail holds at least two eigenvalues (else the refinement is skipped).
-__global__ void k_tail_start(int n, const double* __restrict__ lam, double tau, int* t0, int* need) {
+// raises a flag when the tail holds at least two eigenvalues and starts before index keep
+// (else the refinement level is skipped: a tail made only of discarded vectors needs no
+// resolution among its own pairs).
+__global__ void k_tail_start(int n, const double* __restrict__ lam, double tau, int keep, int* t0, int* need) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double top = lam[0];
   int s = n;
@@ -679,7 +684,7 @@ __global__ void k_tail_start(int n, const double* __restrict__ lam, double tau, 
       if (lam[i] < tau * top) { s = i; break; }
   }
   *t0 = s;
-  *need = (n - s >= 2) ? 1 : 0;
+  *need = (n - s >= 2 && s < keep) ? 1 : 0;
 }
 
 // One Ogita-Aishima correction, given XtX, SX = X^T A X (both n x n) and ||A||_F, in three
@@ -919,9 +924,14 @@ static void oa_iteration(Ctx& c, int n, const double* S, double* X, double* XtX,
 // Symmetric eigendecomposition to FP64 accuracy (absolute error ~ eps_64 ||S||) from FP32
 // Jacobi sweeps: level 1 diagonalises S in FP32 and refines all pairs in FP64 (Ogita-Aishima);
 // eigenvalues closer than the FP32 resolution (~1e-7 ||S||) stay lumped in a cluster, so
-// levels 2 and 3 re-diagonalise the trailing block of X^T S X (the eigenvalues below
-// 1e-5 and 1e-10 of the largest) on its own scale and refine again.  Levels with fewer than
-// two tail eigenvalues are skipped on the device.
+// levels 2 to 5 re-diagonalise the trailing block of X^T S X (the eigenvalues below 1e-3,
+// 1e-6, 1e-9 and 1e-12 of the largest) on its own scale and refine again.  Levels with fewer
+// than two tail eigenvalues are skipped on the device.  The levels are three decades apart:
+// a pair just above a level's threshold tau has a gap of order tau times its relative
+// spacing, while its coupling after the previous level is at that level's FP32 resolution
+// (~1e-7 of the previous threshold), so the refinement starts from vector errors of ~1e-4 or
+// less even for log-evenly spaced spectra; with levels five decades apart, spectra with ~10 %
+// relative spacing between neighbours were left with eigenvalue errors near 1e-6 ||S||.
 // Each tail level starts with one Newton-Schulz step on X: the last refinement of a level can
 // take a large first-order step for a tail pair that the level could not yet resolve (its
 // Rayleigh quotients drift apart by more than the threshold while their coupling is still at
@@ -943,8 +953,9 @@ static void oa_iteration(Ctx& c, int n, const double* S, double* X, double* XtX,
 constexpr float JAC_TOL2_FULL = QTT_JAC_TOL2_FULL;
 constexpr float JAC_TOL2_TAIL = QTT_JAC_TOL2_TAIL;
 
-void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
+void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep) {
   QTT_CHECK_ARG(n >= 1, "eigh: n >= 1");
+  if (keep <= 0 || keep > n) keep = n;
   if (n > 160) throw Error(QTT_ERR_UNSUPPORTED, "eigh: n > 160 not supported");
   // FP32 Jacobi: QTT_JAC_CTAS CTAs share the eigenvector rows for the larger matrices (each
   // keeps all of A)
@@ -960,39 +971,41 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V) {
   int* need = t0 + 1;
   {
     ProfScope ps(c, KC_EIG);
-    k_jacobi_f32<<<jac_ctas, dim3(32, 32), smf, c.stream>>>(n, S, X.p, 10, nullptr, JAC_TOL2_FULL);
+    k_jacobi_f32<<<jac_ctas, dim3(32, 32), smf, c.stream>>>(n, S, X.p, 10, nullptr, JAC_TOL2_FULL, nullptr);
     after_launch(c, "jacobi_f32");
   }
 
   k_frob<<<1, 1024, 0, c.stream>>>(int64_t(n) * n, S, an.p);
   after_launch(c, "frob");
-  const double taus[3] = {0.0, 1e-5, 1e-10};
-  for (int level = 0; level < 3; ++level) {
+  constexpr int kLevels = 5;
+  const double taus[kLevels] = {0.0, 1e-3, 1e-6, 1e-9, 1e-12};
+  for (int level = 0; level < kLevels; ++level) {
     if (level > 0) {
-      newton_schulz(c, n, X.p, XtX.p, AX.p);
-      k_tail_start<<<1, 1, 0, c.stream>>>(n, lam.p, taus[level], t0, need);
+      k_tail_start<<<1, 1, 0, c.stream>>>(n, lam.p, taus[level], keep, t0, need);
       after_launch(c, "tail_start");
       c.guard = need;
+      newton_schulz(c, n, X.p, XtX.p, AX.p);
       gemm(c, 1, n, n, n, 1.0, S, 0, n, 1, X.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
       gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, AX.p, 0, n, 1, 0.0, SX.p, 0, n, 1);
       c.guard = nullptr;
       {
         ProfScope ps(c, KC_EIG);
-        k_jacobi_f32<<<jac_ctas, dim3(32, 32), smf, c.stream>>>(n, SX.p, Y.p, 8, t0, JAC_TOL2_TAIL);
+        k_jacobi_f32<<<jac_ctas, dim3(32, 32), smf, c.stream>>>(n, SX.p, Y.p, 8, t0, JAC_TOL2_TAIL, need);
         after_launch(c, "jacobi_f32_tail");
       }
       c.guard = need;
       gemm(c, 1, n, n, n, 1.0, X.p, 0, n, 1, Y.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
       copy_guarded(c, X.p, AX.p, int64_t(nn), need);
     }
-    for (int it = 0; it < (level == 0 ? 4 : 3); ++it)
+    for (int it = 0; it < (level == 0 ? 3 : 2); ++it)
       oa_iteration(c, n, S, X.p, XtX.p, AX.p, SX.p, E.p, lam.p, an.p, part.p);
-    c.guard = nullptr;
-    // eigenvalue estimates of the refined vectors, then sort (descending)
+    // eigenvalue estimates of the refined vectors, then sort (descending); a skipped level
+    // leaves X and lam as they were, and the sort is then the identity
     gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, X.p, 0, n, 1, 0.0, XtX.p, 0, n, 1);
     gemm(c, 1, n, n, n, 1.0, S, 0, n, 1, X.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
     gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, AX.p, 0, n, 1, 0.0, SX.p, 0, n, 1);
-    oa_update(c, n, XtX.p, SX.p, an.p, E.p, lam.p, part.p, nullptr);
+    oa_update(c, n, XtX.p, SX.p, an.p, E.p, lam.p, part.p, c.guard);
+    c.guard = nullptr;
     k_sort_eig<<<1, 1024, n * sizeof(int), c.stream>>>(n, lam.p, X.p, w, Xs.p);
     after_launch(c, "sort_eig");
     copy(c, X.p, Xs.p, int64_t(nn));

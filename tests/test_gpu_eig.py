@@ -25,6 +25,10 @@ def spectrum(kind, n, g):
         lam = np.concatenate([np.sort(g.random(n // 4))[::-1] * 10, 1.6e-5 * g.random(n // 4), np.zeros(n - 2 * (n // 4))])
     elif kind == "geometric":
         lam = 10.0 ** (-np.linspace(0, 15, n))
+    elif kind.startswith("geometric"):
+        # log-evenly spaced over a few decades: neighbours ~7-20 % apart at every scale, so
+        # every refinement level has pairs just above its threshold with small absolute gaps
+        lam = 10.0 ** (-np.linspace(0, int(kind[len("geometric"):]), n))
     elif kind == "cluster":
         lam = np.concatenate([np.ones(n // 2), 1 + 1e-9 * g.random(n // 4), 0.5 * np.ones(n - n // 2 - n // 4)])
     else:
@@ -32,7 +36,8 @@ def spectrum(kind, n, g):
     return lam
 
 
-@pytest.mark.parametrize("kind", ["dominant_flat_tail", "zeros", "geometric", "cluster", "random"])
+@pytest.mark.parametrize("kind", ["dominant_flat_tail", "zeros", "geometric", "geometric4", "geometric8",
+                                  "geometric12", "cluster", "random"])
 @pytest.mark.parametrize("n", [16, 64, 128])
 def test_sym_eig(ctx, kind, n):
     from paper_2507_05222_gb300 import qtt
@@ -63,7 +68,7 @@ def test_sym_eig(ctx, kind, n):
         assert np.abs(S @ V - V * w).max() <= 1e-11 * scale
 
 
-@pytest.mark.parametrize("kind", ["zeros", "dominant_flat_tail", "geometric"])
+@pytest.mark.parametrize("kind", ["zeros", "dominant_flat_tail", "geometric", "geometric8"])
 def test_sym_eig_many_seeds(ctx, kind):
     """Multi-level spectra (a dominant group, a group ~1e-6 below it, an exact null space) over
     many seeds: every level's refinement must leave X orthonormal whatever rounding the FP32
