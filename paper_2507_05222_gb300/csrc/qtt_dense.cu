@@ -348,6 +348,79 @@ int grid_for(int64_t n, int threads) {
   return int(std::max<int64_t>(1, std::min<int64_t>(g, 65535 * 8)));
 }
 
+// Direct contraction for small problems: C[o] = alpha sum_k A[a(o) + ka(k)] B[b(o) + kb(k)]
+// (+ beta C[o]), every operand read in place through per-label strides.  The output index is
+// split over the output labels (row-major in the order given), the contracted index over the
+// contracted labels; LPO lanes share one output (strided over k, four independent partial
+// sums per lane, then a shuffle reduction in a fixed order).  One launch replaces the
+// permutes, the GEMM and the split-K reduction of the general path.
+constexpr int kDirectMaxLabels = 8;
+constexpr int64_t kDirectMaxMacs = int64_t(1) << 18;
+constexpr int64_t kDirectMaxK = 4096;
+struct DirectArgs {
+  int no = 0, nk = 0;
+  int odim[kDirectMaxLabels], oa[kDirectMaxLabels], ob[kDirectMaxLabels], oc[kDirectMaxLabels];
+  int kdim[kDirectMaxLabels], ka[kDirectMaxLabels], kb[kDirectMaxLabels];
+  int nout = 0, K = 0;
+  double alpha = 1.0, beta = 0.0;
+};
+
+template <int LPO>
+__global__ void __launch_bounds__(256) k_contract_direct(DirectArgs a, const double* __restrict__ A,
+                                                         const double* __restrict__ B, double* C,
+                                                         const int* __restrict__ guard) {
+  if (guard && *guard == 0) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = t / LPO, lane = t % LPO;
+  const bool valid = o < a.nout;   // every lane of a warp stays for the shuffle reduction
+  int r = valid ? o : 0, aoff = 0, boff = 0, coff = 0;
+  for (int i = a.no - 1; i >= 0; --i) {
+    const int ci = r % a.odim[i];
+    r /= a.odim[i];
+    aoff += ci * a.oa[i];
+    boff += ci * a.ob[i];
+    coff += ci * a.oc[i];
+  }
+  auto term = [&](int k) {
+    int rk = k, ka = 0, kb = 0;
+    for (int j = a.nk - 1; j >= 0; --j) {
+      const int cj = rk % a.kdim[j];
+      rk /= a.kdim[j];
+      ka += cj * a.ka[j];
+      kb += cj * a.kb[j];
+    }
+    return make_int2(ka, kb);
+  };
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int k = valid ? lane : a.K;
+  for (; k + 3 * LPO < a.K; k += 4 * LPO) {
+    const int2 o0 = term(k), o1 = term(k + LPO), o2 = term(k + 2 * LPO), o3 = term(k + 3 * LPO);
+    s0 = fma(__ldg(A + aoff + o0.x), __ldg(B + boff + o0.y), s0);
+    s1 = fma(__ldg(A + aoff + o1.x), __ldg(B + boff + o1.y), s1);
+    s2 = fma(__ldg(A + aoff + o2.x), __ldg(B + boff + o2.y), s2);
+    s3 = fma(__ldg(A + aoff + o3.x), __ldg(B + boff + o3.y), s3);
+  }
+  for (; k < a.K; k += LPO) {
+    const int2 o0 = term(k);
+    s0 = fma(__ldg(A + aoff + o0.x), __ldg(B + boff + o0.y), s0);
+  }
+  double v = (s0 + s1) + (s2 + s3);
+  for (int off = LPO / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off, LPO);
+  if (valid && lane == 0) C[coff] = (a.beta == 0.0) ? a.alpha * v : a.alpha * v + a.beta * C[coff];
+}
+
+void contract_direct(Ctx& c, DirectArgs& a, const double* A, const double* B, double* C) {
+  ProfScope ps(c, KC_GEMM, 2.0 * double(a.nout) * double(a.K));
+  if (a.K >= 32) {
+    k_contract_direct<32><<<grid_for(int64_t(a.nout) * 32, 256), 256, 0, c.stream>>>(a, A, B, C, c.guard);
+  } else if (a.K >= 8) {
+    k_contract_direct<8><<<grid_for(int64_t(a.nout) * 8, 256), 256, 0, c.stream>>>(a, A, B, C, c.guard);
+  } else {
+    k_contract_direct<1><<<grid_for(int64_t(a.nout), 256), 256, 0, c.stream>>>(a, A, B, C, c.guard);
+  }
+  after_launch(c, "contract_direct");
+}
+
 }  // namespace
 
 void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
@@ -361,6 +434,24 @@ void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, 
     fill(c, W.p, batch * M * N, 0.0);
     k_splitk_reduce<<<grid_for(batch * M * N, 256), 256, 0, c.stream>>>(batch, M, N, 1, alpha, W.p, beta, C, sCb, sCm, sCn, c.guard);
     after_launch(c, "splitk_reduce");
+    return;
+  }
+  auto span = [](int64_t n0, int64_t s0, int64_t n1, int64_t s1, int64_t n2, int64_t s2) {
+    return (n0 - 1) * std::abs(s0) + (n1 - 1) * std::abs(s1) + (n2 - 1) * std::abs(s2);
+  };
+  const int64_t kIntMax = (int64_t(1) << 31) - 1;
+  if (batch * M * N * K <= kDirectMaxMacs && K <= kDirectMaxK && span(batch, sAb, M, sAm, K, sAk) < kIntMax &&
+      span(batch, sBb, K, sBk, N, sBn) < kIntMax && span(batch, sCb, M, sCm, N, sCn) < kIntMax) {
+    DirectArgs a;
+    a.no = 3; a.nk = 1;
+    a.odim[0] = int(batch); a.odim[1] = int(M); a.odim[2] = int(N);
+    a.oa[0] = int(sAb); a.oa[1] = int(sAm); a.oa[2] = 0;
+    a.ob[0] = int(sBb); a.ob[1] = 0; a.ob[2] = int(sBn);
+    a.oc[0] = int(sCb); a.oc[1] = int(sCm); a.oc[2] = int(sCn);
+    a.kdim[0] = int(K); a.ka[0] = int(sAk); a.kb[0] = int(sBk);
+    a.nout = int(batch * M * N); a.K = int(K);
+    a.alpha = alpha; a.beta = beta;
+    contract_direct(c, a, A, B, C);
     return;
   }
   if (c.root->gemm_mode == 0 && batch * M * N * K >= (int64_t(1) << 23) && M >= 16 && N >= 16 && K >= 16) {
@@ -600,6 +691,38 @@ void einsum(Ctx& c, const char* spec, double alpha, const TV& A, const TV& B, do
   };
   int64_t Bt = prod(batch), M = prod(fa), N = prod(fb), K = prod(kk);
   if (Bt == 0 || M == 0 || N == 0) return;
+  if (K >= 1 && Bt * M * N * K <= kDirectMaxMacs && K <= kDirectMaxK && lc.size() <= size_t(kDirectMaxLabels) &&
+      kk.size() <= size_t(kDirectMaxLabels)) {
+    // small problem: one direct launch, operands read in place
+    auto stride_in = [&](const std::vector<char>& l, const TV& t, char x) -> int {
+      int64_t st = 1;
+      for (int i = int(l.size()) - 1; i >= 0; --i) {
+        if (l[i] == x) return int(st);
+        st *= t.dim[i];
+      }
+      return 0;
+    };
+    DirectArgs a;
+    a.no = int(lc.size());
+    for (int i = 0; i < a.no; ++i) {
+      a.odim[i] = int(dim[lc[i]]);
+      a.oa[i] = stride_in(la, A, lc[i]);
+      a.ob[i] = stride_in(lb, B, lc[i]);
+      a.oc[i] = stride_in(lc, C, lc[i]);
+    }
+    a.nk = int(kk.size());
+    for (int j = 0; j < a.nk; ++j) {
+      a.kdim[j] = int(dim[kk[j]]);
+      a.ka[j] = stride_in(la, A, kk[j]);
+      a.kb[j] = stride_in(lb, B, kk[j]);
+    }
+    a.nout = int(Bt * M * N);
+    a.K = int(K);
+    a.alpha = alpha;
+    a.beta = beta;
+    contract_direct(c, a, A.p, B.p, C.p);
+    return;
+  }
   // The contracted labels may be taken in the order of A or of B: pick the order that lets
   // both operands be read in place, if any.
   std::vector<char> kkB;
