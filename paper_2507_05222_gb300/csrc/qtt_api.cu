@@ -125,6 +125,7 @@ int qtt_ctx_create(qtt_ctx** out, int device, void* cuda_stream, qtt_alloc_fn al
   c->alloc_fn = alloc;
   c->free_fn = free_fn;
   c->alloc_user = user;
+  init_tile_counters(*c);
   *out = reinterpret_cast<qtt_ctx*>(c.release());
   API_END
 }
@@ -140,6 +141,7 @@ void qtt_ctx_destroy(qtt_ctx* ctx) {
       cudaEventDestroy(pr.e0);
       cudaEventDestroy(pr.e1);
     }
+  free_tile_counters(*c);
   delete c->pool;
   delete c;
 }

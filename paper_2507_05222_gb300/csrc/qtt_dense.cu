@@ -187,6 +187,18 @@ ProfScope::~ProfScope() {
   if (k >= KC_PH_APPLY && pr.phase == k - KC_PH_APPLY) pr.phase = -1;
 }
 
+void init_tile_counters(Ctx& c) {
+  if (c.tile_ctr) return;
+  QTT_CUDA(cudaMalloc(&c.tile_ctr, kTileCounters * sizeof(int)));
+  QTT_CUDA(cudaMemsetAsync(c.tile_ctr, 0, kTileCounters * sizeof(int), c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+void free_tile_counters(Ctx& c) {
+  if (c.tile_ctr) cudaFree(c.tile_ctr);
+  c.tile_ctr = nullptr;
+}
+
 Ctx& worker(Ctx& c, int i) {
   while (int(c.workers.size()) <= i) {
     Ctx* w = new Ctx;
@@ -202,6 +214,7 @@ Ctx& worker(Ctx& c, int i) {
       throw Error(QTT_ERR_CUDA, std::string("worker stream: ") + cudaGetErrorString(e));
     }
     w->pool = new Pool(c.alloc_fn, c.free_fn, c.alloc_user);
+    init_tile_counters(*w);
     cudaEvent_t j;
     QTT_CUDA(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
     c.ev_join.push_back(j);
@@ -227,6 +240,8 @@ void join(Ctx& c, int n) {
 void destroy_workers(Ctx& c) {
   for (Ctx* w : c.workers) {
     cudaStreamSynchronize(w->stream);
+    destroy_workers(*w);
+    free_tile_counters(*w);
     delete w->pool;
     cudaStreamDestroy(w->stream);
     delete w;
@@ -261,7 +276,8 @@ __global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, i
                                               const double* __restrict__ B, int64_t sBb, int64_t sBk,
                                               int64_t sBn, double beta, double* __restrict__ C,
                                               int64_t sCb, int64_t sCm, int64_t sCn,
-                                              double* __restrict__ W, const int* __restrict__ guard) {
+                                              double* __restrict__ W, int* __restrict__ tile_ctr,
+                                              const int* __restrict__ guard) {
   if (guard && *guard == 0) return;
   constexpr int R = T / 16;          // outputs per thread per dimension
   constexpr int L = T * GK / 256;    // loads per thread per operand tile
@@ -327,6 +343,33 @@ __global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, i
       }
     }
   }
+  if (!W || !tile_ctr) return;
+  // Split-K fix-up without a second launch: the CTA that finishes a tile last (arrival counter)
+  // sums the tile's partials over the splits in split order -- the order of k_splitk_reduce,
+  // whichever CTA is last -- and resets the counter for the next GEMM on this stream.
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  const int64_t tile = (b * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  if (t == 0) last = (atomicAdd(tile_ctr + tile, 1) == splits - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      int64_t gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      double s = 0.0;
+      for (int q = 0; q < splits; ++q) s += __ldcg(W + ((int64_t(q) * batch + b) * M + gm) * N + gn);
+      double* cp = C + b * sCb + gm * sCm + gn * sCn;
+      *cp = (beta == 0.0) ? alpha * s : alpha * s + beta * (*cp);
+    }
+  }
+  if (t == 0) tile_ctr[tile] = 0;
 }
 
 __global__ void k_splitk_reduce(int64_t batch, int64_t M, int64_t N, int splits, double alpha,
@@ -503,17 +546,19 @@ void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, 
   DBuf W;
   if (splits > 1) W.reset(&c, size_t(splits) * batch * M * N);
   double* Wp = splits > 1 ? W.p : nullptr;
+  const int64_t ntiles = int64_t(grid.x) * grid.y * batch;
+  int* ctr = (splits > 1 && c.tile_ctr && ntiles <= kTileCounters) ? c.tile_ctr : nullptr;
   if (T == 64)
     k_gemm<64><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
-                                             sBn, beta, C, sCb, sCm, sCn, Wp, c.guard);
+                                             sBn, beta, C, sCb, sCm, sCn, Wp, ctr, c.guard);
   else if (T == 32)
     k_gemm<32><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
-                                             sBn, beta, C, sCb, sCm, sCn, Wp, c.guard);
+                                             sBn, beta, C, sCb, sCm, sCn, Wp, ctr, c.guard);
   else
     k_gemm<16><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
-                                             sBn, beta, C, sCb, sCm, sCn, Wp, c.guard);
+                                             sBn, beta, C, sCb, sCm, sCn, Wp, ctr, c.guard);
   after_launch(c, "gemm");
-  if (splits > 1) {
+  if (splits > 1 && !ctr) {
     k_splitk_reduce<<<grid_for(batch * M * N, 256), 256, 0, c.stream>>>(batch, M, N, splits, alpha, W.p, beta, C,
                                                                         sCb, sCm, sCn, c.guard);
     after_launch(c, "splitk_reduce");

@@ -146,8 +146,15 @@ struct Ctx {
   // Matrix products: 0 = products of >= 2^23 multiply-adds on the tensor cores (digit
   // splitting, see qtt_ozaki.cu), the rest on the FP64 pipe; 1 = everything on the FP64 pipe.
   int gemm_mode = 0;
+  // Per-tile arrival counters of split-K GEMMs on this context's stream (kTileCounters ints,
+  // zero between launches: the last CTA of a tile resets its counter).
+  int* tile_ctr = nullptr;
   Profiler prof;
 };
+
+constexpr int kTileCounters = 16384;
+void init_tile_counters(Ctx& c);   // allocate and zero c.tile_ctr (outside stream capture of c.stream)
+void free_tile_counters(Ctx& c);
 
 void after_launch(Ctx& c, const char* what);
 
