@@ -141,6 +141,8 @@ def run_ours(args, cfg):
     ctx = qtt.Context(local)
     if args.gemm_mode is not None:
         ctx.set_gemm_mode(args.gemm_mode)
+    if args.cg_mode is not None:
+        ctx.set_cg_mode(args.cg_mode)
     ne, nx, chi = cfg["n_eta"], cfg["n_xi"], cfg["chi"]
     case = qtt.Case(ctx, ne, nx, cfg["R"], cfg["Re"], cfg["dt"], chi, cfg["ordering"], fit_sweeps=cfg["fit_sweeps"],
                     mom=cfg["mom"], poi=cfg["poi"])
@@ -255,7 +257,9 @@ def run_ours(args, cfg):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering")}
                 | {"mom_solve": list(cfg["mom"]), "poisson_solve": list(cfg["poi"]), "fit_sweeps": cfg["fit_sweeps"],
-                   "l2": "256 MB buffer written between timed steps", "replicas": world},
+                   "l2": "256 MB buffer written between timed steps", "replicas": world,
+                   **({"gemm_mode": args.gemm_mode} if args.gemm_mode is not None else {}),
+                   **({"cg_mode": args.cg_mode} if args.cg_mode is not None else {})},
                 "e2e": {"value": world / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -284,6 +288,9 @@ def main():
                     help="set up, one warm-up step, then one step between cudaProfilerStart/Stop (for ncu)")
     ap.add_argument("--gemm-mode", type=int, default=None, choices=(0, 1),
                     help="0: large products on the tensor cores (digit-split FP64); 1: FP64 pipe")
+    ap.add_argument("--cg-mode", type=int, default=None, choices=(0, 1, 2),
+                    help="ALS local solves: 0 one FP64 cooperative kernel (default), 1 one kernel per stage, "
+                         "2 one cooperative kernel with tensor-core contractions where it fits")
     ap.add_argument("--phase-breakdown", action="store_true",
                     help="print kernel-class time by step phase (diagnostic; no bench line)")
     ap.add_argument("--kernel-probe", action="store_true",

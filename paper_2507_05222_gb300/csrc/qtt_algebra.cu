@@ -912,12 +912,18 @@ int als(Ctx& c, const qtt_mpo* A, const std::vector<Term>& rhs, qtt_mps* x, int 
     int r0 = x->bonds[k], r1 = x->bonds[k + 1];
     int64_t nel = int64_t(r0) * d * r1;
     const int w0 = A->bonds[k], w1 = A->bonds[k + 1];
-    if (c.root->cg_mode == 0 && cg_persistent_fits(c, r0, r1, w0, w1, d)) {
+    const int mode = c.root->cg_mode;
+    const bool tc = mode == 2 && cg_tc_fits(c, r0, r1, w0, w1, d);
+    if (tc || ((mode == 0 || mode == 2) && cg_persistent_fits(c, r0, r1, w0, w1, d))) {
       DBuf bvec(&c, nel), xk(&c, nel);
       local_sum(c, rhs, E, x, k, bvec.p);
       copy(c, xk.p, x->core(k), nel);
-      cg_persistent(c, LA[k].p, A->core(k), RA[k + 1].p, bvec.p, xk.p, r0, r1, w0, w1, d, cg_iters, cg_tol,
-                    reinterpret_cast<int*>(tot.p));
+      if (tc)
+        cg_tc(c, LA[k].p, A->core(k), RA[k + 1].p, bvec.p, xk.p, r0, r1, w0, w1, d, cg_iters, cg_tol,
+              reinterpret_cast<int*>(tot.p));
+      else
+        cg_persistent(c, LA[k].p, A->core(k), RA[k + 1].p, bvec.p, xk.p, r0, r1, w0, w1, d, cg_iters, cg_tol,
+                      reinterpret_cast<int*>(tot.p));
       return xk;
     }
     DBuf bvec(&c, nel), Ax(&c, nel), r(&c, nel), p(&c, nel), Ap(&c, nel), xk(&c, nel);

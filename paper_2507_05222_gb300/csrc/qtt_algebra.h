@@ -62,6 +62,13 @@ bool cg_persistent_fits(const Ctx& c, int r0, int r1, int w0, int w1, int d);
 void cg_init_attributes();   // kernel attributes and occupancy, once (before any stream capture)
 void cg_persistent(Ctx& c, const double* L, const double* W, const double* R, const double* b, double* x, int r0,
                    int r1, int w0, int w1, int d, int iters, double tol, int* total_dev);
+// The same solve with both contractions as exact digit-split products on the tensor cores
+// (qtt_cg.cu, CG mode 2); the caller's own stream only (one CTA per SM), r0 <= 64, products on
+// the tensor cores (gemm mode 0).
+bool cg_tc_fits(const Ctx& c, int r0, int r1, int w0, int w1, int d);
+void cg_tc_init_attributes();
+void cg_tc(Ctx& c, const double* L, const double* W, const double* R, const double* b, double* x, int r0, int r1,
+           int w0, int w1, int d, int iters, double tol, int* total_dev);
 
 void dot_dev(Ctx& c, const qtt_mps* a, const qtt_mps* b, double* out_dev);
 void norm_dev(Ctx& c, const qtt_mps* y, double* out_dev);

@@ -639,6 +639,7 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
   cs.drop_graph();
   init_kernel_attributes();
   cg_init_attributes();
+  cg_tc_init_attributes();
   init_ozaki_attributes();
   for (int i = 0; i < 4; ++i) worker(c, i);
   if (!cs.gstream) QTT_CUDA(cudaStreamCreateWithFlags(&cs.gstream, cudaStreamNonBlocking));

@@ -236,6 +236,10 @@ void gemm_ozaki(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double a
                 int64_t sAm, int64_t sAk, const double* B, int64_t sBb, int64_t sBk, int64_t sBn, double beta,
                 double* C, int64_t sCb, int64_t sCm, int64_t sCn);
 void init_ozaki_attributes();   // kernel attributes, once (before any stream capture)
+// Seven bf16 digit slices out[s][r][Kp] and scale exponents ex[r] of the R rows of X (K values
+// each, strides sR, sK), as the tensor-core products use them (qtt_ozaki.cu).
+void oz_split_rows(Ctx& c, int64_t R, int64_t K, int64_t Kp, const double* X, int64_t sR, int64_t sK, void* out,
+                   int* ex);
 void copy(Ctx& c, double* dst, const double* src, int64_t n);
 void axpby(Ctx& c, int64_t n, double a, const double* x, double b, double* y);  // y = a x + b y
 // Deterministic dot product into a device scalar.

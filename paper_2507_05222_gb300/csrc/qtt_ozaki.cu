@@ -20,12 +20,12 @@
 #include <algorithm>
 
 #include "qtt_internal.h"
+#include "qtt_ozaki_dev.cuh"
 
 namespace qtt {
 
 namespace {
 
-constexpr int OZ_S = 7;            // digits per operand
 constexpr int OZ_KC = 64;          // k per chunk of exact FP32 accumulation
 constexpr int OZ_BM = 128;         // rows of A per CTA (8 warps x 16)
 constexpr int OZ_BN = 32;          // columns of B per CTA (4 n8 tiles)
@@ -76,22 +76,8 @@ __global__ void k_oz_digits(int64_t batch, int64_t R, int64_t K, int64_t Kp, con
       k = bk % Kp;
       b = bk / Kp;
     }
-    long long F = 0;
-    if (k < K) {
-      const double x = X[b * sB + r * sR + k * sK];
-      const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
-      const int bexp = int((bits >> 52) & 0x7ff);
-      if (bexp != 0 && bexp != 0x7ff) {
-        // x = +-mant 2^(bexp - 1075) with a 53-bit integer mant; F = x 2^(8S - e)
-        const long long mant = static_cast<long long>((bits & 0xfffffffffffffull) | 0x10000000000000ull);
-        const int sh = bexp - 1075 + 8 * OZ_S - ex[b * R + r];
-        long long v;
-        if (sh >= 0) v = mant << sh;                                   // |x| 2^-e < 1/2: below 2^55
-        else if (sh > -63) v = (mant + (1ll << (-sh - 1))) >> (-sh);   // rounded to nearest
-        else v = 0;
-        F = (bits >> 63) ? -v : v;
-      }
-    }
+    const long long F0 = (k < K) ? oz_fixed(X[b * sB + r * sR + k * sK], ex[b * R + r]) : 0;
+    long long F = F0;
     __nv_bfloat16* o = out + ((b * OZ_S) * R + r) * Kp + k;
 #pragma unroll
     for (int s = OZ_S - 1; s >= 1; --s) {
@@ -101,66 +87,6 @@ __global__ void k_oz_digits(int64_t batch, int64_t R, int64_t K, int64_t Kp, con
     }
     o[0] = __float2bfloat16_rn(float(F));   // |F| <= 128
   }
-}
-
-// (hi 2^64 + lo) 2^E as a double, rounded to nearest even, by integer operations on the bit
-// pattern (the FP64 unit of this part is ~64x slower than its integer units).  |value| < 2^127.
-__device__ __forceinline__ double fixed_to_double(long long hi, unsigned long long lo, int E) {
-  const bool neg = hi < 0;
-  unsigned long long h = static_cast<unsigned long long>(hi), l = lo;
-  if (neg) {
-    l = ~l + 1ull;
-    h = ~h + (l == 0ull ? 1ull : 0ull);
-  }
-  if (h == 0ull && l == 0ull) return 0.0;
-  // normalise so that bit 127 is set
-  const int lz = h ? __clzll(static_cast<long long>(h)) : 64 + __clzll(static_cast<long long>(l));
-  if (lz >= 64) {
-    h = l << (lz - 64);
-    l = 0ull;
-  } else if (lz > 0) {
-    h = (h << lz) | (l >> (64 - lz));
-    l <<= lz;
-  }
-  unsigned long long m = h >> 11;                                  // 53 bits
-  const bool guard = (h >> 10) & 1ull;
-  const bool sticky = ((h & 0x3ffull) != 0ull) || (l != 0ull);
-  int X = 127 - lz + E;                                           // exponent of the leading bit
-  if (guard && (sticky || (m & 1ull))) {
-    ++m;
-    if (m == (1ull << 53)) {
-      m >>= 1;
-      ++X;
-    }
-  }
-  if (X < -1022 || X > 1023) {                                    // outside the normal range
-    const double r = scalbn(static_cast<double>(m), X - 52);
-    return neg ? -r : r;
-  }
-  const unsigned long long bits = (neg ? (1ull << 63) : 0ull) | (static_cast<unsigned long long>(X + 1023) << 52) |
-                                  (m & 0xfffffffffffffull);
-  return __longlong_as_double(static_cast<long long>(bits));
-}
-
-// 16-byte global -> shared copy that does not stall the thread; full = false writes zeros.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool full) {
-  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-  const int n = full ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(a), "l"(gmem), "r"(n) : "memory");
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
-  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-               "{%0,%1,%2,%3};"
-               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // C = alpha A B + beta C from the digit slices of A (rows) and of B (columns).  CTA tile
@@ -363,6 +289,18 @@ void gemm_ozaki(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double a
                                                         c.guard);
     after_launch(c, "oz_reduce");
   }
+}
+
+// Digit slices out[s][r][Kp] (bf16, s = 0..OZ_S-1) and scale exponents ex[r] of the R rows of X
+// (K values each, strides sR, sK; zero digits for K <= k < Kp).
+void oz_split_rows(Ctx& c, int64_t R, int64_t K, int64_t Kp, const double* X, int64_t sR, int64_t sK, void* out,
+                   int* ex) {
+  k_oz_rowexp<<<unsigned((R * 32 + 255) / 256), 256, 0, c.stream>>>(1, R, K, X, 0, sR, sK, ex, c.guard);
+  after_launch(c, "oz_rowexp");
+  const int64_t t = R * Kp;
+  k_oz_digits<<<unsigned(std::min<int64_t>((t + 255) / 256, 8192)), 256, 0, c.stream>>>(
+      1, R, K, Kp, X, 0, sR, sK, ex, static_cast<__nv_bfloat16*>(out), c.guard);
+  after_launch(c, "oz_digits");
 }
 
 }  // namespace qtt

@@ -150,7 +150,7 @@ def test_dot(ctx):
     assert abs(v - ref) <= 1e-12 * np.linalg.norm(tt.full(a)) * np.linalg.norm(tt.full(b))
 
 
-@pytest.fixture(params=[0, 1], ids=["cg_one_kernel", "cg_per_stage"])
+@pytest.fixture(params=[0, 1, 2], ids=["cg_one_kernel", "cg_per_stage", "cg_one_kernel_tensor_cores"])
 def cg_mode(ctx, request):
     ctx.set_cg_mode(request.param)
     yield request.param
@@ -185,6 +185,34 @@ def test_poisson_solve_full_rank_exact(ctx, cg_mode):
     ref = np.linalg.solve(tt.full_mpo(ops.Ap), tt.full(b))
     assert rel(down(ctx, g), ref) < 1e-10
     assert res < 1e-10
+
+
+def test_poisson_solve_tensor_core_cg_equals_fp64(ctx):
+    """ALS local solves at bonds 64 (n = 12, the middle sites hold 64 x 2 x 64 cores): the
+    cooperative CG with both contractions as digit-split tensor-core products (mode 2) against
+    the same kernel structure on the FP64 pipe (mode 0) and the per-stage kernels (mode 1).
+    The CG runs unconverged to its budget, so the results agree to the rounding-order level
+    amplified by the solve (~1e3), and the iteration counts agree."""
+    from paper_2507_05222_gb300 import qtt
+    ne, nx = 6, 6
+    ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, "interleaved")
+    n = ne + nx
+    b = inputs.random_cores(n, 16, seed=84)
+    x0 = inputs.random_cores(n, 64, seed=85, scale=0.1)
+    out = []
+    try:
+        for mode in (2, 0, 1):
+            ctx.set_cg_mode(mode)
+            g = up(ctx, x0)
+            cg, res = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.Ap), up(ctx, b), g, 2, 20, 1e-12)
+            out.append((down(ctx, g), cg, res))
+    finally:
+        ctx.set_cg_mode(0)
+    (x_tc, cg_tc, r_tc), (x_64, cg_64, r_64), (x_ps, cg_ps, r_ps) = out
+    assert rel(x_64, x_ps) < 1e-10
+    assert rel(x_tc, x_64) < 1e-10
+    assert abs(cg_tc - cg_64) <= 2 and abs(cg_64 - cg_ps) <= 2
+    assert abs(r_tc - r_64) <= 1e-6 * r_64
 
 
 def test_field_reorder(ctx):
