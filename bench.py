@@ -288,9 +288,10 @@ def main():
                     help="set up, one warm-up step, then one step between cudaProfilerStart/Stop (for ncu)")
     ap.add_argument("--gemm-mode", type=int, default=None, choices=(0, 1),
                     help="0: large products on the tensor cores (digit-split FP64); 1: FP64 pipe")
-    ap.add_argument("--cg-mode", type=int, default=None, choices=(0, 1, 2),
-                    help="ALS local solves: 0 one FP64 cooperative kernel (default), 1 one kernel per stage, "
-                         "2 one cooperative kernel with tensor-core contractions where it fits")
+    ap.add_argument("--cg-mode", type=int, default=None, choices=(0, 1, 2, 3),
+                    help="ALS local solves: 0 one cooperative kernel, tensor-core contractions at full-bond sites "
+                         "(default); 1 one kernel per stage; 2 one FP64 cooperative kernel; 3 tensor cores wherever "
+                         "the cooperative kernel fits")
     ap.add_argument("--phase-breakdown", action="store_true",
                     help="print kernel-class time by step phase (diagnostic; no bench line)")
     ap.add_argument("--kernel-probe", action="store_true",

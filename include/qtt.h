@@ -123,13 +123,14 @@ int qtt_ctx_profile(qtt_ctx* ctx, int on, double* ms_out, double* flops_out, int
  * with momentum, unused, Poisson, projection -- row 5 = outside any phase; column k = kernel
  * class k), and launches_out[6] (kernel launches enqueued in each row).  Either may be NULL. */
 int qtt_ctx_profile_phases(qtt_ctx* ctx, double* ms_out, int64_t* launches_out);
-/* How ALS local systems are solved (Sec. II.A.4): mode 0 (default) runs each local CG solve
- * as one cooperative kernel on the FP64 pipe (one CTA per SM, grid barriers between its stages)
- * where the bonds allow it (bonds <= 128, operator bonds <= 16, d <= 4); mode 2 does the same
- * but, on the context's own stream with left bond <= 64 and the tensor-core product mode
+/* How ALS local systems are solved (Sec. II.A.4).  Mode 2 runs each local CG solve as one
+ * cooperative kernel on the FP64 pipe (one CTA per SM, grid barriers between its stages) where
+ * the bonds allow it (bonds <= 128, operator bonds <= 16, d <= 4).  Mode 3 does the same but,
+ * on the context's own stream with left bond <= 64 and the tensor-core product mode
  * (qtt_ctx_set_gemm_mode 0), runs both contractions as exact digit-split products on the
- * tensor cores; mode 1 launches one kernel per contraction and per CG update.  All give the
- * same iterates up to rounding order.  Returns QTT_ERR_ARG for another mode. */
+ * tensor cores.  Mode 0 (default) takes mode 3 at sites whose bonds multiply to at least 4096
+ * and mode 2 elsewhere.  Mode 1 launches one kernel per contraction and per CG update.  All give
+ * the same iterates up to rounding order.  Returns QTT_ERR_ARG for another mode. */
 int qtt_ctx_set_cg_mode(qtt_ctx* ctx, int mode);
 
 /* ------------------------------------------------------------------------ MPS and MPO */

@@ -752,9 +752,9 @@ int qtt_case_phase_ms(qtt_case* h, double* ms4) {
 int qtt_ctx_set_cg_mode(qtt_ctx* ctx, int mode) {
   API_BEGIN
   QTT_CHECK_ARG(ctx, "ctx is null");
-  QTT_CHECK_ARG(mode == 0 || mode == 1 || mode == 2,
-                "cg mode must be 0 (one FP64 kernel per solve), 1 (one kernel per stage) or 2 (one kernel per solve "
-                "with tensor-core contractions where it fits)");
+  QTT_CHECK_ARG(mode >= 0 && mode <= 3,
+                "cg mode must be 0 (one kernel per solve, tensor-core contractions at full-bond sites), 1 (one kernel "
+                "per stage), 2 (one FP64 kernel per solve) or 3 (one kernel per solve, tensor cores wherever it fits)");
   reinterpret_cast<Ctx*>(ctx)->cg_mode = mode;
   API_END
 }

@@ -150,7 +150,8 @@ def test_dot(ctx):
     assert abs(v - ref) <= 1e-12 * np.linalg.norm(tt.full(a)) * np.linalg.norm(tt.full(b))
 
 
-@pytest.fixture(params=[0, 1, 2], ids=["cg_one_kernel", "cg_per_stage", "cg_one_kernel_tensor_cores"])
+@pytest.fixture(params=[0, 1, 2, 3], ids=["cg_default", "cg_per_stage", "cg_one_kernel_fp64",
+                                          "cg_one_kernel_tensor_cores"])
 def cg_mode(ctx, request):
     ctx.set_cg_mode(request.param)
     yield request.param
@@ -189,8 +190,9 @@ def test_poisson_solve_full_rank_exact(ctx, cg_mode):
 
 def test_poisson_solve_tensor_core_cg_equals_fp64(ctx):
     """ALS local solves at bonds 64 (n = 12, the middle sites hold 64 x 2 x 64 cores): the
-    cooperative CG with both contractions as digit-split tensor-core products (mode 2) against
-    the same kernel structure on the FP64 pipe (mode 0) and the per-stage kernels (mode 1).
+    cooperative CG with both contractions as digit-split tensor-core products (mode 3) against
+    the same kernel structure on the FP64 pipe (mode 2), the per-stage kernels (mode 1) and the
+    default mix (mode 0: tensor cores at the full-bond sites).
     The CG runs unconverged to its budget, so the results agree to the rounding-order level
     amplified by the solve (~1e3), and the iteration counts agree."""
     from paper_2507_05222_gb300 import qtt
@@ -201,17 +203,18 @@ def test_poisson_solve_tensor_core_cg_equals_fp64(ctx):
     x0 = inputs.random_cores(n, 64, seed=85, scale=0.1)
     out = []
     try:
-        for mode in (2, 0, 1):
+        for mode in (3, 2, 1, 0):
             ctx.set_cg_mode(mode)
             g = up(ctx, x0)
             cg, res = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.Ap), up(ctx, b), g, 2, 20, 1e-12)
             out.append((down(ctx, g), cg, res))
     finally:
         ctx.set_cg_mode(0)
-    (x_tc, cg_tc, r_tc), (x_64, cg_64, r_64), (x_ps, cg_ps, r_ps) = out
+    (x_tc, cg_tc, r_tc), (x_64, cg_64, r_64), (x_ps, cg_ps, r_ps), (x_d, cg_d, r_d) = out
     assert rel(x_64, x_ps) < 1e-10
     assert rel(x_tc, x_64) < 1e-10
-    assert abs(cg_tc - cg_64) <= 2 and abs(cg_64 - cg_ps) <= 2
+    assert rel(x_d, x_64) < 1e-10
+    assert abs(cg_tc - cg_64) <= 2 and abs(cg_64 - cg_ps) <= 2 and abs(cg_d - cg_64) <= 2
     assert abs(r_tc - r_64) <= 1e-6 * r_64
 
 
