@@ -637,26 +637,28 @@ __device__ double tc_stage_b(const CgTcArgs& a, const double* P, unsigned char* 
   __nv_bfloat16* sB = sA + size_t(OZ_S) * TC_BM * TC_LDB;
   long long hi[4] = {0, 0, 0, 0};
   unsigned long long lo[4] = {0ull, 0ull, 0ull, 0ull};
-  const int nch = a.KpB / TC_KC;
+  // k in pieces of 32 (KpB is a multiple of 64): 768 = 24 pieces, three per warp
+  constexpr int KW = TC_KC / 2;
+  const int nch = a.KpB / KW;
   for (int q = warp; q < nch; q += TC_THREADS / 32) {
-    const int k0 = q * TC_KC;
-    // 16 rows of T1 and 8 rows of Q, 7 slices each, 64 k: 16-byte asynchronous copies
-    for (int idx = lane; idx < OZ_S * TC_BM * 8; idx += 32) {   // (slice, row, 16-byte vector)
-      const int c8 = idx & 7, sr = idx >> 3, s = sr >> 4, row = sr & 15, c = c0 + row;
+    const int k0 = q * KW;
+    // 16 rows of T1 and 8 rows of Q, 7 slices each, 32 k: 16-byte asynchronous copies
+    for (int idx = lane; idx < OZ_S * TC_BM * 4; idx += 32) {   // (slice, row, 16-byte vector)
+      const int c4 = idx & 3, sr = idx >> 2, s = sr >> 4, row = sr & 15, c = c0 + row;
       const bool in = c < a.MB;
-      cp_async16(sA + (s * TC_BM + row) * TC_LDB + c8 * 8,
-                 in ? a.Td + (size_t(s) * a.MB + c) * a.KpB + k0 + c8 * 8 : a.Td, in);
+      cp_async16(sA + (s * TC_BM + row) * TC_LDB + c4 * 8,
+                 in ? a.Td + (size_t(s) * a.MB + c) * a.KpB + k0 + c4 * 8 : a.Td, in);
     }
-    for (int idx = lane; idx < OZ_S * TC_N * 8; idx += 32) {
-      const int c8 = idx & 7, sr = idx >> 3, s = sr >> 3, j = sr & 7, n = n0 + j;
+    for (int idx = lane; idx < OZ_S * TC_N * 4; idx += 32) {
+      const int c4 = idx & 3, sr = idx >> 2, s = sr >> 3, j = sr & 7, n = n0 + j;
       const bool in = n < a.NB;
-      cp_async16(sB + (s * TC_N + j) * TC_LDB + c8 * 8,
-                 in ? a.Qd + (size_t(s) * a.NB + n) * a.KpB + k0 + c8 * 8 : a.Qd, in);
+      cp_async16(sB + (s * TC_N + j) * TC_LDB + c4 * 8,
+                 in ? a.Qd + (size_t(s) * a.NB + n) * a.KpB + k0 + c4 * 8 : a.Qd, in);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncwarp();
-    tc_mma_chunk(sA, TC_LDB, size_t(TC_BM) * TC_LDB, sB, TC_LDB, size_t(TC_N) * TC_LDB, TC_KC, hi, lo);
+    tc_mma_chunk(sA, TC_LDB, size_t(TC_BM) * TC_LDB, sB, TC_LDB, size_t(TC_N) * TC_LDB, KW, hi, lo);
     __syncwarp();
   }
   // add the warps' partials in warp order (exact), convert once per output
