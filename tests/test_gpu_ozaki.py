@@ -38,7 +38,10 @@ def exact(A, B):
 
 
 @pytest.mark.parametrize("m,n,k", [(64, 32, 16), (130, 70, 64), (256, 128, 384), (1000, 48, 200), (17, 33, 17),
-                                   (4096, 128, 64), (128, 64, 4096)])
+                                   (4096, 128, 64), (128, 64, 4096),
+                                   # FP64 path: direct small contractions with 1, 8 and 32 lanes per
+                                   # output, and split-K tiles finished by the last CTA of each tile
+                                   (40, 30, 5), (16, 16, 1024), (3, 1000, 60), (16, 16, 4100), (33, 65, 2000)])
 def test_ozaki_matches_fp64(ctx, m, n, k):
     from paper_2507_05222_gb300 import qtt
     g = inputs.rng(m * 7 + n * 3 + k)
