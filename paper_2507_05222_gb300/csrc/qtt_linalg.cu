@@ -653,16 +653,17 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
         if (h1 && k != l) A[a10] = n10;
         if (h1 && h2) A[a11] = n11;
       }
-      // columns p, q of this CTA's rows of V (independent of the A update)
-      for (int k = ty; k < npairs; k += 32) {
+      // columns p, q of this CTA's rows of V (independent of the A update): one (pair, row)
+      // item per thread, rows fastest
+      const int vrows = r1 - r0;
+      for (int idx = tid; idx < npairs * vrows; idx += 1024) {
+        const int k = idx / vrows, i = idx - k * vrows;
         const int2 pqk = pq[k];
         if (pqk.y >= n) continue;
         const float2 r = cs[k];
-        for (int i = tx; i < r1 - r0; i += 32) {
-          float x = V[i * ld + pqk.x], y = V[i * ld + pqk.y];
-          V[i * ld + pqk.x] = r.x * x - r.y * y;
-          V[i * ld + pqk.y] = r.y * x + r.x * y;
-        }
+        float x = V[i * ld + pqk.x], y = V[i * ld + pqk.y];
+        V[i * ld + pqk.x] = r.x * x - r.y * y;
+        V[i * ld + pqk.y] = r.y * x + r.x * y;
       }
       __syncthreads();
     }
@@ -948,7 +949,7 @@ static void oa_iteration(Ctx& c, int n, const double* S, double* X, double* XtX,
 #define QTT_JAC_TOL2_TAIL 1e-12f
 #endif
 #ifndef QTT_JAC_CTAS
-#define QTT_JAC_CTAS 4
+#define QTT_JAC_CTAS 8
 #endif
 constexpr float JAC_TOL2_FULL = QTT_JAC_TOL2_FULL;
 constexpr float JAC_TOL2_TAIL = QTT_JAC_TOL2_TAIL;
@@ -958,7 +959,7 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep) {
   if (keep <= 0 || keep > n) keep = n;
   if (n > 160) throw Error(QTT_ERR_UNSUPPORTED, "eigh: n > 160 not supported");
   // FP32 Jacobi: QTT_JAC_CTAS CTAs share the eigenvector rows for the larger matrices (each
-  // keeps all of A)
+  // keeps all of A; 8: 16 rows each at n = 128)
   const int jac_ctas = n >= 64 ? QTT_JAC_CTAS : 1;
   const size_t npairs = size_t((n + 1) & ~1) / 2;
   const size_t smf = ((size_t(n) * (n + 1) + size_t(n / jac_ctas + 1) * (n + 1) + 1) & ~size_t(1)) * sizeof(float) +
