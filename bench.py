@@ -264,7 +264,8 @@ def run_ours(args, cfg):
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                             "kernel": "core contractions: k_gemm (FP64 pipe) + k_oz_gemm (digit-split FP64 on the tensor cores), FP64-equivalent flops",
+                             "kernel": "core contractions: k_gemm + k_contract_direct (FP64 pipe) + k_oz_gemm (digit-split FP64 on "
+                                       "the tensor cores), FP64-equivalent flops",
                              "share_of_step": g["ms"] / nprof / step_ms if step_ms > 0 else None},
                 "kernel_classes_ms_per_step": {k: v["ms"] / nprof for k, v in prof.items() if not k.startswith("phase")},
                 "phase_ms_last_timed_step": phases,
