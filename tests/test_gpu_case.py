@@ -218,3 +218,84 @@ def test_tensor_core_products_equal_fp64_pipe(ctx):
         assert rel(x, y) < 1e-9
     for k in ("cg_u", "cg_v", "cg_p"):
         assert abs(ia[0][k] - ib[0][k]) <= 2
+
+
+def smooth_field(ne, nx, seed, amp, modes):
+    """A field with a decaying QTT spectrum: modes products of a sine in xi and a cosine in eta
+    (QTT rank <= 4 each) with amplitudes 2^(-k/2) and seeded phases, so that truncation to chi is
+    active but the kept and discarded singular values stay apart (unlike i.i.d. noise, whose flat
+    spectrum makes the chi-truncation non-unique)."""
+    g = inputs.rng(seed)
+    i = (np.arange(2 ** ne) + 0.5) / 2 ** ne
+    j = np.arange(2 ** nx) / 2 ** nx
+    f = np.zeros((2 ** ne, 2 ** nx))
+    for k in range(1, modes + 1):
+        ph, ps = g.uniform(0, 2 * np.pi, 2)
+        f += 2.0 ** (-k / 2) * np.outer(np.cos(np.pi * k * i + ps), np.sin(2 * np.pi * k * j + ph))
+    return amp * f
+
+
+def headline_state(ctx, chi=64):
+    from paper_2507_05222_gb300 import qtt
+    ne = nx = 10
+    ops = Q.Ops(ne, nx, 40.0, 200.0, 8e-4, "interleaved")
+    u0 = 1.0 + smooth_field(ne, nx, 11, 1e-2, 24)
+    v0 = smooth_field(ne, nx, 12, 1e-2, 24)
+    u, v = ops.encode(u0, chi), ops.encode(v0, chi)
+    p = S.padded([np.zeros((1, 2, 1))] * (ne + nx), chi, inputs.random_cores(ne + nx, chi, 13, scale=1e-8))
+    return ops, (u, v, p)
+
+
+def test_headline_operations_match_oracle(ctx):
+    """The well-conditioned operations of the step at the timed size (2^20 cells, chi = 64):
+    MPO·MPS products with rounding, the Hadamard fit and a momentum-operator ALS solve, each
+    against the oracle on the same input.  The products are held to the Gram-rounding limit:
+    this state keeps singular values down to ~1e-14 sigma_1 in its bonds, and directions with
+    sigma below sqrt(eps) sigma_1 are not resolved by a Gram eigenproblem, which leaves ~1e-8
+    of the product (measured 5e-8 with tensor-core contractions, 1e-8 on the FP64 pipe)."""
+    from paper_2507_05222_gb300 import qtt
+    ops, (u, v, p) = headline_state(ctx)
+    gu, gv = qtt.MPS.from_cores(ctx, u), qtt.MPS.from_cores(ctx, v)
+    for M, x, gx in ((ops.Dx, u, gu), (ops.Dz, v, gv)):
+        ref = tt.full(tt.round_tt(tt.mpo_mps(M, x), 64))
+        g = qtt.mpo_apply_round(ctx, qtt.MPO.from_cores(ctx, M), gx, 64)
+        assert rel(qtt.qtt_decode(ctx, g), ref) < 1e-6
+    ref = tt.full(tt.hadamard_round(u, v, 64, sweeps=2))
+    g = qtt.mps_hadamard_round(ctx, gu, gv, 64, sweeps=2)
+    assert rel(qtt.qtt_decode(ctx, g), ref) < 1e-11
+    xr, cgr = tt.als(ops.H, [("vec", 1.0, u)], u, 1, 8, 1e-10)
+    g = qtt.MPS.from_cores(ctx, u)
+    cg, _ = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.H), qtt.MPS.from_cores(ctx, u), g, 1, 8, 1e-10)
+    assert abs(cg - cgr) <= 2
+    assert rel(qtt.qtt_decode(ctx, g), tt.full(xr)) < 1e-6
+
+
+def test_headline_step_matches_oracle(ctx):
+    """One step of the timed workload (2^20 cells as 10 + 10 interleaved bits, chi = 64, Re = 200,
+    dt = 8e-4, R = 40, the solver budgets of bench.py) through the captured CUDA graph that
+    bench.py replays, against the oracle's step on the same state.  At this size the step is
+    ill-conditioned with respect to rounding: the Poisson ALS (2 sweeps of 20 unconverged CG
+    iterations per site on a 2^20-cell problem) amplifies a 2^-50 relative change of its initial
+    guess into percent-level changes of the result (the oracle's own step moves by ~1.5 % in u,
+    ~12 % in v, ~4 % in p).  So the bar is that rounding spread: the GPU may differ from the
+    oracle by at most three times what the oracle differs from itself under that perturbation;
+    the CG iteration counts agree within two and the forces are finite."""
+    from paper_2507_05222_gb300 import qtt
+    ops, (u, v, p) = headline_state(ctx)
+    chi = 64
+    case = qtt.Case(ctx, 10, 10, 40.0, 200.0, 8e-4, chi, "interleaved", fit_sweeps=1, mom=(1, 8, 1e-10),
+                    poi=(2, 20, 1e-10))
+    case.use_graph(True)
+    case.set_state(qtt.MPS.from_cores(ctx, u), qtt.MPS.from_cores(ctx, v), qtt.MPS.from_cores(ctx, p))
+    info = case.fractional_step(1, with_forces=True)
+    o = S.StepOpts(chi=chi, fit_sweeps=1, mom_sweeps=1, mom_cg=8, poi_sweeps=2, poi_cg=20, cg_tol=1e-10)
+    ref = S.step(ops, u, v, p, o)
+    pert = S.step(ops, u, v, [c * (1.0 + 2.0 ** -50) for c in p], o)
+    oi = ref[3]
+    assert abs(info[0]["cg_u"] - oi["cg_u"]) <= 2 and abs(info[0]["cg_v"] - oi["cg_v"]) <= 2
+    assert abs(info[0]["cg_p"] - oi["cg_p"]) <= 2
+    for g, r, q in zip(case.get_state(), ref[:3], pert[:3]):
+        full_r = tt.full(r)
+        spread = rel(tt.full(q), full_r)
+        assert rel(qtt.qtt_decode(ctx, g), full_r) <= 3.0 * spread + 1e-10
+    assert np.isfinite(info[0]["cd"]) and np.isfinite(info[0]["cl"])
