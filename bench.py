@@ -237,13 +237,19 @@ def run_ours(args, cfg):
         x.get_flat(t.data_ptr())
     h2d = sum(sizes) * 8
     d2h = sum(sizes) * 8 + 40
-    t0 = time.perf_counter()
-    for k in range(args.steps):
+
+    def e2e_step():
         fields = [qtt.MPS.from_flat(ctx, b, 2, t.data_ptr()) for b, t in zip(bonds, pin_in)]
         case.set_state(*fields)
         info = qtt.fractional_step(ctx, case, 1, with_forces=True)
         for x, t in zip(case.get_state(), pin_out):
             x.get_flat(t.data_ptr())
+        return info
+
+    e2e_step()   # untimed: captures the step's graph with the force read-out once
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        info = e2e_step()
     e2e_s = (time.perf_counter() - t0) / args.steps
     # ---- CPU baseline: the FP64 oracle on the host cores, one step of the same workload
     cpu = None
