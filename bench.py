@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(workload="cylinder_qtt_step_2^20_chi64", n_eta=10, n_xi=10, ordering="interleaved", R=40.0,
                 Re=200.0, dt=8e-4, chi=64, fit_sweeps=1, mom=(1, 8, 1e-10), poi=(2, 20, 1e-10), seed=0)
 METRIC = "QTT fractional steps/s at 2^20 cells, chi=64, fixed oracle error; % TC/HBM roof"
-FP64_PEAK_TFLOPS = 1.012   # measured FP64 FMA throughput of this GB300 ("Peaks")
+FP64_PEAK_TFLOPS = 1.012   # FP64 FMA throughput measured on GB300 (independent FMA chains on all SMs)
 
 
 def env_rank():

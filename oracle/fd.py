@@ -19,9 +19,9 @@ What it computes (cited by section / equation of arXiv:2507.05222):
 * lift and drag from the wall stress (App. F, eq:liftdrag) and the Strouhal number
   from lift zero crossings (eq:st).
 
-Readings where the paper is silent or garbled are listed in the design doc (wall = ghost
-row i=-1; analytic metrics; Neumann ghost p_{-1}=p_0; stress with the outward
-cylinder normal and ds = (D/2) 2 pi d_xi).
+Readings where the paper is silent or garbled: the wall is ghost row i=-1 (App. E); the
+metric terms are analytic; the Neumann pressure ghost is p_{-1}=p_0; the wall stress uses
+the outward cylinder normal and ds = (D/2) 2 pi d_xi.
 """
 from __future__ import annotations
 
