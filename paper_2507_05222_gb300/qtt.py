@@ -212,7 +212,10 @@ class Context:
         _check(lib().qtt_ctx_set_gemm_mode(self.h, int(mode)))
 
     def set_cg_mode(self, mode: int):
-        """0: one cooperative kernel per ALS local CG solve (default); 1: one kernel per stage."""
+        """ALS local CG solves: 0 (default) one cooperative kernel per solve, its contractions on
+        the tensor cores at full-bond sites (bonds multiplying to >= 4096) and on the FP64 pipe
+        elsewhere; 1 one kernel per stage; 2 the cooperative kernel on the FP64 pipe only; 3 the
+        tensor-core contractions wherever the cooperative kernel fits."""
         _check(lib().qtt_ctx_set_cg_mode(self.h, int(mode)))
 
     def profile_phases(self):
