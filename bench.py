@@ -42,6 +42,24 @@ def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(values, world, device):
+    """Per-rank timings reduced to their element-wise maximum over the job's ranks (every rank
+    receives it); the identity on one rank.  device: "cuda" under NCCL, "cpu" under gloo."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_throughput(world, seconds_per_step):
+    """Whole-job steps/s of `world` independent replicas whose slowest rank takes
+    seconds_per_step per step (weak scaling: each rank advances its own case)."""
+    return world / seconds_per_step
+
+
 def initial_fields(cfg):
     from paper_2507_05222_gb300 import inputs
     ne, nx, chi, s = cfg["n_eta"], cfg["n_xi"], cfg["chi"], cfg["seed"]
@@ -210,10 +228,6 @@ def run_ours(args, cfg):
     ms = [a.elapsed_time(b) for a, b in ev]
     clk = clocks.stop()
     step_ms = sum(ms) / len(ms)
-    if world > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
     # ---- per-class kernel timing (roofline of the dominant class): the same kernels launched one
     # by one (timing events cannot sit inside the captured graph), L2 flushed between steps
     case.use_graph(False)
@@ -251,6 +265,7 @@ def run_ours(args, cfg):
     for k in range(args.steps):
         info = e2e_step()
     e2e_s = (time.perf_counter() - t0) / args.steps
+    step_ms, e2e_s = max_over_ranks([step_ms, e2e_s], world, "cuda")   # the slowest rank
     # ---- CPU baseline: the FP64 oracle on the host cores, one step of the same workload
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -258,7 +273,7 @@ def run_ours(args, cfg):
         cpu = {"value": sps, "unit": "steps/s", "cores": cores, "kind": "oracle",
                "sample": f"{done} full fractional step(s) of the workload, numpy FP64 oracle, {dt:.1f} s"}
     if rank == 0:
-        line = {"metric": METRIC, "value": world * 1e3 / step_ms, "unit": "steps/s", "n_gpus": world,
+        line = {"metric": METRIC, "value": job_throughput(world, step_ms * 1e-3), "unit": "steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering")}
@@ -266,7 +281,8 @@ def run_ours(args, cfg):
                    "l2": "256 MB buffer written between timed steps", "replicas": world,
                    **({"gemm_mode": args.gemm_mode} if args.gemm_mode is not None else {}),
                    **({"cg_mode": args.cg_mode} if args.cg_mode is not None else {})},
-                "e2e": {"value": world / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "e2e": {"value": job_throughput(world, e2e_s), "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
