@@ -13,6 +13,7 @@ The step (same sequence as the CUDA library, written independently):
    H = |J| (I - dt/Re Lap_h):  H u* = |J| (.) rhs_u + dt/Re |J| bcLap_u  (warm start u);
 4. pressure Poisson by ALS (eq:Poisson with the Jacobian weighting of Sec. III.C):
    (-|J| Lap_h^p) p = -|J| (.) (D_x u* + D_z v* + bc_div) / dt   (warm start p^m);
+   both solves sweep under the true-residual stop rule of ``tt.als`` (options ``SolveOpts``);
 5. projection, one fit each (warm start u*, v*):  u = u* - dt D_x^p p,  v = v* - dt D_z^p p.
 """
 from __future__ import annotations
@@ -26,14 +27,21 @@ from .qtt_ops import Ops
 
 
 @dataclass
+class SolveOpts:
+    """Options of one ALS solve (stop rule of ``tt.als``)."""
+    max_sweeps: int
+    rel_tol: float
+    cg_max_iter: int
+    cg_tol: float = 1e-2
+    stall: float = 0.1
+
+
+@dataclass
 class StepOpts:
     chi: int
     fit_sweeps: int = 1
-    mom_sweeps: int = 1
-    mom_cg: int = 8
-    poi_sweeps: int = 2
-    poi_cg: int = 20
-    cg_tol: float = 1e-12
+    mom: SolveOpts = field(default_factory=lambda: SolveOpts(4, 1e-12, 100))
+    poi: SolveOpts = field(default_factory=lambda: SolveOpts(12, 1e-10, 500))
 
 
 def _nz(terms):
@@ -52,15 +60,17 @@ def step(ops: Ops, u, v, p, o: StepOpts):
     rhs_v = tt.fit(_nz([("vec", 1.0, v), ("had", -dt, u, dxv), ("had", -dt, u, ops.bcx_v),
                         ("had", -dt, v, dzv), ("had", -dt, v, ops.bcz_v)]), v, o.fit_sweeps)
     k = dt / Re
-    us, cg_u = tt.als(ops.H, _nz([("mpo", 1.0, ops.Jdiag, rhs_u), ("vec", k, ops.JbcLap_u)]), u,
-                      o.mom_sweeps, o.mom_cg, o.cg_tol)
-    vs, cg_v = tt.als(ops.H, _nz([("mpo", 1.0, ops.Jdiag, rhs_v), ("vec", k, ops.JbcLap_v)]), v,
-                      o.mom_sweeps, o.mom_cg, o.cg_tol)
-    pn, cg_p = tt.als(ops.Ap, _nz([("mpo", 1.0, ops.Px, us), ("mpo", 1.0, ops.Pz, vs),
-                                   ("vec", 1.0, ops.bcdiv_w)]), p, o.poi_sweeps, o.poi_cg, o.cg_tol)
+    m, q = o.mom, o.poi
+    us, iu = tt.als(ops.H, _nz([("mpo", 1.0, ops.Jdiag, rhs_u), ("vec", k, ops.JbcLap_u)]), u,
+                    m.max_sweeps, m.cg_max_iter, m.cg_tol, m.rel_tol, m.stall)
+    vs, iv = tt.als(ops.H, _nz([("mpo", 1.0, ops.Jdiag, rhs_v), ("vec", k, ops.JbcLap_v)]), v,
+                    m.max_sweeps, m.cg_max_iter, m.cg_tol, m.rel_tol, m.stall)
+    pn, ip = tt.als(ops.Ap, _nz([("mpo", 1.0, ops.Px, us), ("mpo", 1.0, ops.Pz, vs),
+                                 ("vec", 1.0, ops.bcdiv_w)]), p, q.max_sweeps, q.cg_max_iter, q.cg_tol,
+                    q.rel_tol, q.stall)
     un = tt.fit([("vec", 1.0, us), ("mpo", -dt, ops.Dxp, pn)], us, o.fit_sweeps)
     vn = tt.fit([("vec", 1.0, vs), ("mpo", -dt, ops.Dzp, pn)], vs, o.fit_sweeps)
-    info = dict(cg_u=cg_u, cg_v=cg_v, cg_p=cg_p)
+    info = dict(u=iu, v=iv, p=ip, cg_u=iu["cg_iters"], cg_v=iv["cg_iters"], cg_p=ip["cg_iters"])
     return un, vn, pn, info
 
 

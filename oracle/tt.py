@@ -20,7 +20,9 @@ Operations and the passage each follows:
 * ``fit``                    -- variational (fit) evaluation of sums of products at fixed
                                 bond dimension (Sec. II.B, Table I right column);
 * ``als``                    -- single-site DMRG / ALS for SPD systems (Sec. II.A.4, Fig. 5)
-                                with local CG on the "fast matvec" (App. G).
+                                with local CG on the "fast matvec" (App. G), swept until the
+                                true relative residual (``residual``) meets a tolerance or
+                                stops falling (stop rule above ``als``).
 The truncation rule (keep min(chi, #sigma > eps*sigma_1, structural bound)) is the
 reading of Sec. II ("first chi values" / "below a threshold").
 """
@@ -415,15 +417,55 @@ def cg(matvec, b, x0, iters: int, tol: float):
     return x, it
 
 
-def als(A, terms, x0, sweeps: int, cg_iters: int, cg_tol: float):
+# Stop rule of the ALS solver (the paper leaves it open; Sec. II.A.4 only says "sweeps").
+# After every full sweep the true relative residual ||A x - b|| / ||b|| of the un-truncated
+# TT A x (+) (-b) is evaluated entry by entry (``residual``), and the solve stops with
+#   CONVERGED   once it is <= rel_tol;
+#   STALLED     once a sweep reduced it by less than the fraction ``stall`` (> 0; 0 disables the
+#               test): at a fixed bond the
+#               ALS converges to a stationary point of the energy on the rank-chi manifold, whose
+#               residual is bounded below by the truncation, so further sweeps cannot reach rel_tol;
+#   MAX_SWEEPS  after max_sweeps sweeps.
+# Each local CG solve of a sweep stops once ||r_loc|| <= cg_tol * res ||b_loc||, res being the
+# true relative residual before the sweep (inexact local solves tied to the global error), or
+# after cg_max_iter iterations.
+CONVERGED, STALLED, MAX_SWEEPS = 0, 1, 2
+
+
+def dense_terms(terms) -> np.ndarray:
+    """Dense value of a sum of fit/ALS terms, each product formed as a TT first (no dense matrix)."""
+    out = 0.0
+    for term in terms:
+        if term[0] == "vec":
+            out = out + term[1] * full(term[2])
+        elif term[0] == "had":
+            out = out + term[1] * full(term[2]) * full(term[3])
+        else:
+            out = out + term[1] * full(mpo_mps(term[2], term[3]))
+    return out
+
+
+def residual(A, x, b_dense, b_norm) -> float:
+    """||A x - b|| / ||b||: the exact TT A x is reconstructed and b subtracted entry by entry, so
+    the difference carries only the rounding of each entry (no cancellation of squared norms)."""
+    r = full(mpo_mps(A, x)) - b_dense
+    return float(np.linalg.norm(r) / b_norm)
+
+
+def als(A, terms, x0, max_sweeps: int, cg_max_iter: int, cg_tol: float, rel_tol: float = 0.0,
+        stall: float = 0.1):
     """Single-site ALS for A x = sum(terms) with A symmetric positive definite.
 
     Minimises 1/2 <x, A x> - <x, b> core by core (Sec. II.A.4): the local system
     M_eff x_k = b_eff (size r_{k-1} d r_k) is solved by CG on the fast matvec,
     warm-started from the current core; the core is then split by QR and the R factor
-    pushed into the neighbour (gauge move).  Sweeps alternate left-to-right and
-    right-to-left; the result is right-canonical.
+    pushed into the neighbour (gauge move).  A sweep is a left-to-right half-sweep followed
+    by a right-to-left one; the result is right-canonical.  Sweeps continue under the stop rule
+    above.  Returns (x, info) with info = dict(sweeps, cg_iters, rel_residual, status, history).
     """
+    b_dense = dense_terms(terms)
+    nb = float(np.linalg.norm(b_dense))
+    nb = nb if nb > 0.0 else 1.0
     x = right_orth(x0)
     n = len(x)
     d = x[0].shape[1]
@@ -438,18 +480,25 @@ def als(A, terms, x0, sweeps: int, cg_iters: int, cg_tol: float):
         for t, term in enumerate(terms):
             Rs[t][k] = _right_update(term, Rs[t][k + 1], x[k], k)
     total_cg = 0
+    res = residual(A, x, b_dense, nb)
+    history = [res]
 
-    def solve_site(k):
+    def solve_site(k, tol):
         nonlocal total_cg
         bk = sum(_local(term, Ls[t][k], Rs[t][k + 1], k) for t, term in enumerate(terms))
         mv = lambda v: _op_local(LA[k], A[k], RA[k + 1], v)
-        xk, it = cg(mv, bk, x[k], cg_iters, cg_tol)
+        xk, it = cg(mv, bk, x[k], cg_max_iter, tol)
         total_cg += it
         return xk
 
-    for _ in range(sweeps):
+    status = MAX_SWEEPS
+    if res <= rel_tol:
+        status = CONVERGED
+    sweep = 0
+    while status != CONVERGED and sweep < max_sweeps:
+        tol = cg_tol * res
         for k in range(n):
-            xk = solve_site(k)
+            xk = solve_site(k, tol)
             if k < n - 1:
                 r0, _, r1 = xk.shape
                 Q, R = qr_pos(xk.reshape(r0 * d, r1))
@@ -461,7 +510,7 @@ def als(A, terms, x0, sweeps: int, cg_iters: int, cg_tol: float):
             else:
                 x[k] = xk
         for k in range(n - 1, -1, -1):
-            xk = solve_site(k)
+            xk = solve_site(k, tol)
             if k > 0:
                 r0, _, r1 = xk.shape
                 Q, R = qr_pos(xk.reshape(r0, d * r1).T)
@@ -472,17 +521,20 @@ def als(A, terms, x0, sweeps: int, cg_iters: int, cg_tol: float):
                     Rs[t][k] = _right_update(term, Rs[t][k + 1], x[k], k)
             else:
                 x[k] = xk
-    return x, total_cg
+        sweep += 1
+        new = residual(A, x, b_dense, nb)
+        history.append(new)
+        if new <= rel_tol:
+            status = CONVERGED
+        elif stall > 0.0 and not (new <= (1.0 - stall) * res):
+            status = STALLED
+        res = new
+        if status == STALLED:
+            break
+    info = dict(sweeps=sweep, cg_iters=total_cg, rel_residual=res, status=status, history=history)
+    return x, info
 
 
 def terms_full(terms) -> np.ndarray:
     """Dense value of a list of fit/ALS terms (for tests)."""
-    out = 0.0
-    for term in terms:
-        if term[0] == "vec":
-            out = out + term[1] * full(term[2])
-        elif term[0] == "had":
-            out = out + term[1] * full(term[2]) * full(term[3])
-        else:
-            out = out + term[1] * (full_mpo(term[2]) @ full(term[3]))
-    return out
+    return dense_terms(terms)

@@ -334,16 +334,75 @@ def test_cg_solves_spd():
 
 def test_als_full_rank_equals_sparse_solve():
     """Single-site ALS (Sec. II.A.4) at full bond dimension reaches the sparse direct
-    solution of the J-weighted Poisson problem (Sec. III.C)."""
+    solution of the J-weighted Poisson problem (Sec. III.C) and stops on the residual."""
     ne, nx = 3, 4
     ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, "interleaved")
     n = ne + nx
     rhs = inputs.random_cores(n, 4, seed=31)
     x0 = inputs.random_cores(n, 16, seed=32, scale=0.1)
-    x, _ = tt.als(ops.Ap, [("vec", 1.0, rhs)], x0, sweeps=6, cg_iters=300, cg_tol=1e-15)
+    x, info = tt.als(ops.Ap, [("vec", 1.0, rhs)], x0, max_sweeps=8, cg_max_iter=300, cg_tol=1e-3,
+                     rel_tol=1e-12, stall=0.0)
     A = tt.full_mpo(ops.Ap)
     ref = spla.spsolve(sp.csr_matrix(A), tt.full(rhs))
+    assert info["status"] == tt.CONVERGED and info["rel_residual"] <= 1e-12
+    assert info["sweeps"] == len(info["history"]) - 1 and info["sweeps"] <= 8
     assert np.allclose(tt.full(x), ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+def test_residual_is_entrywise_and_resolves_rounding_level():
+    """The ALS stop test's residual ||A x - b|| / ||b|| equals the dense matrix-vector value, and
+    for the exact solution it is at rounding level (~1e-15), far below the ~1e-8 floor of the
+    expanded form ||Ax||^2 - 2 <b, Ax> + ||b||^2 (which cancels)."""
+    ne, nx = 3, 4
+    ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, "interleaved")
+    n = ne + nx
+    x = inputs.random_cores(n, 16, seed=33)
+    b = inputs.random_cores(n, 4, seed=34)
+    bd = tt.full(b)
+    A = tt.full_mpo(ops.Ap)
+    want = np.linalg.norm(A @ tt.full(x) - bd) / np.linalg.norm(bd)
+    assert abs(tt.residual(ops.Ap, x, bd, np.linalg.norm(bd)) - want) <= 1e-13 * want
+    xs = np.linalg.solve(A, bd)
+    xe = tt.tt_svd(xs, n, 2, 64)
+    r = tt.residual(ops.Ap, xe, bd, np.linalg.norm(bd))
+    assert r < 1e-13
+    y = tt.mpo_mps(ops.Ap, xe)
+    expanded = tt.dot(y, y) - 2 * tt.dot(b, y) + tt.dot(b, b)
+    assert np.sqrt(abs(expanded)) / np.linalg.norm(bd) > 10 * r
+
+
+def test_als_stop_rule_stalls_at_the_rank_floor():
+    """At a bond below the solution's rank the ALS residual levels off (the truncation bounds it
+    from below): the solve ends STALLED once a sweep gains less than the stall fraction; the energy
+    1/2 <x, A x> - <b, x> never rises (every local CG step minimises it); max_sweeps ends an
+    unfinished solve as MAX_SWEEPS; a solve that starts at the solution takes no sweep."""
+    ne = nx = 4
+    ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, "interleaved")
+    n = ne + nx
+    rhs = inputs.random_cores(n, 16, seed=35)
+    x0 = inputs.random_cores(n, 4, seed=36, scale=0.1)
+    x, info = tt.als(ops.Ap, [("vec", 1.0, rhs)], x0, max_sweeps=30, cg_max_iter=500, cg_tol=1e-3,
+                     rel_tol=1e-12, stall=0.05)
+    h = info["history"]
+    assert info["status"] == tt.STALLED
+    assert h[-1] > 0.95 * h[-2] and all(b <= 0.95 * a for a, b in zip(h[:-2], h[1:-1]))
+    assert info["rel_residual"] == h[-1] > 1e-6
+    bd = tt.full(rhs)
+    A = tt.full_mpo(ops.Ap)
+    energy = []
+    for s in range(1, 6):
+        xs, _ = tt.als(ops.Ap, [("vec", 1.0, rhs)], x0, max_sweeps=s, cg_max_iter=500, cg_tol=1e-3,
+                       rel_tol=0.0, stall=0.0)
+        f = tt.full(xs)
+        energy.append(0.5 * f @ (A @ f) - bd @ f)
+    assert all(b <= a + 1e-12 * abs(a) for a, b in zip(energy, energy[1:]))
+    _, info = tt.als(ops.Ap, [("vec", 1.0, rhs)], x0, max_sweeps=2, cg_max_iter=500, cg_tol=1e-3,
+                     rel_tol=1e-14, stall=0.0)
+    assert info["status"] == tt.MAX_SWEEPS and info["sweeps"] == 2
+    xe = tt.tt_svd(np.linalg.solve(A, bd), n, 2, 256)
+    _, info = tt.als(ops.Ap, [("vec", 1.0, rhs)], xe, max_sweeps=5, cg_max_iter=10, cg_tol=1e-3,
+                     rel_tol=1e-10, stall=0.1)
+    assert info["status"] == tt.CONVERGED and info["sweeps"] == 0 and info["cg_iters"] == 0
 
 
 # ------------------------------------------------------------------ L0 step and diagnostics
@@ -424,8 +483,11 @@ def test_l1_step_equals_l0_at_full_rank(ordering):
     v0 = inputs.gaussian_field(ne, nx, 2, 1e-3)
     u, v = ops.encode(u0, chi), ops.encode(v0, chi)
     p = S.padded([np.zeros((1, 2, 1))] * (ne + nx), chi, inputs.random_cores(ne + nx, chi, 3, scale=1e-8))
-    o = S.StepOpts(chi=chi, fit_sweeps=2, mom_sweeps=3, mom_cg=100, poi_sweeps=6, poi_cg=200, cg_tol=1e-15)
-    un, vn, pn, _ = S.step(ops, u, v, p, o)
+    o = S.StepOpts(chi=chi, fit_sweeps=2, mom=S.SolveOpts(6, 1e-14, 200, 1e-3, 0.0),
+                   poi=S.SolveOpts(8, 1e-13, 300, 1e-3, 0.0))
+    un, vn, pn, info = S.step(ops, u, v, p, o)
+    for k in "uvp":
+        assert info[k]["status"] == tt.CONVERGED
     uf, vf, pf, _, _ = L0.step(u0, v0)
     for a, b in ((un, uf), (vn, vf), (pn, pf)):
         b = b.reshape(2 ** ne, 2 ** nx)
