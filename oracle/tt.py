@@ -115,10 +115,11 @@ def qr_pos(a):
     return np.linalg.qr(a, mode="reduced")
 
 
-def round_tt(cores, chi: int, eps: float = 0.0):
+def round_tt(cores, chi: int, eps: float = 0.0, info: dict | None = None):
     """TT-rounding (Sec. II.A): left-to-right QR, then right-to-left truncated SVD.
 
-    Equals ``tt_svd`` of the represented tensor with pre_bonds = bonds(cores).
+    Equals ``tt_svd`` of the represented tensor with pre_bonds = bonds(cores).  ``info`` (a dict,
+    optional) receives ``discarded_norm`` = sqrt(sum over cuts of the discarded sigma^2).
     """
     d = cores[0].shape[1]
     n = len(cores)
@@ -130,12 +131,16 @@ def round_tt(cores, chi: int, eps: float = 0.0):
         Q, R = qr_pos(c[k].reshape(r0 * d, r1))
         c[k] = Q.reshape(r0, d, Q.shape[1])
         c[k + 1] = np.einsum("ab,bsc->asc", R, c[k + 1])
+    disc = 0.0
     for k in range(n - 1, 0, -1):
         r0, _, r1 = c[k].shape
         U, S, Vt = np.linalg.svd(c[k].reshape(r0, d * r1), full_matrices=False)
         b = kept_rank(S, chi, eps, min(m[k], d * r1))
+        disc += float(np.sum(S[b:] ** 2))
         c[k] = Vt[:b].reshape(b, d, r1)
         c[k - 1] = np.einsum("asb,bc->asc", c[k - 1], U[:, :b] * S[:b])
+    if info is not None:
+        info["discarded_norm"] = float(np.sqrt(disc))
     return c
 
 
@@ -390,39 +395,47 @@ def _op_local(L, W, R, x):
     return np.einsum("cwa,wstv,atb,dvb->csd", L, W, x, R, optimize=OPT)
 
 
-def cg(matvec, b, x0, iters: int, tol: float):
-    """Conjugate gradients with a fixed iteration budget; stops early only when
-    ||r|| <= tol ||b|| (or r = 0)."""
+def cg(matvec, b, x0, iters: int, tol: float, dinv=None):
+    """Conjugate gradients (preconditioned by the diagonal scaling ``dinv`` when given) with an
+    iteration budget; stops early when ||r|| <= tol ||b|| (or r = 0, or p.Ap <= 0)."""
     x = x0.copy()
     r = b - matvec(x)
-    p = r.copy()
+    z = r * dinv if dinv is not None else r
+    p = z.copy()
     rr = float(np.vdot(r, r))
+    rz = float(np.vdot(r, z))
     bb = float(np.vdot(b, b))
     it = 0
-    for it in range(iters):
-        if rr <= tol * tol * bb or rr == 0.0:
-            break
+    while it < iters and rr > tol * tol * bb and rr > 0.0:
         Ap = matvec(p)
         pAp = float(np.vdot(p, Ap))
         if pAp <= 0.0:
             break
-        alpha = rr / pAp
+        alpha = rz / pAp
         x = x + alpha * p
         r = r - alpha * Ap
-        rr_new = float(np.vdot(r, r))
-        p = r + (rr_new / rr) * p
-        rr = rr_new
-    else:
-        it = iters
+        z = r * dinv if dinv is not None else r
+        rz_new = float(np.vdot(r, z))
+        rr = float(np.vdot(r, r))
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        it += 1
     return x, it
+
+
+def local_diag(L, W, R):
+    """Diagonal of the local ALS matrix L . W . R (Fig. 5): d[c, s, e] = sum_{w, v} L[c, w, c]
+    W[w, s, s, v] R[e, v, e]."""
+    return np.einsum("cwc,wssv,eve->cse", L, W, R)
 
 
 # Stop rule of the ALS solver (the paper leaves it open; Sec. II.A.4 only says "sweeps").
 # After every full sweep the true relative residual ||A x - b|| / ||b|| of the un-truncated
 # TT A x (+) (-b) is evaluated entry by entry (``residual``), and the solve stops with
 #   CONVERGED   once it is <= rel_tol;
-#   STALLED     once a sweep reduced it by less than the fraction ``stall`` (> 0; 0 disables the
-#               test): at a fixed bond the
+#   STALLED     once a sweep after the first reduced it by less than the fraction ``stall`` (> 0;
+#               0 disables the test; the first sweep from a poor start may raise the residual,
+#               since the sweeps minimise the energy, not the residual): at a fixed bond the
 #               ALS converges to a stationary point of the energy on the rank-chi manifold, whose
 #               residual is bounded below by the truncation, so further sweeps cannot reach rel_tol;
 #   MAX_SWEEPS  after max_sweeps sweeps.
@@ -457,11 +470,12 @@ def als(A, terms, x0, max_sweeps: int, cg_max_iter: int, cg_tol: float, rel_tol:
     """Single-site ALS for A x = sum(terms) with A symmetric positive definite.
 
     Minimises 1/2 <x, A x> - <x, b> core by core (Sec. II.A.4): the local system
-    M_eff x_k = b_eff (size r_{k-1} d r_k) is solved by CG on the fast matvec,
-    warm-started from the current core; the core is then split by QR and the R factor
-    pushed into the neighbour (gauge move).  A sweep is a left-to-right half-sweep followed
-    by a right-to-left one; the result is right-canonical.  Sweeps continue under the stop rule
-    above.  Returns (x, info) with info = dict(sweeps, cg_iters, rel_residual, status, history).
+    M_eff x_k = b_eff (size r_{k-1} d r_k) is solved by CG on the fast matvec, preconditioned
+    by the inverse of M_eff's diagonal (the paper preconditions the local updates but does not
+    say how, App. G; where a diagonal entry is not positive it is left unscaled), warm-started
+    from the current core; the core is then split by QR and the R factor pushed into the
+    neighbour (gauge move).  A sweep is a left-to-right half-sweep followed by a right-to-left
+    one; the result is right-canonical.  Sweeps continue under the stop rule above.  Returns (x, info) with info = dict(sweeps, cg_iters, rel_residual, status, history).
     """
     b_dense = dense_terms(terms)
     nb = float(np.linalg.norm(b_dense))
@@ -487,7 +501,9 @@ def als(A, terms, x0, max_sweeps: int, cg_max_iter: int, cg_tol: float, rel_tol:
         nonlocal total_cg
         bk = sum(_local(term, Ls[t][k], Rs[t][k + 1], k) for t, term in enumerate(terms))
         mv = lambda v: _op_local(LA[k], A[k], RA[k + 1], v)
-        xk, it = cg(mv, bk, x[k], cg_max_iter, tol)
+        dg = local_diag(LA[k], A[k], RA[k + 1])
+        dinv = np.where(dg > 0.0, 1.0 / np.where(dg > 0.0, dg, 1.0), 1.0)
+        xk, it = cg(mv, bk, x[k], cg_max_iter, tol, dinv)
         total_cg += it
         return xk
 
@@ -526,7 +542,7 @@ def als(A, terms, x0, max_sweeps: int, cg_max_iter: int, cg_tol: float, rel_tol:
         history.append(new)
         if new <= rel_tol:
             status = CONVERGED
-        elif stall > 0.0 and not (new <= (1.0 - stall) * res):
+        elif stall > 0.0 and sweep >= 2 and not (new <= (1.0 - stall) * res):
             status = STALLED
         res = new
         if status == STALLED:

@@ -296,6 +296,21 @@ def test_direct_sum_mpo_mps_hadamard_dense():
     assert np.isclose(tt.dot(a, b), ad @ bd, rtol=1e-12)
 
 
+def test_round_discarded_norm_is_the_rounding_error():
+    """The discarded norm of a canonical TT-SVD sweep equals ||x - round(x)||: the truncation
+    errors of different cuts are orthogonal (the left part is orthonormal at every cut), so the
+    TT-SVD bound of Sec. II's rounding holds with equality."""
+    x = inputs.random_cores(10, 16, seed=5)
+    for chi in (4, 8, 12, 32):
+        info = {}
+        y = tt.round_tt(x, chi, info=info)
+        err = np.linalg.norm(tt.full(x) - tt.full(y))
+        assert abs(info["discarded_norm"] - err) <= 1e-12 * np.linalg.norm(tt.full(x))
+    info = {}
+    tt.round_tt(x, 64, info=info)
+    assert info["discarded_norm"] == 0.0
+
+
 def test_fit_exact_when_representable():
     """Variational fit (Table I) is exact when the target has rank <= chi: Hadamard of
     rank-2 sin and rank-1 exp fields, plus an MPO term and a plain term."""
@@ -325,11 +340,28 @@ def test_hadamard_round_quality():
 
 
 def test_cg_solves_spd():
+    """CG and diagonally preconditioned CG reach the direct solution of an SPD system; on a
+    badly scaled matrix the preconditioned one needs far fewer iterations."""
     g = inputs.rng(3)
     A = g.standard_normal((30, 30)); A = A @ A.T + 30 * np.eye(30)
     b = g.standard_normal(30)
     x, it = tt.cg(lambda v: A @ v, b, np.zeros(30), 200, 1e-14)
     assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-10)
+    Dm = np.diag(np.logspace(0, 4, 30))
+    B = Dm @ A @ Dm
+    x0, it0 = tt.cg(lambda v: B @ v, b, np.zeros(30), 2000, 1e-13)
+    x1, it1 = tt.cg(lambda v: B @ v, b, np.zeros(30), 2000, 1e-13, dinv=1.0 / np.diag(B))
+    ref = np.linalg.solve(B, b)
+    assert np.allclose(x1, ref, rtol=1e-8) and it1 < it0 / 3
+
+
+def test_local_diag_is_the_diagonal_of_the_local_matrix():
+    """The ALS preconditioner's diagonal equals the diagonal of the assembled local matrix
+    (Fig. 5: M_eff = L (x) W (x) R contracted over the operator bonds)."""
+    g = inputs.rng(4)
+    L = g.standard_normal((5, 3, 5)); W = g.standard_normal((3, 2, 2, 4)); R = g.standard_normal((6, 4, 6))
+    M = np.einsum("cwa,wstv,evb->cseatb", L, W, R).reshape(5 * 2 * 6, 5 * 2 * 6)
+    assert np.allclose(tt.local_diag(L, W, R).ravel(), np.diag(M), rtol=1e-13, atol=0)
 
 
 def test_als_full_rank_equals_sparse_solve():
