@@ -2,16 +2,20 @@
 
 Workload (the headline configuration): stationary cylinder, log-polar O-grid
 r in [0.5, 20] D (R = 40), 2^10 x 2^10 cells (20 interleaved quantics bits), Re = 200,
-dt = 8e-4, chi = 64, FP64.  Synthetic seeded state: uniform inflow plus a Gaussian
-perturbation of amplitude 1e-3 on u and v, pressure zero padded with 1e-8 noise.
-A step = one full fractional step: four MPO-MPS products with rounding, two fused
-variational right-hand sides, two momentum ALS solves, one Poisson ALS solve, two
-projection fits.
+dt = 8e-4, chi = 64, FP64.  Synthetic seeded state: a smooth wake-shaped velocity field
+(inputs.wake_field: wall layer, a deficit behind the cylinder, travelling-wave packets)
+encoded at chi = 64, pressure zero padded with 1e-8 noise; the warm-up steps give it a
+consistent pressure.  A step = one full fractional step: four MPO-MPS products with
+rounding, two fused variational right-hand sides, two momentum ALS solves and one Poisson
+ALS solve, each swept until its true relative residual meets its tolerance or stops
+falling (include/qtt.h), two projection fits.
 
 Output: one JSON line on rank 0 (see the build contract): steps/s over K device-timed steps
-(L2 flushed between steps), end-to-end steps/s through host buffers, roofline of the FP64
-GEMM (the dominant kernel class), clocks during the timed region, kernel launches, and the
-FP64 oracle timed on the host cores as a baseline.
+(L2 flushed between steps), the solve records of the timed steps, end-to-end steps/s through
+host buffers, the roofline of the dominant kernel class (the cooperative CG solves), clocks
+during the timed region, kernel launches, the fixed-error checks (GPU step against the FP64
+oracle's step from the same state; C_D, C_L with every product on the FP64 pipe) and the FP64
+oracle timed on the host cores as a baseline.
 
 --impl reference times the FP64 oracle (the CPU program the GPU path is checked against)
 on the same workload.
@@ -32,10 +36,18 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# Solve options (max_sweeps, rel_tol, cg_max_iter, cg_tol, stall): the stop rule of include/qtt.h.
 WORKLOAD = dict(workload="cylinder_qtt_step_2^20_chi64", n_eta=10, n_xi=10, ordering="interleaved", R=40.0,
-                Re=200.0, dt=8e-4, chi=64, fit_sweeps=1, mom=(1, 8, 1e-10), poi=(2, 20, 1e-10), seed=0)
+                Re=200.0, dt=8e-4, chi=64, fit_sweeps=1, mom=(6, 1e-10, 100, 1e-2, 0.1),
+                poi=(12, 1e-10, 500, 1e-2, 0.1), seed=7)
 METRIC = "QTT fractional steps/s at 2^20 cells, chi=64, fixed oracle error; % TC/HBM roof"
-FP64_PEAK_TFLOPS = 1.012   # FP64 FMA throughput measured on GB300 (independent FMA chains on all SMs)
+# FP64 ALU peak: 152 SMs x 2 FP64 FMA per clock (measured per SM) x 2 flops x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Bound on the GPU-oracle difference of one step (relative, per field), derived from the
+# converged step's own sensitivity at this size: a 2^-50 relative change of the initial
+# pressure moves the oracle's step by up to 1.7e-7 (v), so a difference within ten times that
+# is a difference in rounding, not in the algorithm.
+STEP_PARITY_BOUND = 2e-6
 
 
 def env_rank():
@@ -63,9 +75,8 @@ def job_throughput(world, seconds_per_step):
 def initial_fields(cfg):
     from paper_2507_05222_gb300 import inputs
     ne, nx, chi, s = cfg["n_eta"], cfg["n_xi"], cfg["chi"], cfg["seed"]
-    u0 = 1.0 + inputs.gaussian_field(ne, nx, s + 1, 1e-3)
-    v0 = inputs.gaussian_field(ne, nx, s + 2, 1e-3)
-    pad = inputs.random_cores(ne + nx, chi, s + 3, scale=1e-8)
+    u0, v0 = inputs.wake_field(ne, nx, s)
+    pad = inputs.random_cores(ne + nx, chi, s + 2, scale=1e-8)
     return u0, v0, pad
 
 
@@ -110,25 +121,34 @@ class Clocks:
                 "reasons": reasons, "samples": len(sm)}
 
 
-def oracle_steps(cfg, k_steps, budget_s=None):
-    """Time the FP64 oracle (L1 QTT step, numpy) on the host cores; returns (steps/s, steps, s, cores)."""
+def oracle_start(cfg):
+    """The oracle's ops and the workload's initial cores (the same cores the GPU starts from)."""
     from oracle import qtt_ops as Q, step as S
-    import numpy as np
     u0, v0, pad = initial_fields(cfg)
     ops = Q.Ops(cfg["n_eta"], cfg["n_xi"], cfg["R"], cfg["Re"], cfg["dt"], cfg["ordering"])
     u, v = ops.encode(u0, cfg["chi"]), ops.encode(v0, cfg["chi"])
     p = S.padded([np.zeros((1, 2, 1))] * (cfg["n_eta"] + cfg["n_xi"]), cfg["chi"], pad)
-    o = S.StepOpts(chi=cfg["chi"], fit_sweeps=cfg["fit_sweeps"], mom_sweeps=cfg["mom"][0], mom_cg=cfg["mom"][1],
-                   poi_sweeps=cfg["poi"][0], poi_cg=cfg["poi"][1], cg_tol=cfg["poi"][2])
+    o = S.StepOpts(chi=cfg["chi"], fit_sweeps=cfg["fit_sweeps"], mom=S.SolveOpts(*cfg["mom"]),
+                   poi=S.SolveOpts(*cfg["poi"]))
+    return ops, (u, v, p), o
+
+
+def oracle_steps(cfg, k_steps, budget_s=None):
+    """Time the FP64 oracle (L1 QTT step, numpy) on the host cores from the workload's initial
+    state; returns (steps/s, steps, seconds, cores, cores of the state after the first step)."""
+    from oracle import step as S
+    ops, (u, v, p), o = oracle_start(cfg)
     t0 = time.perf_counter()
-    done = 0
+    done, first = 0, None
     for _ in range(k_steps):
         u, v, p, _ = S.step(ops, u, v, p, o)
         done += 1
+        if first is None:
+            first = (u, v, p)
         if budget_s is not None and time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return done / dt, done, dt, len(os.sched_getaffinity(0))
+    return done / dt, done, dt, len(os.sched_getaffinity(0)), first
 
 
 def run_reference(args, cfg):
@@ -137,11 +157,13 @@ def run_reference(args, cfg):
         return
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state; its warm-up steps would only repeat the timed work
-    sps, done, dt, cores = oracle_steps(cfg, args.steps)
+    # each oracle step takes tens of seconds at the headline size: stop after ~150 s of steps
+    sps, done, dt, cores, _ = oracle_steps(cfg, args.steps, budget_s=150.0)
     line = {"impl": "reference", "metric": METRIC, "value": sps, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * dt / done, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering")},
+            "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering")}
+            | {"mom_solve": list(cfg["mom"]), "poisson_solve": list(cfg["poi"]), "fit_sweeps": cfg["fit_sweeps"]},
             "cpu_baseline": {"value": sps, "unit": "steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{done} full fractional steps of the workload (numpy FP64 oracle)"},
             "e2e": {"value": sps, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -183,30 +205,35 @@ def run_ours(args, cfg):
         # kernel-class time by step phase, kernels launched one by one (eager), next to the
         # phase wall times of a replayed graph step
         for _ in range(2):
-            qtt.fractional_step(ctx, case, 1, info=False)
+            qtt.fractional_step(ctx, case, 1, check=False)
         ctx.sync()
         graph_phases = case.phase_ms()
         case.use_graph(False)
-        qtt.fractional_step(ctx, case, 1, info=False)
+        qtt.fractional_step(ctx, case, 1, check=False)
         ctx.sync()
         ctx.profile(True)
-        qtt.fractional_step(ctx, case, 1, info=False)
+        qtt.fractional_step(ctx, case, 1, check=False)
         ctx.profile(False)
         print(json.dumps({"graph_phase_ms": graph_phases, "eager_phase_ms": case.phase_ms(),
                           "eager_kernel_ms_by_phase": ctx.profile_phases()}))
         return
     if args.profile_one_step:
-        qtt.fractional_step(ctx, case, 1, info=False)
+        qtt.fractional_step(ctx, case, 1, check=False)
         ctx.sync()
         qtt.profiler_range(True)
-        qtt.fractional_step(ctx, case, 1, info=False)
+        qtt.fractional_step(ctx, case, 1, check=False)
         ctx.sync()
         qtt.profiler_range(False)
         return
     flush = torch.empty(int(256 * 2 ** 20 // 4), dtype=torch.float32, device="cuda")  # 256 MB > L2 (129 MB)
     stream = ctx.stream
-    for _ in range(args.warmup):
-        qtt.fractional_step(ctx, case, 1, info=False)
+    # warm-up steps; the first one (captured into the step graph on its first replay) is kept
+    # for the parity check against the oracle's first step from the same state
+    first = None
+    for w in range(args.warmup):
+        qtt.fractional_step(ctx, case, 1, check=False)
+        if w == 0:
+            first = [qtt.qtt_decode(ctx, x) for x in case.get_state()] if ne + nx <= 24 else None
     ctx.sync()
     # ---- timed region: K device-timed steps, L2 flushed between steps (outside the events)
     clocks = Clocks(local)
@@ -216,11 +243,12 @@ def run_ours(args, cfg):
     torch.cuda.synchronize()
     n0 = ctx.kernel_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    recs = []
     with torch.cuda.stream(stream):
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(stream)
-            qtt.fractional_step(ctx, case, 1, info=False)
+            recs += qtt.fractional_step(ctx, case, 1, check=False)
             ev[k][1].record(stream)
     torch.cuda.synchronize()
     launches = ctx.kernel_launches() - n0
@@ -228,18 +256,44 @@ def run_ours(args, cfg):
     ms = [a.elapsed_time(b) for a, b in ev]
     clk = clocks.stop()
     step_ms = sum(ms) / len(ms)
-    # ---- per-class kernel timing (roofline of the dominant class): the same kernels launched one
-    # by one (timing events cannot sit inside the captured graph), L2 flushed between steps
+    solves = {k: dict(sweeps=[r[k]["sweeps"] for r in recs], cg_iters=[r[k]["cg_iters"] for r in recs],
+                      max_rel_residual=max(r[k]["rel_residual"] for r in recs),
+                      statuses=sorted({qtt.SOLVE_STATUS.get(r[k]["status"], str(r[k]["status"])) for r in recs}))
+              for k in "uvp"}
+    solves_ok = all(r["rc"] == 0 and r["finite"] == 1 for r in recs)
+    # ---- per-class kernel timing (roofline of the dominant class): one step launched kernel by
+    # kernel with events around every launch (events cannot sit inside the captured graph),
+    # from the state the timed steps left, L2 flushed first
+    snap = [x.copy() for x in case.get_state()]
     case.use_graph(False)
+    flush.fill_(-1.0)
     ctx.profile(True)
-    for k in range(min(args.steps, 2)):
-        flush.fill_(float(k))
-        qtt.fractional_step(ctx, case, 1, info=False)
+    qtt.fractional_step(ctx, case, 1, check=False)
     prof = ctx.profile(False)
+    eager_phases = case.phase_ms()
+    by_phase = ctx.profile_phases()
     case.use_graph(True)
-    nprof = min(args.steps, 2)
-    g = prof["gemm_f64"]
-    achieved = g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else 0.0
+    case.set_state(*snap)
+    cg = prof["cg_update"]
+    achieved = cg["flops"] / (cg["ms"] * 1e-3) / 1e12 if cg["ms"] > 0 else 0.0
+    eager_ms = sum(eager_phases.values())
+    # ---- C_D, C_L drift against the FP64 pipe: the same K steps from the same state with every
+    # product on the FP64 pipe (gemm mode 1) instead of the digit-split tensor-core products
+    drift = None
+    if not args.no_checks and args.gemm_mode is None:
+        base = qtt.fractional_step(ctx, case, args.steps, with_forces=True, check=False)
+        case.set_state(*snap)
+        ctx.set_gemm_mode(1)
+        case.use_graph(True)
+        f64 = qtt.fractional_step(ctx, case, args.steps, with_forces=True, check=False)
+        ctx.set_gemm_mode(0)
+        case.use_graph(True)
+        case.set_state(*snap)
+        drift = {"cd_rel": abs(base[-1]["cd"] - f64[-1]["cd"]) / abs(f64[-1]["cd"]),
+                 "cl_rel": abs(base[-1]["cl"] - f64[-1]["cl"]) / max(abs(f64[-1]["cl"]), 1e-300),
+                 "cd": [base[-1]["cd"], f64[-1]["cd"]], "cl": [base[-1]["cl"], f64[-1]["cl"]],
+                 "steps": args.steps, "ok": None}
+        drift["ok"] = bool(drift["cd_rel"] <= 1e-3 and drift["cl_rel"] <= 1e-3)
     # ---- end to end through the C ABI with host buffers: state cores in from pinned host
     # memory, one step, state cores and force coefficients back to the host
     state = case.get_state()
@@ -250,12 +304,12 @@ def run_ours(args, cfg):
     for x, t in zip(state, pin_in):
         x.get_flat(t.data_ptr())
     h2d = sum(sizes) * 8
-    d2h = sum(sizes) * 8 + 40
+    d2h = sum(sizes) * 8 + 16
 
     def e2e_step():
         fields = [qtt.MPS.from_flat(ctx, b, 2, t.data_ptr()) for b, t in zip(bonds, pin_in)]
         case.set_state(*fields)
-        info = qtt.fractional_step(ctx, case, 1, with_forces=True)
+        info = qtt.fractional_step(ctx, case, 1, with_forces=True, check=False)
         for x, t in zip(case.get_state(), pin_out):
             x.get_flat(t.data_ptr())
         return info
@@ -266,19 +320,27 @@ def run_ours(args, cfg):
         info = e2e_step()
     e2e_s = (time.perf_counter() - t0) / args.steps
     step_ms, e2e_s = max_over_ranks([step_ms, e2e_s], world, "cuda")   # the slowest rank
-    # ---- CPU baseline: the FP64 oracle on the host cores, one step of the same workload
-    cpu = None
+    # ---- CPU baseline: the FP64 oracle on the host cores, one step of the workload from its
+    # initial state; that step is also the parity reference of the GPU's first warm-up step
+    cpu, parity = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        sps, done, dt, cores = oracle_steps(cfg, 2, budget_s=20.0)
+        from oracle import tt
+        sps, done, dt, cores, ofirst = oracle_steps(cfg, 1)
         cpu = {"value": sps, "unit": "steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"{done} full fractional step(s) of the workload, numpy FP64 oracle, {dt:.1f} s"}
+               "sample": f"{done} full fractional step(s) of the workload from its initial state, numpy FP64 "
+                         f"oracle, {dt:.1f} s"}
+        if first is not None:
+            diffs = [float(np.linalg.norm(g - tt.full(o)) / np.linalg.norm(tt.full(o))) for g, o in zip(first, ofirst)]
+            parity = {"gpu_vs_oracle_first_step": dict(zip("uvp", diffs)), "bound": STEP_PARITY_BOUND,
+                      "ok": bool(max(diffs) <= STEP_PARITY_BOUND)}
     if rank == 0:
         line = {"metric": METRIC, "value": job_throughput(world, step_ms * 1e-3), "unit": "steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering")}
                 | {"mom_solve": list(cfg["mom"]), "poisson_solve": list(cfg["poi"]), "fit_sweeps": cfg["fit_sweeps"],
-                   "l2": "256 MB buffer written between timed steps", "replicas": world,
+                   "state": f"wake_field seed {cfg['seed']}", "l2": "256 MB buffer written between timed steps",
+                   "replicas": world,
                    **({"gemm_mode": args.gemm_mode} if args.gemm_mode is not None else {}),
                    **({"cg_mode": args.cg_mode} if args.cg_mode is not None else {})},
                 "e2e": {"value": job_throughput(world, e2e_s), "unit": "steps/s", "h2d_bytes_per_step": h2d,
@@ -286,11 +348,16 @@ def run_ours(args, cfg):
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                             "kernel": "core contractions: k_gemm + k_contract_direct (FP64 pipe) + k_oz_gemm (digit-split FP64 on "
-                                       "the tensor cores), FP64-equivalent flops",
-                             "share_of_step": g["ms"] / nprof / step_ms if step_ms > 0 else None},
-                "kernel_classes_ms_per_step": {k: v["ms"] / nprof for k, v in prof.items() if not k.startswith("phase")},
-                "phase_ms_last_timed_step": phases,
+                             "kernel": "ALS local CG solves (k_cg_persistent on the FP64 pipe, k_cg_tc with digit-split "
+                                       "tensor-core contractions at full-bond sites), FP64-equivalent flops counted "
+                                       "on the device, over their summed CUDA-event time in one eager step",
+                             "peak_basis": "152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
+                             "share_of_step": cg["ms"] / eager_ms if eager_ms > 0 else None},
+                "kernel_classes_ms_eager_step": {k: v["ms"] for k, v in prof.items() if not k.startswith("phase")},
+                "kernel_classes_ms_by_phase": by_phase,
+                "phase_ms_last_timed_step": phases, "phase_ms_eager_step": eager_phases,
+                "solves": solves,
+                "fixed_error": {"solves_ok": solves_ok, "parity": parity, "drift_vs_fp64_pipe": drift},
                 "clocks": clk, "cpu_baseline": cpu,
                 "last_step": {"cd": info[0]["cd"], "cl": info[0]["cl"]}}
         print(json.dumps(line))
@@ -305,6 +372,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-checks", action="store_true", help="skip the C_D, C_L drift run on the FP64 pipe")
     ap.add_argument("--n", type=int, default=None, help="bits per direction (smaller test case)")
     ap.add_argument("--chi", type=int, default=None)
     ap.add_argument("--profile-one-step", action="store_true",

@@ -77,19 +77,47 @@ typedef struct {
 
 typedef struct {
   int max_bond;            /* largest bond of the result */
-  double norm;             /* ||result||_2 (device-computed; valid after qtt_ctx_sync) */
+  double norm;             /* ||result||_2 */
+  double discarded_norm;   /* sqrt(sum over cuts of the discarded sigma^2): the TT-SVD error bound
+                              (Sec. II, rounding), equal to ||exact - result|| for a canonical
+                              sweep.  From Gram eigenvalues it resolves only values above
+                              ~1e-8 ||exact|| (they square the singular values).  -1 for
+                              mps_hadamard_round, whose result is a variational fit. */
 } qtt_round_info;
 
-/* Options of the single-site ALS solver (Sec. II.A.4). */
+/* Options of the single-site ALS solver (Sec. II.A.4).  The paper leaves the stop open; the
+ * solver evaluates the true relative residual ||A x - b|| / ||b|| after every full sweep (left
+ * to right, then right to left) and stops
+ *   - when it is <= rel_tol                                   (QTT_SOLVE_CONVERGED),
+ *   - when a sweep after the first reduced it by less than the fraction stall
+ *                                                             (QTT_SOLVE_STALLED: at a fixed
+ *     bond the sweeps approach a stationary point on the rank-chi manifold whose residual the
+ *     truncation bounds from below; stall <= 0 disables this test; the first sweep is exempt
+ *     because sweeps minimise the energy, and from a poor start the residual may first rise),
+ *   - after max_sweeps sweeps                                 (QTT_SOLVE_MAX_SWEEPS).
+ * Each local CG solve of a sweep stops when ||r_loc|| <= cg_tol * res * ||b_loc||, res being the
+ * true relative residual before the sweep, or after cg_max_iter iterations.
+ * The residual is the un-truncated TT A x (+) (-b) evaluated entry by entry on the device
+ * (2^n values, n <= 30), so it carries only the rounding of each entry. */
 typedef struct {
-  int sweeps;              /* full sweeps (left-to-right + right-to-left) */
-  int cg_iters;            /* CG iteration budget per site */
-  double cg_tol;           /* CG stops early when ||r|| <= cg_tol ||b_local|| */
+  int max_sweeps;
+  double rel_tol;
+  int cg_max_iter;
+  double cg_tol;
+  double stall;
 } qtt_solve_opts;
 
+#define QTT_SOLVE_CONVERGED 0
+#define QTT_SOLVE_STALLED 1
+#define QTT_SOLVE_MAX_SWEEPS 2
+#define QTT_SOLVE_NONFINITE 3     /* the residual became NaN or Inf */
+#define QTT_SOLVE_TIMEOUT 4       /* a bounded grid barrier of a local CG solve ran out */
+
 typedef struct {
-  int cg_iters_total;      /* CG iterations spent (all sites, all sweeps) */
-  double rel_residual;     /* ||A x - b|| / ||b|| after the last sweep, or -1 if not computed */
+  int sweeps;              /* full sweeps done */
+  int cg_iters;            /* CG iterations spent (all sites, all sweeps) */
+  double rel_residual;     /* ||A x - b|| / ||b|| of the returned x */
+  int status;              /* QTT_SOLVE_* */
 } qtt_solve_info;
 
 /* ------------------------------------------------------------------------------ context */
@@ -123,6 +151,13 @@ int qtt_ctx_profile(qtt_ctx* ctx, int on, double* ms_out, double* flops_out, int
  * with momentum, unused, Poisson, projection -- row 5 = outside any phase; column k = kernel
  * class k), and launches_out[6] (kernel launches enqueued in each row).  Either may be NULL. */
 int qtt_ctx_profile_phases(qtt_ctx* ctx, double* ms_out, int64_t* launches_out);
+/* Limit (seconds, > 0) of every bounded device wait of this context: the grid barriers of the
+ * cooperative CG solves (default 2 s).  A wait that runs out makes its kernel leave at once;
+ * the solve then ends with QTT_SOLVE_TIMEOUT and the call returns QTT_ERR_TIMEOUT, with the
+ * context still usable.  Takes effect for work enqueued afterwards (a captured step keeps the
+ * limit it was captured with: set it before the first fractional_step or after
+ * qtt_case_use_graph).  Tests shorten it to exercise the timeout path without any fault. */
+int qtt_ctx_set_wait_limit(qtt_ctx* ctx, double seconds);
 /* How ALS local systems are solved (Sec. II.A.4).  Mode 2 runs each local CG solve as one
  * cooperative kernel on the FP64 pipe (one CTA per SM, grid barriers between its stages) where
  * the bonds allow it (bonds <= 128, operator bonds <= 16, d <= 4).  Mode 3 does the same but,
@@ -193,7 +228,7 @@ int mps_hadamard_round(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, qtt_tru
  * exists for callers that cannot allocate device memory when they need an overlap -- code
  * running inside another allocator's callback, loops that cannot afford a cudaMalloc that may
  * synchronise the device, or processes whose device memory is fully reserved by another pool).
- *   n, d       number of cores and physical size (1 <= d <= 4)
+ *   n, d       number of cores and physical size (1 <= n <= 64, 1 <= d <= 4)
  *   a_bonds, b_bonds   host arrays of n+1 bonds, each in [1, 128], first and last equal to 1
  *   a_cores, b_cores   device arrays: all cores concatenated, each (r_{k-1}, d, r_k) row-major,
  *                      no padding between cores (caller-owned, read only)
@@ -241,12 +276,15 @@ int qtt_check_recip(qtt_ctx* ctx, int n, const double* x, double* err2);
 /* <a, b> into *out_host (synchronous). */
 int mps_dot(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, double* out_host);
 
-/* Solve A x = b for SPD A by single-site ALS (Sec. II.A.4, Sec. III.C): x_inout is the warm
- * start and receives the solution (its bond profile is kept).  The residual is computed when
- * info != NULL (costs one extra contraction sweep); QTT_ERR_NOT_CONVERGED is returned when
- * tol > 0 and the relative residual stays above tol. */
+/* Solve A x = b for SPD A by single-site ALS (Sec. II.A.4, Sec. III.C) under the stop rule of
+ * qtt_solve_opts: x_inout is the warm start and receives the solution (its bond profile is
+ * kept).  Blocks the host until the solve has finished.  Returns QTT_OK when the residual met
+ * opts->rel_tol, QTT_ERR_NOT_CONVERGED when the solve stalled or ran out of sweeps (x_inout then
+ * holds the last iterate), QTT_ERR_TIMEOUT when a grid barrier ran out, QTT_ERR_NONFINITE when
+ * the residual became NaN or Inf; info (may be NULL) is filled in every one of these cases.
+ * n <= 30 (the residual is evaluated on 2^n entries). */
 int poisson_solve(qtt_ctx* ctx, const qtt_mpo* A, const qtt_mps* b, qtt_mps* x_inout,
-                  const qtt_solve_opts* opts, double tol, qtt_solve_info* info);
+                  const qtt_solve_opts* opts, qtt_solve_info* info);
 
 /* -------------------------------------------------------- cylinder case (Sec. III, IV) */
 
@@ -264,7 +302,8 @@ typedef struct {
 } qtt_case_params;
 
 typedef struct {
-  int cg_u, cg_v, cg_p;    /* CG iterations of the three solves */
+  qtt_solve_info u, v, p;  /* the two momentum solves and the Poisson solve of the step */
+  int finite;              /* 1 if the new u and v have finite norms */
   double cd, cl;           /* drag and lift coefficients after the step (eq:liftdrag) */
 } qtt_step_info;
 
@@ -283,8 +322,12 @@ int qtt_case_get_operator(qtt_case* c, int which, qtt_mpo** out);
 /* Boundary vectors for tests: which = 0 bcx_u, 1 bcz_u, 2 bcx_v, 3 bcz_v, 4 |J| bcLap_u,
  * 5 |J| bcLap_v, 6 bc_div (weighted), 7 |J|.  *out = NULL when the vector is identically zero. */
 int qtt_case_get_vector(qtt_case* c, int which, qtt_mps** out);
-/* Advance nsteps fractional steps (Sec. III.C); per_step (may be NULL) receives nsteps
- * records, valid after qtt_ctx_sync.  Forces are evaluated when with_forces != 0. */
+/* Advance nsteps fractional steps (Sec. III.C) and block the host until they have finished.
+ * per_step (may be NULL) receives nsteps records.  Forces are evaluated when with_forces != 0
+ * and per_step is given.  Returns QTT_ERR_TIMEOUT if a local CG barrier ran out, QTT_ERR_NONFINITE
+ * if a residual or a new velocity norm was NaN or Inf, QTT_ERR_NOT_CONVERGED if a solve used all
+ * of its sweeps without meeting its tolerance (a stall at the bond's floor is not an error),
+ * checked over all steps whether or not per_step is given. */
 int fractional_step(qtt_ctx* ctx, qtt_case* c, int nsteps, int with_forces,
                     qtt_step_info* per_step);
 /* Replay mode of fractional_step.  enable != 0 (the default): the first call captures one

@@ -104,133 +104,31 @@ __global__ void k_diag_core(const double* __restrict__ A, int r0, int d, int r1,
   }
 }
 
-// CG for the ALS local systems (Sec. II.A.4), spread over CG_BLOCKS blocks.  State lives on
-// the device so that the host never waits: rr is kept in two slots (iteration `it` reads
-// slot it & 1 and writes slot (it + 1) & 1) because blocks of one kernel are not ordered with
-// respect to each other.  Partial sums are reduced in a fixed order (deterministic results).
-constexpr int CG_BLOCKS = 32;
-constexpr int CG_THREADS = 256;
-
-struct CGState {
-  double rr[2];
-  double bb, tol2;
-  int active;
-  int count;
-  double part[2][CG_BLOCKS];   // per-block partial sums
-};
-
-__device__ double block_sum_d(double v, double* red) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += red[i];
-  __syncthreads();
-  return s;
-}
-
-__device__ __forceinline__ double sum_parts(const double* part) {
-  double s = 0.0;
-  for (int i = 0; i < CG_BLOCKS; ++i) s += part[i];
-  return s;
-}
-
-// r = b - Ax, p = r; partial r.r and b.b per block.
-__global__ void __launch_bounds__(CG_THREADS) k_cg_init1(int64_t n, const double* __restrict__ b,
-                                                         const double* __restrict__ Ax, double* __restrict__ r,
-                                                         double* __restrict__ p, CGState* st) {
-  __shared__ double red[32];
-  double rr = 0, bb = 0;
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
-    double re = b[e] - Ax[e];
-    r[e] = re;
-    p[e] = re;
-    rr += re * re;
-    bb += b[e] * b[e];
-  }
-  rr = block_sum_d(rr, red);
-  bb = block_sum_d(bb, red);
-  if (threadIdx.x == 0) {
-    st->part[0][blockIdx.x] = rr;
-    st->part[1][blockIdx.x] = bb;
-  }
-}
-
-__global__ void k_cg_init2(CGState* st, double tol2) {
+// *acc += sum of the discarded eigenvalues w[bk..nv) of a Gram rounding cut (sigma^2 each).
+__global__ void k_disc_add(const double* w, int nv, int bk, double* acc) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double rr = sum_parts(st->part[0]), bb = sum_parts(st->part[1]);
-  st->rr[0] = rr;
-  st->bb = bb;
-  st->tol2 = tol2;
-  st->active = (rr > tol2 * bb && rr > 0.0) ? 1 : 0;
-  st->count = 0;
+  double s = 0.0;
+  for (int i = bk; i < nv; ++i) s += fmax(w[i], 0.0);
+  *acc += s;
 }
 
-// partial p.Ap
-__global__ void __launch_bounds__(CG_THREADS) k_cg_pap(int64_t n, const double* __restrict__ p,
-                                                       const double* __restrict__ Ap, CGState* st) {
-  __shared__ double red[32];
-  if (!st->active) return;
-  double s = 0;
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
-    s += p[e] * Ap[e];
-  s = block_sum_d(s, red);
-  if (threadIdx.x == 0) st->part[0][blockIdx.x] = s;
-}
-
-// alpha = rr / pAp; x += alpha p; r -= alpha Ap; partial r.r
-__global__ void __launch_bounds__(CG_THREADS) k_cg_xr(int64_t n, int it, double* __restrict__ x, double* __restrict__ r,
-                                                      const double* __restrict__ p, const double* __restrict__ Ap,
-                                                      CGState* st) {
-  __shared__ double red[32];
-  if (!st->active) return;
-  const double pap = sum_parts(st->part[0]);
-  if (!(pap > 0.0)) {                    // every block computes the same pap and stops here
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->active = 0;
-    return;
-  }
-  const double alpha = st->rr[it & 1] / pap;
-  double rn = 0;
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
-    x[e] += alpha * p[e];
-    double re = r[e] - alpha * Ap[e];
-    r[e] = re;
-    rn += re * re;
-  }
-  rn = block_sum_d(rn, red);
-  if (threadIdx.x == 0) st->part[1][blockIdx.x] = rn;
-}
-
-// beta = rr' / rr; p = r + beta p; block 0 records rr', the count and the stopping test.
-__global__ void __launch_bounds__(CG_THREADS) k_cg_p(int64_t n, int it, const double* __restrict__ r,
-                                                     double* __restrict__ p, CGState* st) {
-  if (!st->active) return;
-  const double rn = sum_parts(st->part[1]);
-  const double beta = rn / st->rr[it & 1];
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
-    p[e] = r[e] + beta * p[e];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->rr[(it + 1) & 1] = rn;
-    st->count += 1;
-    st->active = (rn > st->tol2 * st->bb && rn > 0.0) ? 1 : 0;
-  }
-}
-
-__global__ void k_cg_accumulate(const CGState* st, int* total) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *total += st->count;
+__global__ void k_add_value(double* acc, double v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *acc += v;
 }
 
 __global__ void k_sqrt(const double* in, double* out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *out = sqrt(fmax(*in, 0.0));
 }
 
-__global__ void k_set_int(int* p, int v) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
-}
-
 }  // namespace
+
+// Discarded weight of one rounding cut, added to the context's accumulator when a caller asked
+// for it (qtt_round_info.discarded_norm).
+static void add_discarded(Ctx& c, const double* w_dev, int nv, int bk) {
+  if (!c.disc_acc || bk >= nv) return;
+  k_disc_add<<<1, 1, 0, c.stream>>>(w_dev, nv, bk, c.disc_acc);
+  after_launch(c, "disc_add");
+}
 
 void sqrt_dev(Ctx& c, const double* in, double* out) {
   k_sqrt<<<1, 1, 0, c.stream>>>(in, out);
@@ -270,18 +168,25 @@ qtt_mpo* diag_mpo(Ctx& c, const qtt_mps* a) {
 
 // y = M x without rounding: B[k]((a w), s', (b v)) = sum_s M[k](w, s', s, v) A[k](a, s, b)
 // (Sec. II.A.2; fused bond index (x-bond slow, MPO-bond fast)).
-qtt_mps* mpo_mps_exact(Ctx& c, const qtt_mpo* M, const qtt_mps* x) {
-  QTT_CHECK_ARG(M->n == x->n && M->d == x->d, "mpo-mps: shape mismatch");
+void mpo_mps_exact_into(Ctx& c, const qtt_mpo* M, const qtt_mps* x, qtt_mps* y) {
+  QTT_CHECK_ARG(M->n == x->n && M->d == x->d && y->n == x->n && y->d == x->d, "mpo-mps: shape mismatch");
   const int n = x->n, d = x->d;
-  std::vector<int> b(n + 1);
-  for (int k = 0; k <= n; ++k) b[k] = x->bonds[k] * M->bonds[k];
-  qtt_mps* y = new_mps(&c, n, d, b);
+  for (int k = 0; k <= n; ++k) QTT_CHECK_ARG(y->bonds[k] == x->bonds[k] * M->bonds[k], "mpo-mps: output bonds");
   for (int k = 0; k < n; ++k) {
     int a0 = x->bonds[k], a1 = x->bonds[k + 1], w0 = M->bonds[k], w1 = M->bonds[k + 1];
     einsum(c, "wtsv,asb->awtbv", 1.0, tv(M->core(k), {w0, d, d, w1}), tv(x->core(k), {a0, d, a1}), 0.0,
            tv(y->core(k), {a0, w0, d, a1, w1}));
   }
-  return y;
+}
+
+qtt_mps* mpo_mps_exact(Ctx& c, const qtt_mpo* M, const qtt_mps* x) {
+  QTT_CHECK_ARG(M->n == x->n && M->d == x->d, "mpo-mps: shape mismatch");
+  const int n = x->n, d = x->d;
+  std::vector<int> b(n + 1);
+  for (int k = 0; k <= n; ++k) b[k] = x->bonds[k] * M->bonds[k];
+  std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> y(new_mps(&c, n, d, b), free_mps);
+  mpo_mps_exact_into(c, M, x, y.get());
+  return y.release();
 }
 
 qtt_mpo* mpo_mpo_exact(Ctx& c, const qtt_mpo* A, const qtt_mpo* B) {
@@ -399,6 +304,12 @@ qtt_mps* round_svd(Ctx& c, const qtt_mps* x_in, int chi, double eps) {
       if (s > 0.0) ++nz;
     int bk = kept(sig, chi, eps, std::min(m[k], cols));
     bk = std::max(1, std::min(bk, std::max(nz, 1)));
+    if (c.disc_acc) {
+      double disc = 0.0;
+      for (int i = bk; i < nn; ++i) disc += sig[i] * sig[i];
+      k_add_value<<<1, 1, 0, c.stream>>>(c.disc_acc, disc);
+      after_launch(c, "add_value");
+    }
     DBuf newcore(&c, size_t(bk) * cols), carry(&c, size_t(r0) * bk);
     // right singular vectors (cols x bk) -> new core = their transpose (bk x cols);
     // carry = left vectors * S (r0 x bk)
@@ -504,6 +415,7 @@ qtt_mps* round_gram(Ctx& c, const qtt_mps* y, int chi, double eps) {
     einsum(c, "Asc,AtD->sctD", 1.0, tv(T.p, {a0, d, c1}), tv(Z.p, {a0, d, c1}), 0.0, tv(rho.p, {d, c1, d, c1}));
     eigh(c, nv, rho.p, w.p, V.p, std::min(std::min(chi, m[k]), nv));
     int bk = choose_rank(c, w.p, nv, chi, eps, std::min(m[k], nv));
+    add_discarded(c, w.p, nv, bk);
     out[k].reset(&c, size_t(bk) * nv);
     top_vectors_as_core(c, V.p, nv, bk, out[k].p);
     // P_k = Z V[:, :bk]  (a0 x bk)
@@ -584,6 +496,7 @@ qtt_mps* apply_round_gram(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, d
            tv(rho.p, {d, c1, d, c1}));
     eigh(c, nv, rho.p, wv.p, V.p, std::min(std::min(chi, mstruct[k]), nv));
     int bk = choose_rank(c, wv.p, nv, chi, eps, std::min(mstruct[k], nv));
+    add_discarded(c, wv.p, nv, bk);
     out[k].reset(&c, size_t(bk) * nv);
     top_vectors_as_core(c, V.p, nv, bk, out[k].p);
     DBuf Pn(&c, size_t(w0) * a0 * bk);
@@ -647,14 +560,14 @@ int Term::rbond(int k) const {
 }
 
 // Environment shapes: VEC (c, a); HAD (c, a, b); MPO (c, w, a).
-static size_t env_size(const Term& t, int cb, int k) {
+size_t env_size(const Term& t, int cb, int k) {
   if (t.kind == Term::VEC) return size_t(cb) * t.a->bonds[k];
   if (t.kind == Term::HAD) return size_t(cb) * t.a->bonds[k] * t.b->bonds[k];
   return size_t(cb) * t.M->bonds[k] * t.a->bonds[k];
 }
 
 // L_{k+1} from L_k and the new (left-orthonormal) core C of the fitted tensor at site k.
-static void env_left(Ctx& c, const Term& t, const double* L, const double* C, int c0, int c1, int k, double* Lout) {
+void env_left(Ctx& c, const Term& t, const double* L, const double* C, int c0, int c1, int k, double* Lout) {
   const int d = t.a->d;
   if (t.kind == Term::VEC) {
     int a0 = t.a->bonds[k], a1 = t.a->bonds[k + 1];
@@ -687,7 +600,7 @@ static void env_left(Ctx& c, const Term& t, const double* L, const double* C, in
 }
 
 // R_k from R_{k+1} and the new (right-orthonormal) core C at site k.
-static void env_right(Ctx& c, const Term& t, const double* R, const double* C, int c0, int c1, int k, double* Rout) {
+void env_right(Ctx& c, const Term& t, const double* R, const double* C, int c0, int c1, int k, double* Rout) {
   const int d = t.a->d;
   if (t.kind == Term::VEC) {
     int a0 = t.a->bonds[k], a1 = t.a->bonds[k + 1];
@@ -721,8 +634,8 @@ static void env_right(Ctx& c, const Term& t, const double* R, const double* C, i
 
 // out (c0, d, c1) (+)= coef * projection of the term onto the frames L (site k) and R (site k+1).
 // `vec` (if non-null) replaces the term's own core at site k (used by the ALS matvec).
-static void local_target(Ctx& c, const Term& t, const double* L, const double* R, int c0, int c1, int k, double coef,
-                         double beta, double* out, const double* vec = nullptr) {
+void local_target(Ctx& c, const Term& t, const double* L, const double* R, int c0, int c1, int k, double coef,
+                  double beta, double* out, const double* vec) {
   const int d = t.a->d;
   if (t.kind == Term::VEC) {
     int a0 = t.a->bonds[k], a1 = t.a->bonds[k + 1];
@@ -876,138 +789,6 @@ qtt_mps* zipup_hadamard(Ctx& c, const qtt_mps* a, const qtt_mps* b, int chi) {
   return z;
 }
 
-// ------------------------------------------------------------------ ALS (Sec. II.A.4)
-
-int als(Ctx& c, const qtt_mpo* A, const std::vector<Term>& rhs, qtt_mps* x, int sweeps, int cg_iters, double cg_tol,
-        bool canonical, int* cg_total_dev) {
-  QTT_CHECK_ARG(A->n == x->n && A->d == x->d, "als: operator shape");
-  for (const Term& t : rhs) QTT_CHECK_ARG(t.a->n == x->n && t.a->d == x->d, "als: rhs shape");
-  const int n = x->n, d = x->d;
-  if (!canonical) right_orthonormalize(c, x);
-  // operator environments: term MPO(A, x) with bra = x
-  Term opT;
-  opT.kind = Term::MPO;
-  opT.coef = 1.0;
-  opT.M = A;
-  opT.a = x;
-  std::vector<DBuf> LA(n + 1), RA(n + 1);
-  LA[0].reset(&c, 1);
-  fill(c, LA[0].p, 1, 1.0);
-  RA[n].reset(&c, 1);
-  fill(c, RA[n].p, 1, 1.0);
-  for (int k = n - 1; k >= 1; --k) {
-    RA[k].reset(&c, env_size(opT, x->bonds[k], k));
-    env_right(c, opT, RA[k + 1].p, x->core(k), x->bonds[k], x->bonds[k + 1], k, RA[k].p);
-  }
-  Envs E;
-  init_envs(c, rhs, x, E);
-  DBuf stbuf(&c, (sizeof(CGState) + 7) / 8);
-  CGState* st = reinterpret_cast<CGState*>(stbuf.p);
-  DBuf tot(&c, 1);
-  k_set_int<<<1, 1, 0, c.stream>>>(reinterpret_cast<int*>(tot.p), 0);
-  after_launch(c, "set_int");
-  const int* active = &st->active;
-
-  auto solve_site = [&](int k) {
-    int r0 = x->bonds[k], r1 = x->bonds[k + 1];
-    int64_t nel = int64_t(r0) * d * r1;
-    const int w0 = A->bonds[k], w1 = A->bonds[k + 1];
-    // mode 0: tensor-core contractions at full-bond sites (r0 r1 >= 4096, where they measured
-    // faster: ~690 vs ~800 us per Poisson solve at bonds 64), FP64 elsewhere; mode 2: FP64 only;
-    // mode 3: tensor cores wherever the kernel fits
-    const int mode = c.root->cg_mode;
-    const bool tc = (mode == 3 || (mode == 0 && int64_t(r0) * r1 >= 4096)) && cg_tc_fits(c, r0, r1, w0, w1, d);
-    if (tc || (mode != 1 && cg_persistent_fits(c, r0, r1, w0, w1, d))) {
-      DBuf bvec(&c, nel), xk(&c, nel);
-      local_sum(c, rhs, E, x, k, bvec.p);
-      copy(c, xk.p, x->core(k), nel);
-      if (tc)
-        cg_tc(c, LA[k].p, A->core(k), RA[k + 1].p, bvec.p, xk.p, r0, r1, w0, w1, d, cg_iters, cg_tol,
-              reinterpret_cast<int*>(tot.p));
-      else
-        cg_persistent(c, LA[k].p, A->core(k), RA[k + 1].p, bvec.p, xk.p, r0, r1, w0, w1, d, cg_iters, cg_tol,
-                      reinterpret_cast<int*>(tot.p));
-      return xk;
-    }
-    DBuf bvec(&c, nel), Ax(&c, nel), r(&c, nel), p(&c, nel), Ap(&c, nel), xk(&c, nel);
-    local_sum(c, rhs, E, x, k, bvec.p);
-    copy(c, xk.p, x->core(k), nel);
-    local_target(c, opT, LA[k].p, RA[k + 1].p, r0, r1, k, 1.0, 0.0, Ax.p, xk.p);
-    k_cg_init1<<<CG_BLOCKS, CG_THREADS, 0, c.stream>>>(nel, bvec.p, Ax.p, r.p, p.p, st);
-    after_launch(c, "cg_init1");
-    k_cg_init2<<<1, 32, 0, c.stream>>>(st, cg_tol * cg_tol);
-    after_launch(c, "cg_init2");
-    for (int it = 0; it < cg_iters; ++it) {
-      c.guard = active;
-      local_target(c, opT, LA[k].p, RA[k + 1].p, r0, r1, k, 1.0, 0.0, Ap.p, p.p);
-      c.guard = nullptr;
-      ProfScope ps(c, KC_CG);
-      k_cg_pap<<<CG_BLOCKS, CG_THREADS, 0, c.stream>>>(nel, p.p, Ap.p, st);
-      after_launch(c, "cg_pap");
-      k_cg_xr<<<CG_BLOCKS, CG_THREADS, 0, c.stream>>>(nel, it, xk.p, r.p, p.p, Ap.p, st);
-      after_launch(c, "cg_xr");
-      k_cg_p<<<CG_BLOCKS, CG_THREADS, 0, c.stream>>>(nel, it, r.p, p.p, st);
-      after_launch(c, "cg_p");
-    }
-    k_cg_accumulate<<<1, 1, 0, c.stream>>>(st, reinterpret_cast<int*>(tot.p));
-    after_launch(c, "cg_accumulate");
-    return xk;
-  };
-
-  for (int sw = 0; sw < sweeps; ++sw) {
-    for (int k = 0; k < n; ++k) {
-      int r0 = x->bonds[k], r1 = x->bonds[k + 1];
-      DBuf xk = solve_site(k);
-      if (k < n - 1) {
-        DBuf Rm(&c, size_t(r1) * r1);
-        qr(c, 1, r0 * d, r1, 0, xk.p, 0, x->core(k), 0, Rm.p, 0);
-        int r2 = x->bonds[k + 2];
-        DBuf nxt(&c, size_t(r1) * d * r2);
-        einsum(c, "ab,bsc->asc", 1.0, tv(Rm.p, {r1, r1}), tv(x->core(k + 1), {r1, d, r2}), 0.0, tv(nxt.p, {r1, d, r2}));
-        copy(c, x->core(k + 1), nxt.p, int64_t(r1) * d * r2);
-        LA[k + 1].reset(&c, env_size(opT, r1, k + 1));
-        env_left(c, opT, LA[k].p, x->core(k), r0, r1, k, LA[k + 1].p);
-        for (size_t t = 0; t < rhs.size(); ++t) {
-          E.L[t][k + 1].reset(&c, env_size(rhs[t], r1, k + 1));
-          env_left(c, rhs[t], E.L[t][k].p, x->core(k), r0, r1, k, E.L[t][k + 1].p);
-        }
-      } else {
-        copy(c, x->core(k), xk.p, int64_t(r0) * d * r1);
-      }
-    }
-    for (int k = n - 1; k >= 0; --k) {
-      int r0 = x->bonds[k], r1 = x->bonds[k + 1];
-      DBuf xk = solve_site(k);
-      if (k > 0) {
-        DBuf Rm(&c, size_t(r0) * r0);
-        qr(c, 1, d * r1, r0, 1, xk.p, 0, x->core(k), 0, Rm.p, 0);
-        int p0 = x->bonds[k - 1];
-        DBuf prev(&c, size_t(p0) * d * r0);
-        einsum(c, "asb,cb->asc", 1.0, tv(x->core(k - 1), {p0, d, r0}), tv(Rm.p, {r0, r0}), 0.0,
-               tv(prev.p, {p0, d, r0}));
-        copy(c, x->core(k - 1), prev.p, int64_t(p0) * d * r0);
-        RA[k].reset(&c, env_size(opT, r0, k));
-        env_right(c, opT, RA[k + 1].p, x->core(k), r0, r1, k, RA[k].p);
-        for (size_t t = 0; t < rhs.size(); ++t) {
-          E.R[t][k].reset(&c, env_size(rhs[t], r0, k));
-          env_right(c, rhs[t], E.R[t][k + 1].p, x->core(k), r0, r1, k, E.R[t][k].p);
-        }
-      } else {
-        copy(c, x->core(k), xk.p, int64_t(r0) * d * r1);
-      }
-    }
-  }
-  if (cg_total_dev) {
-    QTT_CUDA(cudaMemcpyAsync(cg_total_dev, tot.p, sizeof(int), cudaMemcpyDeviceToDevice, c.stream));
-    return 0;
-  }
-  int h = 0;
-  QTT_CUDA(cudaMemcpyAsync(&h, tot.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-  QTT_CUDA(cudaStreamSynchronize(c.stream));
-  if (h < 0) throw Error(QTT_ERR_CUDA, "als: a CG grid barrier timed out");
-  return h;
-}
-
 // ------------------------------------------------------------------ inner products, norms
 
 void dot_dev(Ctx& c, const qtt_mps* a, const qtt_mps* b, double* out_dev) {
@@ -1089,6 +870,7 @@ qtt_mps* encode_dense(Ctx& c, const double* dense_dev, int n, int d, int chi, do
     int strct = int(std::min<int64_t>(rows, nv));
     eigh(c, nv, rho.p, w.p, V.p, std::min(chi, strct));
     int bk = choose_rank(c, w.p, nv, chi, eps, strct);
+    add_discarded(c, w.p, nv, bk);
     out[k].reset(&c, size_t(bk) * nv);
     top_vectors_as_core(c, V.p, nv, bk, out[k].p);
     DBuf nxt(&c, size_t(rows) * bk);

@@ -49,6 +49,41 @@ void check_trunc(const qtt_trunc& t) {
   if (!(t.rel_tol >= 0.0) || !std::isfinite(t.rel_tol)) throw Error(QTT_ERR_ARG, "trunc: rel_tol must be >= 0");
 }
 
+void check_solve_opts(const qtt_solve_opts& o, const char* what) {
+  if (!(o.max_sweeps >= 0 && o.cg_max_iter >= 0 && o.rel_tol >= 0.0 && o.cg_tol >= 0.0 && std::isfinite(o.rel_tol) &&
+        std::isfinite(o.cg_tol) && std::isfinite(o.stall) && o.stall < 1.0))
+    throw Error(QTT_ERR_ARG, std::string(what) +
+                                 ": solve options need max_sweeps, cg_max_iter >= 0, rel_tol, cg_tol >= 0, stall < 1");
+}
+
+void fill_solve_info(const AlsCtl& h, qtt_solve_info* info) {
+  info->sweeps = h.sweeps;
+  info->cg_iters = h.cg_total < 0 ? -1 : h.cg_total;
+  info->rel_residual = h.res;
+  info->status = h.status;
+}
+
+// QTT_OK for a solve that met its tolerance or stopped at its bond's floor; the error codes of
+// include/qtt.h otherwise.  `floor_ok` = false makes a stall an error too (poisson_solve).
+int solve_status_code(int status, bool floor_ok = false) {
+  switch (status) {
+    case QTT_SOLVE_CONVERGED: return QTT_OK;
+    case QTT_SOLVE_STALLED: return floor_ok ? QTT_OK : QTT_ERR_NOT_CONVERGED;
+    case QTT_SOLVE_MAX_SWEEPS: return QTT_ERR_NOT_CONVERGED;
+    case QTT_SOLVE_NONFINITE: return QTT_ERR_NONFINITE;
+    case QTT_SOLVE_TIMEOUT: return QTT_ERR_TIMEOUT;
+    default: return QTT_ERR_CUDA;
+  }
+}
+
+std::string solve_status_text(const AlsCtl& h) {
+  static const char* names[] = {"converged", "stalled above the tolerance", "out of sweeps", "non-finite residual",
+                                "a CG grid barrier timed out"};
+  const char* s = (h.status >= 0 && h.status <= 4) ? names[h.status] : "did not finish";
+  return std::string(s) + " after " + std::to_string(h.sweeps) + " sweeps, relative residual " +
+         std::to_string(h.res);
+}
+
 cudaMemcpyKind kind_in(int kind) {
   if (kind == QTT_HOST) return cudaMemcpyHostToDevice;
   if (kind == QTT_DEVICE) return cudaMemcpyDeviceToDevice;
@@ -61,17 +96,38 @@ cudaMemcpyKind kind_out(int kind) {
   throw Error(QTT_ERR_ARG, "pointer kind must be QTT_HOST or QTT_DEVICE");
 }
 
-void fill_info(Ctx& c, const qtt_mps* y, qtt_round_info* info) {
+// Collects the discarded weight of the roundings of one call when the caller asked for it.
+struct DiscScope {
+  Ctx& c;
+  DBuf acc;
+  DiscScope(Ctx& ctx, bool on) : c(ctx) {
+    if (on) {
+      acc.reset(&c, 1);
+      fill(c, acc.p, 1, 0.0);
+      c.disc_acc = acc.p;
+    }
+  }
+  ~DiscScope() { c.disc_acc = nullptr; }
+  DiscScope(const DiscScope&) = delete;
+  DiscScope& operator=(const DiscScope&) = delete;
+};
+
+// max bond, norm (right-canonical result: the norm of its first core) and discarded norm
+// (sqrt of the accumulated weight; -1 when the result is a variational fit).
+void fill_info(Ctx& c, const qtt_mps* y, qtt_round_info* info, const DiscScope* disc) {
   if (!info) return;
   int mb = 1;
   for (int b : y->bonds) mb = std::max(mb, b);
   info->max_bond = mb;
   DBuf d(&c, 1);
   dot_dev(c, y, y, d.p);
-  double v = 0.0;
-  QTT_CUDA(cudaMemcpyAsync(&v, d.p, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  double v[2] = {0.0, -1.0};
+  QTT_CUDA(cudaMemcpyAsync(&v[0], d.p, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  if (disc && disc->acc.p)
+    QTT_CUDA(cudaMemcpyAsync(&v[1], disc->acc.p, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   QTT_CUDA(cudaStreamSynchronize(c.stream));
-  info->norm = std::sqrt(std::max(v, 0.0));
+  info->norm = std::sqrt(std::max(v[0], 0.0));
+  info->discarded_norm = v[1] >= 0.0 ? std::sqrt(v[1]) : -1.0;
 }
 
 __global__ void k_reorder(const double* __restrict__ src, double* __restrict__ dst, int ne, int nx, int ordering,
@@ -142,6 +198,8 @@ void qtt_ctx_destroy(qtt_ctx* ctx) {
       cudaEventDestroy(pr.e1);
     }
   free_tile_counters(*c);
+  if (c->prof.dev_flops) cudaFree(c->prof.dev_flops);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c->pool;
   delete c;
 }
@@ -172,6 +230,15 @@ int qtt_ctx_profile(qtt_ctx* ctx, int on, double* ms_out, double* flops_out, int
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   QTT_CUDA(cudaStreamSynchronize(c.stream));
   Profiler& P = c.prof;
+  if (P.dev_flops) {
+    double f = 0.0;
+    QTT_CUDA(cudaMemcpy(&f, P.dev_flops, sizeof(double), cudaMemcpyDeviceToHost));
+    QTT_CUDA(cudaMemset(P.dev_flops, 0, sizeof(double)));
+    P.flops[KC_CG] += f;
+  } else if (on) {
+    QTT_CUDA(cudaMalloc(&P.dev_flops, sizeof(double)));
+    QTT_CUDA(cudaMemset(P.dev_flops, 0, sizeof(double)));
+  }
   for (auto& row : P.phase_ms)
     for (double& v : row) v = 0.0;
   for (int k = 0; k < KC_N; ++k) {
@@ -355,8 +422,9 @@ int qtt_encode(qtt_ctx* ctx, const double* dense, int kind, int n, int d, qtt_tr
   for (int i = 0; i < n; ++i) N *= d;
   DBuf buf(&c, size_t(N));
   QTT_CUDA(cudaMemcpyAsync(buf.p, dense, N * sizeof(double), kind_in(kind), c.stream));
+  DiscScope disc(c, info != nullptr);
   qtt_mps* y = encode_dense(c, buf.p, n, d, tr.chi_max, tr.rel_tol);
-  fill_info(c, y, info);
+  fill_info(c, y, info, &disc);
   *out = y;
   API_END
 }
@@ -404,8 +472,9 @@ int qtt_round(qtt_ctx* ctx, const qtt_mps* x, qtt_trunc tr, qtt_mps** out, qtt_r
   check_mps(x, "round");
   check_trunc(tr);
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  DiscScope disc(c, info != nullptr);
   qtt_mps* y = round_any(c, x, tr.chi_max, tr.rel_tol);
-  fill_info(c, y, info);
+  fill_info(c, y, info, &disc);
   *out = y;
   API_END
 }
@@ -421,8 +490,9 @@ int mps_axpby_round(qtt_ctx* ctx, double alpha, const qtt_mps* x, double beta, c
   check_trunc(tr);
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> s(direct_sum(c, alpha, x, beta, y), free_mps);
+  DiscScope disc(c, info != nullptr);
   qtt_mps* z = round_any(c, s.get(), tr.chi_max, tr.rel_tol);
-  fill_info(c, z, info);
+  fill_info(c, z, info, &disc);
   *out = z;
   API_END
 }
@@ -436,13 +506,14 @@ int mpo_apply_round(qtt_ctx* ctx, const qtt_mpo* M, const qtt_mps* x, qtt_trunc 
   check_trunc(tr);
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   qtt_mps* y;
+  DiscScope disc(c, info != nullptr);
   if (tr.rel_tol > 0.0) {
     std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> e(mpo_mps_exact(c, M, x), free_mps);
     y = round_any(c, e.get(), tr.chi_max, tr.rel_tol);
   } else {
     y = apply_round_gram(c, M, x, tr.chi_max, 0.0);
   }
-  fill_info(c, y, info);
+  fill_info(c, y, info, &disc);
   *out = y;
   API_END
 }
@@ -469,7 +540,7 @@ int mps_hadamard_round(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, qtt_tru
   }
   std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> guard(y, free_mps);
   fit(c, {Term::had(1.0, a, b)}, y, sweeps, canonical);
-  fill_info(c, y, info);
+  fill_info(c, y, info, nullptr);
   *out = guard.release();
   API_END
 }
@@ -570,38 +641,29 @@ int mps_dot(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, double* out_host) 
 }
 
 int poisson_solve(qtt_ctx* ctx, const qtt_mpo* A, const qtt_mps* b, qtt_mps* x_inout, const qtt_solve_opts* opts,
-                  double tol, qtt_solve_info* info) {
+                  qtt_solve_info* info) {
   API_BEGIN
   QTT_CHECK_ARG(ctx && A && opts, "poisson_solve: null argument");
   check_mps(b, "poisson_solve b");
   check_mps(x_inout, "poisson_solve x");
   QTT_CHECK_ARG(A->n == b->n && b->n == x_inout->n && A->d == b->d && b->d == x_inout->d, "poisson_solve: shapes");
-  QTT_CHECK_ARG(opts->sweeps >= 0 && opts->cg_iters >= 0 && opts->cg_tol >= 0.0, "poisson_solve: options");
+  check_solve_opts(*opts, "poisson_solve");
   for (int k = 1; k < x_inout->n; ++k)
     QTT_CHECK_ARG(x_inout->bonds[k] <= x_inout->d * x_inout->bonds[k + 1] &&
                       x_inout->bonds[k] <= x_inout->d * x_inout->bonds[k - 1],
                   "poisson_solve: x bonds must satisfy r_k <= d r_{k+-1}");
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
-  int cg = als(c, A, {Term::vec(1.0, b)}, x_inout, opts->sweeps, opts->cg_iters, opts->cg_tol, false, nullptr);
-  double rel = -1.0;
-  if (info || tol > 0.0) {
-    std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> y(mpo_mps_exact(c, A, x_inout), free_mps);
-    std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> r(direct_sum(c, 1.0, y.get(), -1.0, b), free_mps);
-    DBuf d(&c, 2);
-    norm_dev(c, r.get(), d.p);
-    norm_dev(c, b, d.p + 1);
-    double h[2];
-    QTT_CUDA(cudaMemcpyAsync(h, d.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-    QTT_CUDA(cudaStreamSynchronize(c.stream));
-    rel = h[1] > 0 ? h[0] / h[1] : h[0];
-  }
-  if (info) {
-    info->cg_iters_total = cg;
-    info->rel_residual = rel;
-  }
-  if (tol > 0.0 && !(rel <= tol)) {
-    set_last_error("poisson_solve: relative residual " + std::to_string(rel) + " above tolerance");
-    return QTT_ERR_NOT_CONVERGED;
+  DBuf ctl(&c, kAlsCtlDoubles);
+  AlsCtl* cp = reinterpret_cast<AlsCtl*>(ctl.p);
+  als(c, A, {Term::vec(1.0, b)}, x_inout, *opts, false, cp);
+  AlsCtl h;
+  QTT_CUDA(cudaMemcpyAsync(&h, cp, sizeof(AlsCtl), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  if (info) fill_solve_info(h, info);
+  const int rc = solve_status_code(h.status);
+  if (rc != QTT_OK) {
+    set_last_error("poisson_solve: " + solve_status_text(h));
+    return rc;
   }
   API_END
 }
@@ -713,24 +775,53 @@ int fractional_step(qtt_ctx* ctx, qtt_case* h, int nsteps, int with_forces, qtt_
   Case& cs = *h->cs;
   QTT_CHECK_ARG(cs.u && cs.v && cs.p, "fractional_step: state not set");
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
-  DBuf rec(&c, size_t(std::max(nsteps, 1)) * 4);
-  fill(c, rec.p, int64_t(std::max(nsteps, 1)) * 4, 0.0);
-  run_steps(c, cs, nsteps, with_forces && per_step, per_step ? rec.p : nullptr);
-  if (per_step && nsteps > 0) {
-    std::vector<double> hrec(size_t(nsteps) * 4);
-    QTT_CUDA(cudaMemcpyAsync(hrec.data(), rec.p, hrec.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-    QTT_CUDA(cudaStreamSynchronize(c.stream));
-    for (int s = 0; s < nsteps; ++s) {
-      int cg3[4];
-      std::memcpy(cg3, &hrec[4 * s], 2 * sizeof(double));
-      per_step[s].cg_u = cg3[0];
-      per_step[s].cg_v = cg3[1];
-      per_step[s].cg_p = cg3[2];
-      if (cg3[0] < 0 || cg3[1] < 0 || cg3[2] < 0)
-        throw Error(QTT_ERR_CUDA, "fractional_step: a CG grid barrier timed out (step " + std::to_string(s) + ")");
-      per_step[s].cd = with_forces ? hrec[4 * s + 2] : 0.0;
-      per_step[s].cl = with_forces ? hrec[4 * s + 3] : 0.0;
+  if (nsteps == 0) {
+    set_last_error("");
+    return QTT_OK;
+  }
+  const bool forces = with_forces && per_step;
+  DBuf rec(&c, size_t(nsteps) * kStepRecDoubles);
+  fill(c, rec.p, int64_t(nsteps) * kStepRecDoubles, 0.0);
+  run_steps(c, cs, nsteps, forces, rec.p);
+  std::vector<double> hrec(size_t(nsteps) * kStepRecDoubles);
+  QTT_CUDA(cudaMemcpyAsync(hrec.data(), rec.p, hrec.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  int rc = QTT_OK;
+  std::string msg;
+  for (int s = 0; s < nsteps; ++s) {
+    const double* r = &hrec[size_t(s) * kStepRecDoubles];
+    AlsCtl h[3];
+    std::memcpy(h, r, sizeof(h));
+    const int finite = r[kStepRecFinite] != 0.0;
+    if (per_step) {
+      fill_solve_info(h[0], &per_step[s].u);
+      fill_solve_info(h[1], &per_step[s].v);
+      fill_solve_info(h[2], &per_step[s].p);
+      per_step[s].finite = finite;
+      per_step[s].cd = forces ? r[kStepRecForces] : 0.0;
+      per_step[s].cl = forces ? r[kStepRecForces + 1] : 0.0;
     }
+    if (cs.use_graph) c.root->launches += cs.graph_launches + int64_t(h[0].sweeps) * cs.body_launches[0] +
+                                          int64_t(h[1].sweeps) * cs.body_launches[1] +
+                                          int64_t(h[2].sweeps) * cs.body_launches[2];
+    // the most severe outcome over all steps: timeout, non-finite, out of sweeps
+    for (int i = 0; i < 3; ++i) {
+      const int e = solve_status_code(h[i].status, true);
+      const char* which[3] = {"u momentum", "v momentum", "Poisson"};
+      if (e != QTT_OK && (rc == QTT_OK || e == QTT_ERR_TIMEOUT || (e == QTT_ERR_NONFINITE && rc != QTT_ERR_TIMEOUT))) {
+        rc = e;
+        msg = std::string("fractional_step: ") + which[i] + " solve of step " + std::to_string(s) + ": " +
+              solve_status_text(h[i]);
+      }
+    }
+    if (!finite && rc != QTT_ERR_TIMEOUT) {
+      rc = QTT_ERR_NONFINITE;
+      msg = "fractional_step: the new velocity of step " + std::to_string(s) + " is not finite";
+    }
+  }
+  if (rc != QTT_OK) {
+    set_last_error(msg);
+    return rc;
   }
   API_END
 }
@@ -746,6 +837,15 @@ int qtt_case_phase_ms(qtt_case* h, double* ms4) {
     QTT_CUDA(cudaEventElapsedTime(&t, cs.ph_ev[i], cs.ph_ev[i + 1]));
     ms4[i] = t;
   }
+  API_END
+}
+
+int qtt_ctx_set_wait_limit(qtt_ctx* ctx, double seconds) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx, "ctx is null");
+  QTT_CHECK_ARG(seconds > 0.0 && seconds <= 3600.0, "wait limit must be in (0, 3600] seconds");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  c.wait_ns = static_cast<unsigned long long>(std::max(1.0, seconds * 1e9));
   API_END
 }
 

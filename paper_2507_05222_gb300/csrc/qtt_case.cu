@@ -520,7 +520,20 @@ __global__ void __launch_bounds__(1024) k_forces(int Nx, const double* __restric
   }
 }
 
+__global__ void k_check_finite(const double* __restrict__ x, int64_t n, double* flag) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    if (!isfinite(x[e])) *flag = 0.0;
+}
+
 }  // namespace
+
+// flag = 0 if any of x[0..n) is NaN or Inf (every writer writes 0, so the race is benign).
+void check_finite(Ctx& c, const double* x, int64_t n, double* flag) {
+  const int threads = 256;
+  const int blocks = int(std::min<int64_t>((n + threads - 1) / threads, 4 * int64_t(c.num_sms)));
+  k_check_finite<<<std::max(blocks, 1), threads, 0, c.stream>>>(x, n, flag);
+  after_launch(c, "check_finite");
+}
 
 // Row I of a 2-D field (App. C): the eta-bit cores are sliced at the bits of I, the xi-bit
 // cores kept; the result is decoded to the dense row (length 2^n_xi).
@@ -569,7 +582,8 @@ void case_forces(Ctx& c, Case& cs, double* out_dev) {
 // right-hand side and momentum solve of each velocity component (2 workers), the two
 // projection fits (2 workers).  The Poisson solve couples u* and v* and runs on the caller's
 // stream.  Results that cross streams are allocated before the fork.
-void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
+void step(Ctx& c, Case& cs, double* rec, bool with_forces) {
+  AlsCtl* ctl = reinterpret_cast<AlsCtl*>(rec);
   const qtt_case_params& P = cs.P;
   const int chi = P.chi;
   const double dt = P.dt;
@@ -609,15 +623,15 @@ void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
   fork(c, 2);
   fit(worker(c, 0), tu, rhs_u.get(), P.fit_sweeps, true);
   fit(worker(c, 1), tv_, rhs_v.get(), P.fit_sweeps, true);
-  als(worker(c, 0), cs.H, mu, us.get(), P.mom.sweeps, P.mom.cg_iters, P.mom.cg_tol, true, cg_dev ? cg_dev + 0 : nullptr);
-  als(worker(c, 1), cs.H, mv, vs.get(), P.mom.sweeps, P.mom.cg_iters, P.mom.cg_tol, true, cg_dev ? cg_dev + 1 : nullptr);
+  als(worker(c, 0), cs.H, mu, us.get(), P.mom, true, ctl + 0, &cs.body_launches[0]);
+  als(worker(c, 1), cs.H, mv, vs.get(), P.mom, true, ctl + 1, &cs.body_launches[1]);
   join(c, 2);
   cs.mark(c, 2);
   // (iii) pressure Poisson, J-weighted (Sec. III.C): (-|J| Lap_h^p) p = -|J| (.) div(v*) / dt
   ph.reset(new ProfScope(c, KC_PH_POI));
   std::vector<Term> pr = {Term::mpo(1.0, cs.Px, us.get()), Term::mpo(1.0, cs.Pz, vs.get())};
   if (cs.bcdiv_w) pr.push_back(Term::vec(1.0, cs.bcdiv_w));
-  als(c, cs.Ap, pr, cs.p, P.poi.sweeps, P.poi.cg_iters, P.poi.cg_tol, true, cg_dev ? cg_dev + 2 : nullptr);
+  als(c, cs.Ap, pr, cs.p, P.poi, true, ctl + 2, &cs.body_launches[2]);
   // projection v = v* - dt grad_h p (one fit each, warm start v*)
   cs.mark(c, 3);
   ph.reset(new ProfScope(c, KC_PH_PROJ));
@@ -632,7 +646,10 @@ void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev) {
   // new state into the same buffers (the captured graph reads and writes these addresses)
   copy(c, cs.u->buf.p, un->buf.p, cs.u->off[n]);
   copy(c, cs.v->buf.p, vn->buf.p, cs.v->off[n]);
-  if (forces_dev) case_forces(c, cs, forces_dev);
+  fill(c, rec + kStepRecFinite, 1, 1.0);
+  check_finite(c, cs.u->buf.p, cs.u->off[n], rec + kStepRecFinite);
+  check_finite(c, cs.v->buf.p, cs.v->off[n], rec + kStepRecFinite);
+  if (with_forces) case_forces(c, cs, rec + kStepRecForces);
 }
 
 static void capture(Ctx& c, Case& cs, bool with_forces) {
@@ -645,7 +662,7 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
   if (!cs.gstream) QTT_CUDA(cudaStreamCreateWithFlags(&cs.gstream, cudaStreamNonBlocking));
   if (!cs.ev_in) QTT_CUDA(cudaEventCreateWithFlags(&cs.ev_in, cudaEventDisableTiming));
   if (!cs.ev_out) QTT_CUDA(cudaEventCreateWithFlags(&cs.ev_out, cudaEventDisableTiming));
-  if (!cs.rec) QTT_CUDA(cudaMalloc(&cs.rec, 4 * sizeof(double)));
+  if (!cs.rec) QTT_CUDA(cudaMalloc(&cs.rec, kStepRecDoubles * sizeof(double)));
   cudaStream_t saved = c.stream;
   const bool prof_on = c.root->prof.on;
   c.root->prof.on = false;   // no timing events inside a graph
@@ -659,7 +676,7 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
   cudaError_t err = cudaStreamBeginCapture(cs.gstream, cudaStreamCaptureModeRelaxed);
   try {
     if (err != cudaSuccess) throw Error(QTT_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(err));
-    step(c, cs, reinterpret_cast<int*>(cs.rec), with_forces ? cs.rec + 2 : nullptr);
+    step(c, cs, cs.rec, with_forces);
   } catch (...) {
     cs.capturing = false;
     cudaGraph_t g = nullptr;
@@ -678,7 +695,7 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
   c.pool->end_capture();
   for (Ctx* w : c.workers) w->pool->end_capture();
   c.root->prof.on = prof_on;
-  cs.graph_launches = c.root->launches - n0;
+  cs.graph_launches = c.root->launches - n0 - cs.body_launches[0] - cs.body_launches[1] - cs.body_launches[2];
   c.root->launches = n0;
   if (err != cudaSuccess) throw Error(QTT_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(err));
   QTT_CUDA(cudaGraphInstantiate(&cs.gexec, cs.graph, 0));
@@ -687,10 +704,7 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
 
 void run_steps(Ctx& c, Case& cs, int nsteps, bool with_forces, double* rec_all) {
   if (!cs.use_graph) {
-    for (int s = 0; s < nsteps; ++s) {
-      double* r = rec_all ? rec_all + 4 * s : nullptr;
-      step(c, cs, r ? reinterpret_cast<int*>(r) : nullptr, (with_forces && r) ? r + 2 : nullptr);
-    }
+    for (int s = 0; s < nsteps; ++s) step(c, cs, rec_all + int64_t(kStepRecDoubles) * s, with_forces);
     return;
   }
   if (!cs.gexec || cs.graph_forces != with_forces) capture(c, cs, with_forces);
@@ -700,8 +714,7 @@ void run_steps(Ctx& c, Case& cs, int nsteps, bool with_forces, double* rec_all) 
     QTT_CUDA(cudaGraphLaunch(cs.gexec, cs.gstream));
     QTT_CUDA(cudaEventRecord(cs.ev_out, cs.gstream));
     QTT_CUDA(cudaStreamWaitEvent(c.stream, cs.ev_out, 0));
-    c.root->launches += cs.graph_launches;
-    if (rec_all) copy(c, rec_all + 4 * s, cs.rec, 4);
+    copy(c, rec_all + int64_t(kStepRecDoubles) * s, cs.rec, kStepRecDoubles);
   }
 }
 

@@ -4,7 +4,7 @@
 #include <utility>
 #include <vector>
 
-#include "qtt_internal.h"
+#include "qtt_algebra.h"
 
 namespace qtt {
 
@@ -21,15 +21,16 @@ struct Case {
   // state
   qtt_mps *u = nullptr, *v = nullptr, *p = nullptr;
   // CUDA graph of one step (captured on first use, replayed afterwards; invalidated when the
-  // state buffers change).  The graph writes its per-step record (3 CG counts, C_D, C_L) to rec.
+  // state buffers change).  The graph writes its per-step record (kStepRecDoubles) to rec.
   bool use_graph = true;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   bool graph_forces = false;
-  int64_t graph_launches = 0;
-  double* rec = nullptr;        // 4 doubles of device memory (allocated with cudaMalloc once)
+  int64_t graph_launches = 0;       // kernels of one replay outside the ALS sweep loops
+  int64_t body_launches[3] = {0, 0, 0};  // kernels of one sweep of the u, v and p solves
+  double* rec = nullptr;            // kStepRecDoubles doubles of device memory (cudaMalloc, once)
   // Phase boundaries of the last step (timing events; external event nodes inside the graph):
   // start, after the MPO-MPS products, after the right sides + momentum, after the Poisson
   // solve, after the projection.
@@ -41,13 +42,22 @@ struct Case {
   ~Case();
 };
 
+// Record of one step (device): the AlsCtl of the u, v and p solves, a finiteness flag of the
+// new velocity (1 or 0), then C_D, C_L.
+constexpr int kStepRecFinite = 3 * kAlsCtlDoubles;
+constexpr int kStepRecForces = kStepRecFinite + 1;
+constexpr int kStepRecDoubles = kStepRecForces + 2;
+
 Case* build_case(Ctx& c, const qtt_case_params& P);
-void step(Ctx& c, Case& cs, int* cg_dev, double* forces_dev);
-// nsteps steps, replaying the captured graph when cs.use_graph; records (4 doubles per step:
-// three CG counts packed as ints in the first 16 bytes, then C_D, C_L) into rec_all (device).
+// One step; writes its record to rec (device, kStepRecDoubles) and the forces when asked.
+void step(Ctx& c, Case& cs, double* rec, bool with_forces);
+// nsteps steps, replaying the captured graph when cs.use_graph; records into rec_all (device,
+// kStepRecDoubles per step).
 void run_steps(Ctx& c, Case& cs, int nsteps, bool with_forces, double* rec_all);
 void case_forces(Ctx& c, Case& cs, double* out_dev);
 void read_row(Ctx& c, const Case& cs, const qtt_mps* x, int64_t I, double* row_dev);
+// *flag = 0 if any of x[0..n) is NaN or Inf (left untouched otherwise).
+void check_finite(Ctx& c, const double* x, int64_t n, double* flag);
 
 }  // namespace qtt
 

@@ -19,9 +19,10 @@
 // Every block sums the per-block partials in the same fixed order, so all blocks take the same
 // decisions and results are deterministic.
 //
-// Barrier: an arrival counter in device memory (reset by the host before the launch); a
-// waiting block polls it for at most 2 s (global timer).  The cooperative launch makes every
-// block resident, so the bound is only a safety net: on expiry the block sets the error flag,
+// Barrier: an arrival counter in device memory (reset before the launch); a waiting block polls
+// it for at most the context's wait limit (2 s unless set otherwise; global timer).  The
+// cooperative launch makes every block resident, so the bound is only a safety net: on expiry
+// the block sets the error flag,
 // every block leaves at its next barrier, and the iteration count is overwritten with a
 // negative value that the host turns into an error.  Data written by other blocks inside the
 // kernel are read with ld.global.cg (L2).
@@ -35,7 +36,6 @@ namespace qtt {
 namespace {
 
 constexpr int CGP_THREADS = 256;
-constexpr unsigned long long CGP_TIMEOUT_NS = 2000000000ull;   // 2 s per barrier
 constexpr int CGP_MAX_BOND = 128;
 constexpr int CGP_MAX_W = 16;
 constexpr int CGP_MAX_D = 4;
@@ -43,13 +43,13 @@ constexpr int CGP_MAX_D = 4;
 struct CgBar {
   unsigned int count;   // arrivals so far (monotonic within a launch)
   int error;            // set by a block that gave up waiting
-  int pad[2];
+  unsigned long long limit_ns;   // how long a block waits at one barrier (the context's wait limit)
 };
 
 struct CgArgs {
   int r0, r1, w0, w1, d, bt, iters;
   int eb, ch;     // stage B: e-block width (16, 8, 4, 2 or 1) and T2 row chunks per load
-  double tol2;
+  const double* tol;   // relative tolerance (device scalar, read at launch)
   const double* L;
   const double* W;
   const double* R;
@@ -59,9 +59,12 @@ struct CgArgs {
   double* p;      // 2 x (r0 d r1): directions of even and odd iterations
   double* Ap;
   double* T2;
-  double* part;   // 3 x gridDim.x
+  double* part;   // 4 x gridDim.x
+  const double* dinv;  // diagonal preconditioner (inverse of the local matrix's diagonal; may be null)
   CgBar* bar;
   int* total;     // += iterations done (may be null)
+  double* flops;  // += (iterations + 1) * fpi when profiling (may be null)
+  double fpi;     // flops of one operator application
 };
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
@@ -71,6 +74,15 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
 }
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// Barrier state before a launch: no arrivals, no error, the context's wait limit.
+__global__ void k_bar_init(CgBar* b, unsigned long long limit_ns) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    b->count = 0;
+    b->error = 0;
+    b->limit_ns = limit_ns;
+  }
+}
 
 __device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -92,10 +104,13 @@ __device__ bool grid_sync(CgBar* bar, unsigned int& target, int* flag) {
     red_release_add(&bar->count, 1u);
     const unsigned long long t0 = global_ns();
     unsigned int spins = 0;
+    const unsigned long long limit = bar->limit_ns;
+    // limits below 0.1 ms (tests of the timeout path) are checked at every poll
+    const unsigned int mask = limit < 100000ull ? 0u : 255u;
     while (ld_acquire(&bar->count) < target) {
-      if ((++spins & 255u) == 0u) {
+      if ((++spins & mask) == 0u) {
         if (ld_volatile(&bar->error)) break;
-        if (global_ns() - t0 > CGP_TIMEOUT_NS) {
+        if (global_ns() - t0 > limit) {
           atomicExch(&bar->error, 1);
           break;
         }
@@ -135,7 +150,13 @@ __device__ double sum_partials(const double* part, double* red) {
   return s;
 }
 
-// Stage A: T2 = (L . P) . W, with P the vector P0 or, when Rv is given, P = Rv + beta P0 formed
+// Preconditioned residual z = D^-1 r at element g (z = r without a preconditioner); every place
+// that forms z uses this one expression, so the values agree bit for bit.
+__device__ __forceinline__ double zval(const double* dinv, const double* r, size_t g) {
+  return dinv ? __ldg(dinv + g) * __ldcg(r + g) : __ldcg(r + g);
+}
+
+// Stage A: T2 = (L . P) . W, with P the vector P0 or, when Rv is given, P = z(Rv) + beta P0 formed
 // on the fly (the CG direction update, computed exactly as its owners store it).
 __device__ void stage_a(const CgArgs& a, const double* P0, const double* Rv, double beta, double* sL, double* sW,
                         double* sP, double* sT1) {
@@ -153,7 +174,7 @@ __device__ void stage_a(const CgArgs& a, const double* P0, const double* Rv, dou
 #pragma unroll 4
       for (int row = warp; row < r0 * d; row += nwarps) {
         const size_t g = size_t(row) * r1 + b0 + lane;
-        sP[row * bt + lane] = Rv ? fma(beta, __ldcg(P0 + g), __ldcg(Rv + g)) : __ldcg(P0 + g);
+        sP[row * bt + lane] = Rv ? fma(beta, __ldcg(P0 + g), zval(a.dinv, Rv, g)) : __ldcg(P0 + g);
       }
     }
     __syncthreads();
@@ -243,6 +264,7 @@ __global__ void __launch_bounds__(CGP_THREADS, 2) k_cg_persistent(CgArgs a) {
   double* part_pap = a.part;
   double* part_rr = a.part + G;
   double* part_bb = a.part + 2 * G;
+  double* part_rz = a.part + 3 * G;
   for (int e = tid; e < w0 * d * d * w1; e += nt) sW[e] = __ldg(a.W + e);
   {
     const int NE = (a.r1 + a.eb - 1) / a.eb, e0 = (blockIdx.x % NE) * a.eb;
@@ -262,25 +284,31 @@ __global__ void __launch_bounds__(CGP_THREADS, 2) k_cg_persistent(CgArgs a) {
     if (!(ok = grid_sync(a.bar, target, &flag))) break;
     stage_b(a, nullptr, a.Ap, sR, sT2);
     if (!(ok = grid_sync(a.bar, target, &flag))) break;
-    double rr_p = 0.0, bb_p = 0.0;
+    double rr_p = 0.0, bb_p = 0.0, rz_p = 0.0;
     for (int64_t e = int64_t(blockIdx.x) * nt + tid; e < nel; e += int64_t(G) * nt) {
       const double be = __ldg(a.b + e);
       const double re = be - __ldcg(a.Ap + e);
+      const double ze = a.dinv ? __ldg(a.dinv + e) * re : re;
       a.r[e] = re;
-      a.p[e] = re;
+      a.p[e] = ze;
       rr_p = fma(re, re, rr_p);
+      rz_p = fma(re, ze, rz_p);
       bb_p = fma(be, be, bb_p);
     }
     rr_p = block_reduce(rr_p, red);
+    rz_p = block_reduce(rz_p, red);
     bb_p = block_reduce(bb_p, red);
     if (tid == 0) {
       part_rr[blockIdx.x] = rr_p;
+      part_rz[blockIdx.x] = rz_p;
       part_bb[blockIdx.x] = bb_p;
     }
     if (!(ok = grid_sync(a.bar, target, &flag))) break;
     double rr = sum_partials(part_rr, red);
+    double rz = sum_partials(part_rz, red);
     const double bb = sum_partials(part_bb, red);
-    bool active = rr > a.tol2 * bb && rr > 0.0;
+    const double tol2 = __ldg(a.tol) * __ldg(a.tol);
+    bool active = rr > tol2 * bb && rr > 0.0;
     double beta = 0.0;
     // Three barriers per iteration: after A (T2 and p_it complete), after B (Ap and the p.Ap
     // partials), after C (x, r and the r.r partials).  part_rr is read at the top of an
@@ -292,7 +320,7 @@ __global__ void __launch_bounds__(CGP_THREADS, 2) k_cg_persistent(CgArgs a) {
         stage_a(a, pn, nullptr, 0.0, sL, sW, sP, sT1);
       } else {
         for (int64_t e = int64_t(blockIdx.x) * nt + tid; e < nel; e += int64_t(G) * nt)
-          pn[e] = fma(beta, po[e], a.r[e]);
+          pn[e] = fma(beta, po[e], zval(a.dinv, a.r, e));
         stage_a(a, po, a.r, beta, sL, sW, sP, sT1);
       }
       if (!(ok = grid_sync(a.bar, target, &flag))) break;
@@ -302,28 +330,36 @@ __global__ void __launch_bounds__(CGP_THREADS, 2) k_cg_persistent(CgArgs a) {
       if (!(ok = grid_sync(a.bar, target, &flag))) break;
       const double pap = sum_partials(part_pap, red);
       if (!(pap > 0.0)) break;                       // same decision in every block
-      const double alpha = rr / pap;
-      double rn_p = 0.0;
+      const double alpha = rz / pap;
+      double rn_p = 0.0, rzn_p = 0.0;
       for (int64_t e = int64_t(blockIdx.x) * nt + tid; e < nel; e += int64_t(G) * nt) {
         a.x[e] += alpha * pn[e];
         const double re = a.r[e] - alpha * __ldcg(a.Ap + e);
         a.r[e] = re;
         rn_p = fma(re, re, rn_p);
+        rzn_p = fma(re, a.dinv ? __ldg(a.dinv + e) * re : re, rzn_p);
       }
       rn_p = block_reduce(rn_p, red);
-      if (tid == 0) part_rr[blockIdx.x] = rn_p;
+      rzn_p = block_reduce(rzn_p, red);
+      if (tid == 0) {
+        part_rr[blockIdx.x] = rn_p;
+        part_rz[blockIdx.x] = rzn_p;
+      }
       if (!(ok = grid_sync(a.bar, target, &flag))) break;
       const double rn = sum_partials(part_rr, red);
-      beta = rn / rr;
+      const double rzn = sum_partials(part_rz, red);
+      beta = rzn / rz;
       rr = rn;
+      rz = rzn;
       count += 1;
-      active = rn > a.tol2 * bb && rn > 0.0;
+      active = rn > tol2 * bb && rn > 0.0;
     }
   } while (false);
   if (blockIdx.x == 0 && tid == 0 && a.total) {
     if (ok) *a.total += count;
     else *a.total = CGP_POISON;
   }
+  if (blockIdx.x == 0 && tid == 0 && a.flops && ok) atomicAdd(a.flops, (count + 1) * a.fpi);
 }
 
 // Stage-A block of b.  Per work item the CTA does bt r0 w0 d FP64 FMAs at the SM's 2 per cycle,
@@ -403,7 +439,8 @@ bool cg_persistent_fits(const Ctx& c, int r0, int r1, int w0, int w1, int d) {
 }
 
 void cg_persistent(Ctx& c, const double* L, const double* W, const double* R, const double* b, double* x, int r0,
-                   int r1, int w0, int w1, int d, int iters, double tol, int* total_dev) {
+                   int r1, int w0, int w1, int d, int iters, const double* tol_dev, int* total_dev,
+                   const double* dinv) {
   CgPlan pl;
   QTT_CHECK_ARG(cg_plan(c, r0, r1, w0, w1, d, pl), "cg_persistent: shape outside the supported range");
   cg_init_attributes();
@@ -411,17 +448,20 @@ void cg_persistent(Ctx& c, const double* L, const double* W, const double* R, co
   const int G = pl.G, bt = pl.bt;
   const size_t smem = pl.smem;
   const int64_t nel = int64_t(r0) * d * r1;
-  DBuf r(&c, nel), p(&c, 2 * nel), Ap(&c, nel), T2(&c, size_t(r0) * d * w1 * r1), part(&c, size_t(3) * G),
+  DBuf r(&c, nel), p(&c, 2 * nel), Ap(&c, nel), T2(&c, size_t(r0) * d * w1 * r1), part(&c, size_t(4) * G),
       bar(&c, (sizeof(CgBar) + 7) / 8);
-  QTT_CUDA(cudaMemsetAsync(bar.p, 0, sizeof(CgBar), c.stream));
+  k_bar_init<<<1, 1, 0, c.stream>>>(reinterpret_cast<CgBar*>(bar.p), c.root->wait_ns);
+  after_launch(c, "bar_init");
   CgArgs a;
   a.r0 = r0; a.r1 = r1; a.w0 = w0; a.w1 = w1; a.d = d; a.bt = bt; a.iters = iters;
   a.eb = pl.eb; a.ch = pl.ch;
-  a.tol2 = tol * tol;
+  a.tol = tol_dev;
   a.L = L; a.W = W; a.R = R; a.b = b; a.x = x;
-  a.r = r.p; a.p = p.p; a.Ap = Ap.p; a.T2 = T2.p; a.part = part.p;
+  a.r = r.p; a.p = p.p; a.Ap = Ap.p; a.T2 = T2.p; a.part = part.p; a.dinv = dinv;
   a.bar = reinterpret_cast<CgBar*>(bar.p);
   a.total = total_dev;
+  a.flops = c.root->prof.on ? c.root->prof.dev_flops : nullptr;
+  a.fpi = 2.0 * (double(r0) * w0 * r0 * d * r1 + double(r0) * d * w0 * d * w1 * r1 + double(r0) * d * w1 * r1 * r1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(G));
   cfg.blockDim = dim3(CGP_THREADS);
@@ -469,7 +509,7 @@ struct CgTcArgs {
   int MA, NA, KA, KpA;      // stage A: rows (c, w) = r0 w0, columns (t, b) = d r1, k = a (r0)
   int MB, NB, KB, KpB;      // stage B: rows c = r0, columns (s, e) = d r1, k = (w, t, b)
   int IA, IB, nNA, nNB;
-  double tol2;
+  const double* tol;        // relative tolerance (device scalar, read at launch)
   const __nv_bfloat16* La;  // [S][MA][KpA] digit slices of the rows of L
   const int* eL;            // [MA] scale exponents
   const __nv_bfloat16* Qd;  // [S][NB][KpB] digit slices of the rows of Q
@@ -482,9 +522,12 @@ struct CgTcArgs {
   double* p;                // 2 x nel: directions of even and odd iterations
   double* Ap;
   double* T1;               // MA x NA = MB x KB
-  double* part;             // 3 x gridDim.x
+  double* part;             // 4 x gridDim.x
+  const double* dinv;       // diagonal preconditioner (may be null)
   CgBar* bar;
   int* total;
+  double* flops;            // += (iterations + 1) * fpi when profiling (may be null)
+  double fpi;               // FP64-equivalent flops of one operator application
 };
 
 __device__ __forceinline__ double tc_nan() { return __longlong_as_double(0x7ff8000000000000ll); }
@@ -570,7 +613,7 @@ __device__ void tc_stage_a(const CgTcArgs& a, const double* P0, const double* Rv
     double v = 0.0;
     if (n < a.NA) {
       const size_t g = size_t(k) * a.NA + n;
-      v = Rv ? fma(beta, __ldcg(P0 + g), __ldcg(Rv + g)) : __ldcg(P0 + g);
+      v = Rv ? fma(beta, __ldcg(P0 + g), zval(a.dinv, Rv, g)) : __ldcg(P0 + g);
     }
     sPv[e] = v;
     fmax = max(fmax, oz_field(v));
@@ -704,6 +747,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cg_tc(CgTcArgs a) {
   double* part_pap = a.part;
   double* part_rr = a.part + G;
   double* part_bb = a.part + 2 * G;
+  double* part_rz = a.part + 3 * G;
   // stage-A CTAs: their rows of the L slices, resident for the whole solve
   if (int(blockIdx.x) < a.IA) {
     const int ldA = a.KpA + 8, m0 = (int(blockIdx.x) / a.nNA) * TC_AM, v8 = a.KpA / 8;
@@ -729,25 +773,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cg_tc(CgTcArgs a) {
     if (!(ok = grid_sync(a.bar, target, &flag))) break;
     tc_stage_b(a, nullptr, tc_sm);
     if (!(ok = grid_sync(a.bar, target, &flag))) break;
-    double rr_p = 0.0, bb_p = 0.0;
+    double rr_p = 0.0, bb_p = 0.0, rz_p = 0.0;
     for (int64_t e = int64_t(blockIdx.x) * nt + tid; e < nel; e += int64_t(G) * nt) {
       const double be = __ldg(a.b + e);
       const double re = be - __ldcg(a.Ap + e);
+      const double ze = a.dinv ? __ldg(a.dinv + e) * re : re;
       a.r[e] = re;
-      a.p[e] = re;
+      a.p[e] = ze;
       rr_p = fma(re, re, rr_p);
+      rz_p = fma(re, ze, rz_p);
       bb_p = fma(be, be, bb_p);
     }
     rr_p = block_reduce(rr_p, red);
+    rz_p = block_reduce(rz_p, red);
     bb_p = block_reduce(bb_p, red);
     if (tid == 0) {
       part_rr[blockIdx.x] = rr_p;
+      part_rz[blockIdx.x] = rz_p;
       part_bb[blockIdx.x] = bb_p;
     }
     if (!(ok = grid_sync(a.bar, target, &flag))) break;
     double rr = sum_partials(part_rr, red);
+    double rz = sum_partials(part_rz, red);
     const double bb = sum_partials(part_bb, red);
-    bool active = rr > a.tol2 * bb && rr > 0.0;
+    const double tol2 = __ldg(a.tol) * __ldg(a.tol);
+    bool active = rr > tol2 * bb && rr > 0.0;
     double beta = 0.0;
     for (int it = 0; it < a.iters && active; ++it) {
       double* pn = a.p + (it & 1) * nel;
@@ -756,7 +806,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cg_tc(CgTcArgs a) {
         tc_stage_a(a, pn, nullptr, 0.0, tc_sm);
       } else {
         for (int64_t e = int64_t(blockIdx.x) * nt + tid; e < nel; e += int64_t(G) * nt)
-          pn[e] = fma(beta, po[e], a.r[e]);
+          pn[e] = fma(beta, po[e], zval(a.dinv, a.r, e));
         tc_stage_a(a, po, a.r, beta, tc_sm);
       }
       if (!(ok = grid_sync(a.bar, target, &flag))) break;
@@ -768,28 +818,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cg_tc(CgTcArgs a) {
       if (!(ok = grid_sync(a.bar, target, &flag))) break;
       const double pap = sum_partials(part_pap, red);
       if (!(pap > 0.0)) break;
-      const double alpha = rr / pap;
-      double rn_p = 0.0;
+      const double alpha = rz / pap;
+      double rn_p = 0.0, rzn_p = 0.0;
       for (int64_t e = int64_t(blockIdx.x) * nt + tid; e < nel; e += int64_t(G) * nt) {
         a.x[e] += alpha * pn[e];
         const double re = a.r[e] - alpha * __ldcg(a.Ap + e);
         a.r[e] = re;
         rn_p = fma(re, re, rn_p);
+        rzn_p = fma(re, a.dinv ? __ldg(a.dinv + e) * re : re, rzn_p);
       }
       rn_p = block_reduce(rn_p, red);
-      if (tid == 0) part_rr[blockIdx.x] = rn_p;
+      rzn_p = block_reduce(rzn_p, red);
+      if (tid == 0) {
+        part_rr[blockIdx.x] = rn_p;
+        part_rz[blockIdx.x] = rzn_p;
+      }
       if (!(ok = grid_sync(a.bar, target, &flag))) break;
       const double rn = sum_partials(part_rr, red);
-      beta = rn / rr;
+      const double rzn = sum_partials(part_rz, red);
+      beta = rzn / rz;
       rr = rn;
+      rz = rzn;
       count += 1;
-      active = rn > a.tol2 * bb && rn > 0.0;
+      active = rn > tol2 * bb && rn > 0.0;
     }
   } while (false);
   if (blockIdx.x == 0 && tid == 0 && a.total) {
     if (ok) *a.total += count;
     else *a.total = CGP_POISON;
   }
+  if (blockIdx.x == 0 && tid == 0 && a.flops && ok) atomicAdd(a.flops, (count + 1) * a.fpi);
 }
 
 struct TcPlan {
@@ -845,7 +903,7 @@ bool cg_tc_fits(const Ctx& c, int r0, int r1, int w0, int w1, int d) {
 }
 
 void cg_tc(Ctx& c, const double* L, const double* W, const double* R, const double* b, double* x, int r0, int r1,
-           int w0, int w1, int d, int iters, double tol, int* total_dev) {
+           int w0, int w1, int d, int iters, const double* tol_dev, int* total_dev, const double* dinv) {
   TcPlan pl;
   cg_tc_init_attributes();
   QTT_CHECK_ARG(g_tc_ok && tc_plan(c, r0, r1, w0, w1, d, pl), "cg_tc: shape outside the supported range");
@@ -856,28 +914,31 @@ void cg_tc(Ctx& c, const double* L, const double* W, const double* R, const doub
   DBuf La(&c, halves(size_t(OZ_S) * pl.MA * pl.KpA)), eL(&c, ints(pl.MA)), Q(&c, size_t(pl.NB) * pl.KB),
       Qd(&c, halves(size_t(OZ_S) * pl.NB * pl.KpB)), eQ(&c, ints(pl.NB)), Td(&c, halves(size_t(OZ_S) * pl.MB * pl.KpB)),
       fT(&c, ints(pl.MB)), r(&c, nel), p(&c, 2 * nel), Ap(&c, nel), T1(&c, size_t(pl.MA) * pl.NA),
-      part(&c, size_t(3) * G), bar(&c, (sizeof(CgBar) + 7) / 8);
+      part(&c, size_t(4) * G), bar(&c, (sizeof(CgBar) + 7) / 8);
   // per solve: digit slices of the rows of L, Q = W x_v R and its rows' digit slices
   oz_split_rows(c, pl.MA, pl.KA, pl.KpA, L, pl.KA, 1, La.p, reinterpret_cast<int*>(eL.p));
   einsum(c, "wstv,evb->sewtb", 1.0, tv(const_cast<double*>(W), {w0, d, d, w1}),
          tv(const_cast<double*>(R), {r1, w1, r1}), 0.0, tv(Q.p, {d, r1, w0, d, r1}));
   oz_split_rows(c, pl.NB, pl.KB, pl.KpB, Q.p, pl.KB, 1, Qd.p, reinterpret_cast<int*>(eQ.p));
-  QTT_CUDA(cudaMemsetAsync(bar.p, 0, sizeof(CgBar), c.stream));
+  k_bar_init<<<1, 1, 0, c.stream>>>(reinterpret_cast<CgBar*>(bar.p), c.root->wait_ns);
+  after_launch(c, "bar_init");
   CgTcArgs a;
   a.iters = iters;
   a.MA = pl.MA; a.NA = pl.NA; a.KA = pl.KA; a.KpA = pl.KpA;
   a.MB = pl.MB; a.NB = pl.NB; a.KB = pl.KB; a.KpB = pl.KpB;
   a.IA = pl.IA; a.IB = pl.IB; a.nNA = pl.nNA; a.nNB = pl.nNB;
-  a.tol2 = tol * tol;
+  a.tol = tol_dev;
   a.La = reinterpret_cast<const __nv_bfloat16*>(La.p);
   a.eL = reinterpret_cast<const int*>(eL.p);
   a.Qd = reinterpret_cast<const __nv_bfloat16*>(Qd.p);
   a.eQ = reinterpret_cast<const int*>(eQ.p);
   a.Td = reinterpret_cast<__nv_bfloat16*>(Td.p);
   a.fT = reinterpret_cast<int*>(fT.p);
-  a.b = b; a.x = x; a.r = r.p; a.p = p.p; a.Ap = Ap.p; a.T1 = T1.p; a.part = part.p;
+  a.b = b; a.x = x; a.r = r.p; a.p = p.p; a.Ap = Ap.p; a.T1 = T1.p; a.part = part.p; a.dinv = dinv;
   a.bar = reinterpret_cast<CgBar*>(bar.p);
   a.total = total_dev;
+  a.flops = c.root->prof.on ? c.root->prof.dev_flops : nullptr;
+  a.fpi = 2.0 * (double(r0) * w0 * r0 * d * r1 + double(r0) * d * r1 * w0 * d * r1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(G));
   cfg.blockDim = dim3(TC_THREADS);

@@ -244,6 +244,7 @@ void destroy_workers(Ctx& c) {
     free_tile_counters(*w);
     delete w->pool;
     cudaStreamDestroy(w->stream);
+    if (w->side) cudaStreamDestroy(w->side);
     delete w;
   }
   c.workers.clear();

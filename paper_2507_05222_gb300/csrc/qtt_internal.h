@@ -117,6 +117,9 @@ struct Profiler {
   double phase_ms[KC_PHASES + 1][KC_KERNEL_CLASSES] = {};
   int64_t phase_launches[KC_PHASES + 1] = {0};
   int64_t acc_phase_launches[KC_PHASES + 1] = {0};
+  // Flops of the cooperative CG solves, counted on the device (their iteration counts are
+  // data dependent); one double of device memory, allocated when profiling is first turned on.
+  double* dev_flops = nullptr;
 };
 
 struct Ctx {
@@ -149,6 +152,12 @@ struct Ctx {
   // Per-tile arrival counters of split-K GEMMs on this context's stream (kTileCounters ints,
   // zero between launches: the last CTA of a tile resets its counter).
   int* tile_ctr = nullptr;
+  // Stream on which the body of a conditional graph node (the ALS sweep loop) is captured.
+  cudaStream_t side = nullptr;
+  // When non-null, every TT-SVD cut of a rounding adds its discarded sigma^2 here (device).
+  double* disc_acc = nullptr;
+  // Limit of every bounded device wait (grid barriers of the cooperative CG), read from root.
+  unsigned long long wait_ns = 2000000000ull;
   Profiler prof;
 };
 

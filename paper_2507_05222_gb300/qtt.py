@@ -37,15 +37,19 @@ class qtt_trunc(C.Structure):
 
 
 class qtt_round_info(C.Structure):
-    _fields_ = [("max_bond", C.c_int), ("norm", C.c_double)]
+    _fields_ = [("max_bond", C.c_int), ("norm", C.c_double), ("discarded_norm", C.c_double)]
 
 
 class qtt_solve_opts(C.Structure):
-    _fields_ = [("sweeps", C.c_int), ("cg_iters", C.c_int), ("cg_tol", C.c_double)]
+    _fields_ = [("max_sweeps", C.c_int), ("rel_tol", C.c_double), ("cg_max_iter", C.c_int),
+                ("cg_tol", C.c_double), ("stall", C.c_double)]
 
 
 class qtt_solve_info(C.Structure):
-    _fields_ = [("cg_iters_total", C.c_int), ("rel_residual", C.c_double)]
+    _fields_ = [("sweeps", C.c_int), ("cg_iters", C.c_int), ("rel_residual", C.c_double), ("status", C.c_int)]
+
+
+SOLVE_STATUS = {0: "converged", 1: "stalled", 2: "max_sweeps", 3: "nonfinite", 4: "timeout"}
 
 
 class qtt_case_params(C.Structure):
@@ -56,7 +60,25 @@ class qtt_case_params(C.Structure):
 
 
 class qtt_step_info(C.Structure):
-    _fields_ = [("cg_u", C.c_int), ("cg_v", C.c_int), ("cg_p", C.c_int), ("cd", C.c_double), ("cl", C.c_double)]
+    _fields_ = [("u", qtt_solve_info), ("v", qtt_solve_info), ("p", qtt_solve_info), ("finite", C.c_int),
+                ("cd", C.c_double), ("cl", C.c_double)]
+
+
+def _solve_dict(i: qtt_solve_info) -> dict:
+    return dict(sweeps=i.sweeps, cg_iters=i.cg_iters, rel_residual=i.rel_residual, status=i.status)
+
+
+def solve_opts(max_sweeps: int, rel_tol: float, cg_max_iter: int, cg_tol: float = 1e-2,
+               stall: float = 0.1) -> qtt_solve_opts:
+    """ALS options (stop rule of include/qtt.h): sweeps until the true relative residual is
+    <= rel_tol, a sweep gains less than the fraction ``stall``, or max_sweeps; local CG to
+    cg_tol x the current residual, at most cg_max_iter iterations."""
+    return qtt_solve_opts(int(max_sweeps), float(rel_tol), int(cg_max_iter), float(cg_tol), float(stall))
+
+
+# Step defaults (the oracle's StepOpts has the same): momentum and Poisson solve options.
+MOM_DEFAULT = (6, 1e-10, 100, 1e-2, 0.1)
+POI_DEFAULT = (12, 1e-10, 500, 1e-2, 0.1)
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -79,6 +101,7 @@ _SIGS = {
     "qtt_ctx_profile_phases": (I, [P, DP, C.POINTER(C.c_int64)]),
     "qtt_qr": (I, [P, I, I, I, DP, DP, DP, I]),
     "qtt_ctx_set_cg_mode": (I, [P, I]),
+    "qtt_ctx_set_wait_limit": (I, [P, D]),
     "qtt_check_recip": (I, [P, I, DP, DP]),
     "qtt_dgemm": (I, [P, I, I, I, DP, DP, DP, I]),
     "qtt_ctx_set_gemm_mode": (I, [P, I]),
@@ -106,7 +129,7 @@ _SIGS = {
     "mps_dot": (I, [P, P, P, DP]),
     "qtt_sym_eig": (I, [P, I, DP, DP, DP]),
     "mps_dot_noalloc": (I, [I, I, IP, P, IP, P, P, P]),
-    "poisson_solve": (I, [P, P, P, P, C.POINTER(qtt_solve_opts), D, C.POINTER(qtt_solve_info)]),
+    "poisson_solve": (I, [P, P, P, P, C.POINTER(qtt_solve_opts), C.POINTER(qtt_solve_info)]),
     "qtt_case_create": (I, [P, C.POINTER(qtt_case_params), C.POINTER(P)]),
     "qtt_case_free": (I, [P]),
     "qtt_case_set_state": (I, [P, P, P, P]),
@@ -159,13 +182,19 @@ def _dp(a: np.ndarray):
 class Context:
     """One device, one stream (torch's current stream unless given), torch-backed device memory."""
 
-    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = True):
+    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = True, allocator=None):
+        """allocator: optional (alloc(nbytes) -> int device pointer or 0, free(ptr)) pair of Python
+        callables given to the library's allocator hooks instead of torch's caching allocator."""
         import torch
         self.device = device
         self._torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         sp = P(self.stream.cuda_stream)
-        if use_torch_allocator:
+        if allocator is not None:
+            ua, uf = allocator
+            self._alloc = ALLOC_FN(lambda nbytes, _user: ua(int(nbytes)) or None)
+            self._free = FREE_FN(lambda ptr, _user: uf(int(ptr)))
+        elif use_torch_allocator:
             dev, st = device, self.stream
 
             def _alloc(nbytes, _user):
@@ -206,6 +235,10 @@ class Context:
                                      n.ctypes.data_as(C.POINTER(C.c_int64))))
         return {k: dict(ms=float(ms[i]), flops=float(fl[i]), launches=int(n[i]))
                 for i, k in enumerate(self.PROFILE_CLASSES)}
+
+    def set_wait_limit(self, seconds: float):
+        """Limit of every bounded device wait (grid barriers of the cooperative CG), default 2 s."""
+        _check(lib().qtt_ctx_set_wait_limit(self.h, float(seconds)))
 
     def set_gemm_mode(self, mode: int):
         """0 (default): large products on the tensor cores (digit-split FP64); 1: FP64 pipe only."""
@@ -358,10 +391,27 @@ def _trunc(chi, rel_tol):
     return qtt_trunc(int(chi), float(rel_tol))
 
 
-def qtt_encode(ctx: Context, dense, n: int, chi: int, rel_tol: float = 0.0, d: int = 2) -> MPS:
+def _info_ptr(out_info):
+    return C.byref(out_info[1]) if out_info is not None else None
+
+
+def _round_info(out_info):
+    """(dict to fill, struct) when the caller asked for the rounding record."""
+    return None if out_info is None else (out_info, qtt_round_info())
+
+
+def _fill_round(ri):
+    if ri is not None:
+        d, st = ri
+        d.update(max_bond=st.max_bond, norm=st.norm, discarded_norm=st.discarded_norm)
+
+
+def qtt_encode(ctx: Context, dense, n: int, chi: int, rel_tol: float = 0.0, d: int = 2, out_info=None) -> MPS:
     a = np.ascontiguousarray(np.asarray(dense, dtype=np.float64).ravel())
     h = P()
-    _check(lib().qtt_encode(ctx.h, _dp(a), QTT_HOST, n, d, _trunc(chi, rel_tol), C.byref(h), None))
+    ri = _round_info(out_info)
+    _check(lib().qtt_encode(ctx.h, _dp(a), QTT_HOST, n, d, _trunc(chi, rel_tol), C.byref(h), _info_ptr(ri)))
+    _fill_round(ri)
     return MPS(ctx, h)
 
 
@@ -388,28 +438,39 @@ def qtt_vector_to_field(ctx: Context, vec, n_eta: int, n_xi: int, ordering: str)
     return out.reshape(2 ** n_eta, 2 ** n_xi)
 
 
-def qtt_round(ctx: Context, x: MPS, chi: int, rel_tol: float = 0.0) -> MPS:
+def qtt_round(ctx: Context, x: MPS, chi: int, rel_tol: float = 0.0, out_info=None) -> MPS:
+    """TT-rounding; ``out_info`` (a dict, optional) receives max_bond, norm, discarded_norm."""
     h = P()
-    _check(lib().qtt_round(ctx.h, x.h, _trunc(chi, rel_tol), C.byref(h), None))
+    ri = _round_info(out_info)
+    _check(lib().qtt_round(ctx.h, x.h, _trunc(chi, rel_tol), C.byref(h), _info_ptr(ri)))
+    _fill_round(ri)
     return MPS(ctx, h)
 
 
-def mps_axpby_round(ctx: Context, alpha: float, x: MPS, beta: float, y: MPS, chi: int, rel_tol: float = 0.0) -> MPS:
+def mps_axpby_round(ctx: Context, alpha: float, x: MPS, beta: float, y: MPS, chi: int, rel_tol: float = 0.0,
+                    out_info=None) -> MPS:
     h = P()
-    _check(lib().mps_axpby_round(ctx.h, alpha, x.h, beta, y.h, _trunc(chi, rel_tol), C.byref(h), None))
+    ri = _round_info(out_info)
+    _check(lib().mps_axpby_round(ctx.h, alpha, x.h, beta, y.h, _trunc(chi, rel_tol), C.byref(h), _info_ptr(ri)))
+    _fill_round(ri)
     return MPS(ctx, h)
 
 
-def mpo_apply_round(ctx: Context, M: MPO, x: MPS, chi: int, rel_tol: float = 0.0) -> MPS:
+def mpo_apply_round(ctx: Context, M: MPO, x: MPS, chi: int, rel_tol: float = 0.0, out_info=None) -> MPS:
     h = P()
-    _check(lib().mpo_apply_round(ctx.h, M.h, x.h, _trunc(chi, rel_tol), C.byref(h), None))
+    ri = _round_info(out_info)
+    _check(lib().mpo_apply_round(ctx.h, M.h, x.h, _trunc(chi, rel_tol), C.byref(h), _info_ptr(ri)))
+    _fill_round(ri)
     return MPS(ctx, h)
 
 
-def mps_hadamard_round(ctx: Context, a: MPS, b: MPS, chi: int, sweeps: int = 2, init: MPS | None = None) -> MPS:
+def mps_hadamard_round(ctx: Context, a: MPS, b: MPS, chi: int, sweeps: int = 2, init: MPS | None = None,
+                       out_info=None) -> MPS:
     h = P()
+    ri = _round_info(out_info)
     _check(lib().mps_hadamard_round(ctx.h, a.h, b.h, _trunc(chi, 0.0), init.h if init is not None else None,
-                                    sweeps, C.byref(h), None))
+                                    sweeps, C.byref(h), _info_ptr(ri)))
+    _fill_round(ri)
     return MPS(ctx, h)
 
 
@@ -481,14 +542,17 @@ def mps_dot(ctx: Context, a: MPS, b: MPS) -> float:
     return out.value
 
 
-def poisson_solve(ctx: Context, A: MPO, b: MPS, x: MPS, sweeps: int, cg_iters: int, cg_tol: float,
-                  tol: float = 0.0, residual: bool = True):
-    """Solve A x = b in place on x; returns (cg_iterations, relative_residual)."""
-    o = qtt_solve_opts(sweeps, cg_iters, cg_tol)
+def poisson_solve(ctx: Context, A: MPO, b: MPS, x: MPS, max_sweeps: int, rel_tol: float, cg_max_iter: int,
+                  cg_tol: float = 1e-2, stall: float = 0.1, check: bool = False) -> dict:
+    """Solve A x = b in place on x (ALS under the stop rule of include/qtt.h).  Returns the solve
+    record (sweeps, cg_iters, rel_residual, status) and the return code (``rc``); a stall or
+    running out of sweeps raises only when ``check``; other errors always raise."""
+    o = solve_opts(max_sweeps, rel_tol, cg_max_iter, cg_tol, stall)
     info = qtt_solve_info()
-    rc = lib().poisson_solve(ctx.h, A.h, b.h, x.h, C.byref(o), tol, C.byref(info) if residual else None)
-    _check(rc)
-    return info.cg_iters_total, info.rel_residual
+    rc = lib().poisson_solve(ctx.h, A.h, b.h, x.h, C.byref(o), C.byref(info))
+    if rc != 0 and (check or rc != -4):
+        _check(rc)
+    return dict(_solve_dict(info), rc=rc)
 
 
 # ------------------------------------------------------------------ cylinder case
@@ -496,10 +560,11 @@ def poisson_solve(ctx: Context, A: MPO, b: MPS, x: MPS, sweeps: int, cg_iters: i
 class Case:
     def __init__(self, ctx: Context, n_eta: int, n_xi: int, R: float, Re: float, dt: float, chi: int,
                  ordering: str = "interleaved", D: float = 1.0, rot: float = 0.0, u_inf: float = 1.0,
-                 fit_sweeps: int = 1, mom=(1, 8, 1e-12), poi=(2, 20, 1e-12)):
+                 fit_sweeps: int = 1, mom=MOM_DEFAULT, poi=POI_DEFAULT):
+        """mom, poi: ALS options (max_sweeps, rel_tol, cg_max_iter[, cg_tol[, stall]])."""
         self.ctx = ctx
         self.params = qtt_case_params(n_eta, n_xi, ORDERING[ordering], D, R, Re, dt, rot, u_inf, chi, fit_sweeps,
-                                      qtt_solve_opts(*mom), qtt_solve_opts(*poi))
+                                      solve_opts(*mom), solve_opts(*poi))
         h = P()
         _check(lib().qtt_case_create(ctx.h, C.byref(self.params), C.byref(h)))
         self.h = h
@@ -522,8 +587,8 @@ class Case:
         _check(lib().qtt_case_get_vector(self.h, which, C.byref(h)))
         return MPS(self.ctx, h) if h.value else None
 
-    def fractional_step(self, nsteps: int = 1, with_forces: bool = False):
-        return fractional_step(self.ctx, self, nsteps, with_forces)
+    def fractional_step(self, nsteps: int = 1, with_forces: bool = False, check: bool = True):
+        return fractional_step(self.ctx, self, nsteps, with_forces, check=check)
 
     def phase_ms(self):
         """Wall time (ms) of the last step's phases: apply, rhs+momentum, Poisson, projection."""
@@ -548,14 +613,23 @@ class Case:
             pass
 
 
-def fractional_step(ctx: Context, case: Case, nsteps: int = 1, with_forces: bool = False, info: bool = True):
-    """Advance ``nsteps`` fractional steps; returns per-step dicts (CG counts, C_D, C_L) or None."""
+def fractional_step(ctx: Context, case: Case, nsteps: int = 1, with_forces: bool = False, info: bool = True,
+                    check: bool = True):
+    """Advance ``nsteps`` fractional steps; returns per-step dicts (the three solve records u, v,
+    p, ``finite``, C_D, C_L; plus cg_u, cg_v, cg_p) or None.  A non-zero return code raises when
+    ``check`` (the exception carries the records as ``.records``)."""
     if not info:
         _check(lib().fractional_step(ctx.h, case.h, nsteps, 0, None))
         return None
     recs = (qtt_step_info * max(nsteps, 1))()
-    _check(lib().fractional_step(ctx.h, case.h, nsteps, 1 if with_forces else 0, recs))
-    return [dict(cg_u=r.cg_u, cg_v=r.cg_v, cg_p=r.cg_p, cd=r.cd, cl=r.cl) for r in recs[:nsteps]]
+    rc = lib().fractional_step(ctx.h, case.h, nsteps, 1 if with_forces else 0, recs)
+    out = [dict(u=_solve_dict(r.u), v=_solve_dict(r.v), p=_solve_dict(r.p), finite=r.finite, cd=r.cd, cl=r.cl,
+                cg_u=r.u.cg_iters, cg_v=r.v.cg_iters, cg_p=r.p.cg_iters, rc=rc) for r in recs[:nsteps]]
+    if rc != 0 and check:
+        err = QttError(rc, lib().qtt_last_error().decode())
+        err.records = out
+        raise err
+    return out
 
 
 def qtt_strouhal(t, cl) -> float:

@@ -55,22 +55,36 @@ def test_case_operators_and_vectors(ctx, ordering, ne, nx, rot):
             assert rel(qtt.qtt_decode(ctx, g), tt.full(x)) < 1e-13, w
 
 
+def same_solves(info, oi):
+    """The GPU step's three solves took the oracle's sweep counts and stop decisions, with
+    residuals equal to 1e-6 of themselves (each is resolved to ~1e-15 absolute) and CG counts
+    within two (a local CG stop can move by one on a last-digit difference)."""
+    for k in "uvp":
+        g, o = info[k], oi[k]
+        assert (g["sweeps"], g["status"]) == (o["sweeps"], o["status"]), (k, g, o)
+        assert abs(g["rel_residual"] - o["rel_residual"]) <= 1e-6 * o["rel_residual"] + 1e-15, (k, g, o)
+        assert abs(g["cg_iters"] - o["cg_iters"]) <= 2 * max(1, g["sweeps"]), (k, g, o)
+
+
+def step_opts(chi, qtt):
+    return S.StepOpts(chi=chi, fit_sweeps=1, mom=S.SolveOpts(*qtt.MOM_DEFAULT), poi=S.SolveOpts(*qtt.POI_DEFAULT))
+
+
 @pytest.mark.parametrize("ordering,ne,nx,chi", [("interleaved", 3, 3, 8), ("sequential", 3, 3, 8),
                                                ("interleaved", 4, 4, 8)])
 def test_one_step_matches_oracle(ctx, ordering, ne, nx, chi):
-    """Sec. III.C: one fractional step equals the oracle's L1 step (same algorithm)."""
+    """Sec. III.C: one fractional step equals the oracle's L1 step (same algorithm, solves swept
+    to the true-residual stop rule)."""
     from paper_2507_05222_gb300 import qtt
     R, Re, dt = 40.0, 100.0, 2e-3
     ops = Q.Ops(ne, nx, R, Re, dt, ordering)
     (u, v, p), (gu, gv, gp), _ = make_state(ctx, ops, ne, nx, chi)
-    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, ordering, fit_sweeps=1, mom=(1, 8, 1e-12), poi=(2, 20, 1e-12))
+    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, ordering)
     case.set_state(gu, gv, gp)
-    info = case.fractional_step(1, with_forces=False)
-    o = S.StepOpts(chi=chi, fit_sweeps=1, mom_sweeps=1, mom_cg=8, poi_sweeps=2, poi_cg=20, cg_tol=1e-12)
-    un, vn, pn, oi = S.step(ops, u, v, p, o)
-    # CG stops on a relative-residual threshold; a last-digit difference may move a stop by one
-    assert abs(info[0]["cg_u"] - oi["cg_u"]) <= 2 and abs(info[0]["cg_v"] - oi["cg_v"]) <= 2
-    assert abs(info[0]["cg_p"] - oi["cg_p"]) <= 2
+    info = case.fractional_step(1, with_forces=False, check=False)
+    un, vn, pn, oi = S.step(ops, u, v, p, step_opts(chi, qtt))
+    same_solves(info[0], oi)
+    assert info[0]["finite"] == 1
     su, sv, sp = case.get_state()
     for g, r in ((su, un), (sv, vn), (sp, pn)):
         assert rel(qtt.qtt_decode(ctx, g), tt.full(r)) < TOL
@@ -83,13 +97,14 @@ def test_full_rank_steps_match_fd(ctx):
     R, Re, dt, chi = 40.0, 100.0, 2e-3, 8
     ops = Q.Ops(ne, nx, R, Re, dt, "interleaved")
     _, (gu, gv, gp), (u0, v0) = make_state(ctx, ops, ne, nx, chi)
-    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=2, mom=(3, 100, 1e-15),
-                    poi=(6, 200, 1e-15))
+    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=2, mom=(6, 1e-14, 200, 1e-3, 0.0),
+                    poi=(8, 1e-13, 300, 1e-3, 0.0))
     case.set_state(gu, gv, gp)
     L0 = fd.FDSolver(fd.Case(fd.Grid(ne, nx, R), Re, dt))
     u, v = u0, v0
     for _ in range(3):
-        case.fractional_step(1)
+        info = case.fractional_step(1)
+        assert all(info[0][k]["status"] == 0 for k in "uvp")
         u, v, p, _, _ = L0.step(u, v)
     su, sv, sp = case.get_state()
     for g, r in ((su, u), (sv, v), (sp, p)):
@@ -114,35 +129,65 @@ def test_forces_match_fd(ctx):
     assert abs(cl - rcl) <= 1e-10 * max(1.0, abs(rcl))
 
 
-def test_multi_step_truncated_parity(ctx):
-    """Several steps with active truncation (12 bits, chi = 16): GPU and oracle take the same
-    algorithmic path.  The tolerance follows from the trajectory's own conditioning, measured on
-    the oracle: a 1.7e-15 relative perturbation of u grows to 6e-12 after one step and 1.1e-10
-    after three (amplification ~4e3 and ~7e4: truncated SVDs of near-flat noise spectra).  With
-    per-operation GPU/oracle differences of ~1e-12 (Gram rounding at these spectra), the
-    bounds are 1e-8 after one step and 1e-6 after three."""
+def wake_state(ops, ne, nx, chi, seed):
+    u0, v0 = inputs.wake_field(ne, nx, seed)
+    u, v = ops.encode(u0, chi), ops.encode(v0, chi)
+    p = S.padded([np.zeros((1, 2, 1))] * (ne + nx), chi, inputs.random_cores(ne + nx, chi, seed + 2, scale=1e-8))
+    return u, v, p
+
+
+@pytest.mark.parametrize("seed", list(range(10)))
+def test_multi_step_truncated_parity(ctx, seed):
+    """Config 1 with truncation active: 12 bits (2^6 x 2^6 cells), chi = 16, ten steps from a
+    seeded smooth wake state (a decaying spectrum, so no rounding cut falls inside a degenerate
+    singular pair), solves under the step's stop rule: after every step the GPU state equals the
+    oracle's to 1e-10 and each solve takes the oracle's sweeps and stop decision."""
     from paper_2507_05222_gb300 import qtt
     ne = nx = 6
     R, Re, dt, chi = 40.0, 100.0, 2e-3, 16
     ops = Q.Ops(ne, nx, R, Re, dt, "interleaved")
-    (u, v, p), (gu, gv, gp), _ = make_state(ctx, ops, ne, nx, chi)
-    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=1, mom=(1, 8, 1e-12), poi=(2, 20, 1e-12))
-    case.set_state(gu, gv, gp)
-    o = S.StepOpts(chi=chi, fit_sweeps=1, mom_sweeps=1, mom_cg=8, poi_sweeps=2, poi_cg=20, cg_tol=1e-12)
-    errs = []
-    for s in range(3):
-        case.fractional_step(1)
-        u, v, p, _ = S.step(ops, u, v, p, o)
-        su, sv, sp = case.get_state()
-        errs.append(max(rel(qtt.qtt_decode(ctx, su), tt.full(u)), rel(qtt.qtt_decode(ctx, sv), tt.full(v))))
-    print("per-step max rel diff:", errs)
-    assert errs[0] < 1e-8
-    assert max(errs) < 1e-6
+    u, v, p = wake_state(ops, ne, nx, chi, seed)
+    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved")
+    case.set_state(*(qtt.MPS.from_cores(ctx, x) for x in (u, v, p)))
+    o = step_opts(chi, qtt)
+    for s in range(10):
+        info = case.fractional_step(1, check=False)
+        u, v, p, oi = S.step(ops, u, v, p, o)
+        same_solves(info[0], oi)
+        for g, r in zip(case.get_state(), (u, v, p)):
+            assert rel(qtt.qtt_decode(ctx, g), tt.full(r)) < TOL, (s, seed)
+
+
+def test_full_rank_12bit_step_matches_fd(ctx):
+    """Config 1 at full rank: 12 bits with chi = 64 (= 2^6, no truncation anywhere) and the solves
+    converged to their tolerance: three GPU steps equal three full-grid FD steps (L0) to 1e-10."""
+    from paper_2507_05222_gb300 import qtt
+    ne = nx = 6
+    R, Re, dt, chi = 40.0, 100.0, 2e-3, 64
+    ops = Q.Ops(ne, nx, R, Re, dt, "interleaved")
+    u0 = 1.0 + inputs.gaussian_field(ne, nx, 3, 1e-3)
+    v0 = inputs.gaussian_field(ne, nx, 4, 1e-3)
+    p = S.padded([np.zeros((1, 2, 1))] * (ne + nx), chi, inputs.random_cores(ne + nx, chi, 5, scale=1e-8))
+    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=2, mom=(8, 1e-14, 300, 1e-3, 0.0),
+                    poi=(10, 1e-13, 500, 1e-3, 0.0))
+    case.set_state(qtt.MPS.from_cores(ctx, ops.encode(u0, chi)), qtt.MPS.from_cores(ctx, ops.encode(v0, chi)),
+                   qtt.MPS.from_cores(ctx, p))
+    L0 = fd.FDSolver(fd.Case(fd.Grid(ne, nx, R), Re, dt))
+    u, v = u0, v0
+    for _ in range(3):
+        info = case.fractional_step(1)
+        assert all(info[0][k]["status"] == 0 for k in "uvp")
+        u, v, pf, _, _ = L0.step(u, v)
+    for g, r in zip(case.get_state(), (u, v, pf)):
+        r2 = Q.field_to_vec(np.reshape(r, (2 ** ne, 2 ** nx)), "interleaved")
+        assert rel(qtt.qtt_decode(ctx, g), r2) < 1e-10
 
 
 def test_graph_replay_equals_eager(ctx):
-    """The captured-graph step (default) and kernel-by-kernel launching give identical states
-    (same kernels, deterministic reductions), also after set_state re-captures."""
+    """The captured-graph step (default; the ALS sweep loops are conditional WHILE nodes whose
+    trip counts the device decides) and kernel-by-kernel launching (the host reads the loop flag)
+    give identical states and solve records (same kernels, deterministic reductions), also after
+    set_state re-captures."""
     from paper_2507_05222_gb300 import qtt
     ne = nx = 5
     R, Re, dt, chi = 40.0, 100.0, 2e-3, 16
@@ -150,11 +195,10 @@ def test_graph_replay_equals_eager(ctx):
     _, (gu, gv, gp), _ = make_state(ctx, ops, ne, nx, chi)
     out = []
     for graph in (True, False, True):
-        case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=1, mom=(1, 8, 1e-12),
-                        poi=(2, 20, 1e-12))
+        case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved")
         case.use_graph(graph)
         case.set_state(gu, gv, gp)
-        info = case.fractional_step(3, with_forces=True)
+        info = case.fractional_step(3, with_forces=True, check=False)
         out.append(([qtt.qtt_decode(ctx, x) for x in case.get_state()], info))
     for (a, ia), (b, ib) in ((out[0], out[1]), (out[2], out[1])):
         for x, y in zip(a, b):
@@ -165,10 +209,9 @@ def test_graph_replay_equals_eager(ctx):
 @pytest.mark.parametrize("ne,nx,chi", [(5, 5, 16), (6, 6, 64)])
 def test_cg_one_kernel_equals_per_stage(ctx, ne, nx, chi):
     """The local CG solves as one cooperative kernel give the per-stage kernels' iterates up to
-    rounding order: CG counts within one per step, states within the oracle parity bar (1e-10)
-    after one step (the step amplifies rounding differences ~1e3-fold: unconverged CG).  At
-    chi = 64 the grid runs several work items per CTA in both contraction stages (the momentum
-    solves run on half the SMs)."""
+    rounding order: the same sweep counts and stop decisions, states within the oracle parity
+    bar (1e-10) after one step.  At chi = 64 the grid runs several work items per CTA in both
+    contraction stages (the momentum solves run on half the SMs)."""
     from paper_2507_05222_gb300 import qtt
     R, Re, dt = 40.0, 100.0, 2e-3
     ops = Q.Ops(ne, nx, R, Re, dt, "interleaved")
@@ -177,26 +220,23 @@ def test_cg_one_kernel_equals_per_stage(ctx, ne, nx, chi):
     try:
         for mode in (0, 1):
             ctx.set_cg_mode(mode)
-            case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=1, mom=(1, 8, 1e-12),
-                            poi=(2, 20, 1e-12))
+            case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved")
             case.set_state(gu, gv, gp)
-            info = case.fractional_step(1, with_forces=False)
+            info = case.fractional_step(1, with_forces=False, check=False)
             out.append(([qtt.qtt_decode(ctx, x) for x in case.get_state()], info))
     finally:
         ctx.set_cg_mode(0)
     (a, ia), (b, ib) = out
     for x, y in zip(a, b):
         assert rel(x, y) < TOL
-    for i, j in zip(ia, ib):
-        for k in ("cg_u", "cg_v", "cg_p"):
-            assert abs(i[k] - j[k]) <= 1
+    for k in "uvp":
+        assert (ia[0][k]["sweeps"], ia[0][k]["status"]) == (ib[0][k]["sweeps"], ib[0][k]["status"])
 
 
 def test_tensor_core_products_equal_fp64_pipe(ctx):
     """A step whose large contractions (chi = 64: 4096 x 128 x 64 environment products) run on
     the tensor cores by digit splitting equals the same step with every product on the FP64
-    pipe, within the oracle parity bar after one step (plus the ~1e3-fold amplification of
-    rounding differences by unconverged CG that the one-kernel CG test measures)."""
+    pipe, within the oracle parity bar after one step, with the same sweep counts."""
     from paper_2507_05222_gb300 import qtt
     ne = nx = 6
     R, Re, dt, chi = 40.0, 100.0, 2e-3, 64
@@ -206,18 +246,17 @@ def test_tensor_core_products_equal_fp64_pipe(ctx):
     try:
         for mode in (0, 1):
             ctx.set_gemm_mode(mode)
-            case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=1, mom=(1, 8, 1e-12),
-                            poi=(2, 20, 1e-12))
+            case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved")
             case.set_state(gu, gv, gp)
-            info = case.fractional_step(1, with_forces=False)
+            info = case.fractional_step(1, with_forces=False, check=False)
             out.append(([qtt.qtt_decode(ctx, x) for x in case.get_state()], info))
     finally:
         ctx.set_gemm_mode(0)
     (a, ia), (b, ib) = out
     for x, y in zip(a, b):
-        assert rel(x, y) < 1e-9
-    for k in ("cg_u", "cg_v", "cg_p"):
-        assert abs(ia[0][k] - ib[0][k]) <= 2
+        assert rel(x, y) < TOL
+    for k in "uvp":
+        assert (ia[0][k]["sweeps"], ia[0][k]["status"]) == (ib[0][k]["sweeps"], ib[0][k]["status"])
 
 
 def smooth_field(ne, nx, seed, amp, modes):
@@ -247,11 +286,11 @@ def headline_state(ctx, chi=64):
 
 
 def test_headline_operations_match_oracle(ctx):
-    """The well-conditioned operations of the step at the timed size (2^20 cells, chi = 64):
-    MPO·MPS products with rounding, the Hadamard fit and a momentum-operator ALS solve, each
-    against the oracle on the same input.  The products are held to the Gram-rounding limit:
-    this state keeps singular values down to ~1e-14 sigma_1 in its bonds, and directions with
-    sigma below sqrt(eps) sigma_1 are not resolved by a Gram eigenproblem, which leaves ~1e-8
+    """The operations of the step at the timed size (2^20 cells, chi = 64), each against the
+    oracle on the same input: MPO·MPS products with rounding, the Hadamard fit, and a
+    momentum-operator ALS solve under the stop rule.  The products are held to the Gram-rounding
+    limit: this state keeps singular values down to ~1e-14 sigma_1 in its bonds, and directions
+    with sigma below sqrt(eps) sigma_1 are not resolved by a Gram eigenproblem, which leaves ~1e-8
     of the product (measured 5e-8 with tensor-core contractions, 1e-8 on the FP64 pipe)."""
     from paper_2507_05222_gb300 import qtt
     ops, (u, v, p) = headline_state(ctx)
@@ -263,39 +302,43 @@ def test_headline_operations_match_oracle(ctx):
     ref = tt.full(tt.hadamard_round(u, v, 64, sweeps=2))
     g = qtt.mps_hadamard_round(ctx, gu, gv, 64, sweeps=2)
     assert rel(qtt.qtt_decode(ctx, g), ref) < 1e-11
-    xr, cgr = tt.als(ops.H, [("vec", 1.0, u)], u, 1, 8, 1e-10)
+    opts = (3, 1e-10, 100, 1e-2, 0.1)
+    xr, ir = tt.als(ops.H, [("vec", 1.0, u)], u, opts[0], opts[2], opts[3], opts[1], opts[4])
     g = qtt.MPS.from_cores(ctx, u)
-    cg, _ = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.H), qtt.MPS.from_cores(ctx, u), g, 1, 8, 1e-10)
-    assert abs(cg - cgr) <= 2
-    assert rel(qtt.qtt_decode(ctx, g), tt.full(xr)) < 1e-6
+    gi = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.H), qtt.MPS.from_cores(ctx, u), g, *opts)
+    assert (gi["sweeps"], gi["status"]) == (ir["sweeps"], ir["status"])
+    assert abs(gi["rel_residual"] - ir["rel_residual"]) <= 1e-6 * ir["rel_residual"]
+    assert rel(qtt.qtt_decode(ctx, g), tt.full(xr)) < 1e-8
 
 
 def test_headline_step_matches_oracle(ctx):
     """One step of the timed workload (2^20 cells as 10 + 10 interleaved bits, chi = 64, Re = 200,
-    dt = 8e-4, R = 40, the solver budgets of bench.py) through the captured CUDA graph that
-    bench.py replays, against the oracle's step on the same state.  At this size the step is
-    ill-conditioned with respect to rounding: the Poisson ALS (2 sweeps of 20 unconverged CG
-    iterations per site on a 2^20-cell problem) amplifies a 2^-50 relative change of its initial
-    guess into percent-level changes of the result (the oracle's own step moves by ~1.5 % in u,
-    ~12 % in v, ~4 % in p).  So the bar is that rounding spread: the GPU may differ from the
-    oracle by at most three times what the oracle differs from itself under that perturbation;
-    the CG iteration counts agree within two and the forces are finite."""
+    dt = 8e-4, R = 40, the seeded wake state and the solve options bench.py times) through the
+    captured CUDA graph bench.py replays, against the oracle's step on the same state.  Every
+    solve runs to its stop rule, so the step is well conditioned: its sensitivity is measured here
+    as the change of the oracle's own step under a 2^-50 relative change of the initial pressure
+    (~1e-8 to 2e-7 per field).  The GPU may differ from the oracle by at most ten times that
+    spread (at least 1e-10); every solve takes the oracle's sweep count and stop decision."""
     from paper_2507_05222_gb300 import qtt
-    ops, (u, v, p) = headline_state(ctx)
+    ne = nx = 10
     chi = 64
-    case = qtt.Case(ctx, 10, 10, 40.0, 200.0, 8e-4, chi, "interleaved", fit_sweeps=1, mom=(1, 8, 1e-10),
-                    poi=(2, 20, 1e-10))
+    ops = Q.Ops(ne, nx, 40.0, 200.0, 8e-4, "interleaved")
+    u, v, p = wake_state(ops, ne, nx, chi, 7)
+    case = qtt.Case(ctx, ne, nx, 40.0, 200.0, 8e-4, chi, "interleaved")
     case.use_graph(True)
-    case.set_state(qtt.MPS.from_cores(ctx, u), qtt.MPS.from_cores(ctx, v), qtt.MPS.from_cores(ctx, p))
-    info = case.fractional_step(1, with_forces=True)
-    o = S.StepOpts(chi=chi, fit_sweeps=1, mom_sweeps=1, mom_cg=8, poi_sweeps=2, poi_cg=20, cg_tol=1e-10)
+    case.set_state(*(qtt.MPS.from_cores(ctx, x) for x in (u, v, p)))
+    info = case.fractional_step(1, with_forces=True, check=False)
+    o = step_opts(chi, qtt)
     ref = S.step(ops, u, v, p, o)
     pert = S.step(ops, u, v, [c * (1.0 + 2.0 ** -50) for c in p], o)
-    oi = ref[3]
-    assert abs(info[0]["cg_u"] - oi["cg_u"]) <= 2 and abs(info[0]["cg_v"] - oi["cg_v"]) <= 2
-    assert abs(info[0]["cg_p"] - oi["cg_p"]) <= 2
+    same_solves(info[0], ref[3])
+    spreads, diffs = [], []
     for g, r, q in zip(case.get_state(), ref[:3], pert[:3]):
         full_r = tt.full(r)
-        spread = rel(tt.full(q), full_r)
-        assert rel(qtt.qtt_decode(ctx, g), full_r) <= 3.0 * spread + 1e-10
-    assert np.isfinite(info[0]["cd"]) and np.isfinite(info[0]["cl"])
+        spreads.append(rel(tt.full(q), full_r))
+        diffs.append(rel(qtt.qtt_decode(ctx, g), full_r))
+    print("GPU - oracle:", diffs, "oracle spread:", spreads)
+    for d_, s_ in zip(diffs, spreads):
+        assert d_ <= max(10.0 * s_, 1e-10)
+    assert max(diffs) < 2e-6
+    assert info[0]["finite"] == 1 and np.isfinite(info[0]["cd"]) and np.isfinite(info[0]["cl"])

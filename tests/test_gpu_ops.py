@@ -111,6 +111,41 @@ def test_apply_random(ctx, n, bx, w, chi):
     assert rel(down(ctx, g), tt.full(ref)) < TOL
 
 
+def test_round_info_discarded_norm(ctx):
+    """qtt_round_info: the discarded norm of every rounding entry point equals the oracle's
+    TT-SVD value (which equals the true rounding error), and norm and max bond are the result's.
+    Gram (rel_tol = 0) and thresholded QR + SVD paths both; -1 for the Hadamard fit."""
+    from paper_2507_05222_gb300 import qtt
+    x = inputs.random_cores(10, 16, seed=5)
+    y = inputs.random_cores(10, 8, seed=6)
+    M = inputs.random_mpo_cores(10, 3, seed=7)
+    cases = [
+        (lambda info: qtt.qtt_round(ctx, up(ctx, x), 6, out_info=info), tt.full(x), x, 6),
+        (lambda info: qtt.mps_axpby_round(ctx, 0.7, up(ctx, x), -1.3, up(ctx, y), 10, out_info=info),
+         tt.full(tt.direct_sum(0.7, x, -1.3, y)), tt.direct_sum(0.7, x, -1.3, y), 10),
+        (lambda info: qtt.mpo_apply_round(ctx, qtt.MPO.from_cores(ctx, M), up(ctx, x), 12, out_info=info),
+         tt.full(tt.mpo_mps(M, x)), tt.mpo_mps(M, x), 12),
+        (lambda info: qtt.qtt_encode(ctx, tt.full(x), 10, 8, out_info=info), tt.full(x), x, 8),
+    ]
+    for call, exact, cores, chi in cases:
+        info = {}
+        g = call(info)
+        ref = {}
+        r = tt.round_tt(cores, chi, info=ref)
+        assert abs(info["discarded_norm"] - ref["discarded_norm"]) <= 1e-9 * np.linalg.norm(exact)
+        assert abs(info["discarded_norm"] - np.linalg.norm(exact - down(ctx, g))) <= 1e-9 * np.linalg.norm(exact)
+        assert abs(info["norm"] - np.linalg.norm(tt.full(r))) <= 1e-12 * np.linalg.norm(tt.full(r))
+        assert info["max_bond"] == max(tt.bonds(r))
+    info = {}
+    a = Q.mps1_trig(9, 0.1, 0.0, "sin"); b = Q.mps1_trig(9, 0.1, 0.3, "cos")
+    s = tt.direct_sum(1.0, a, 2.0, b)
+    qtt.qtt_round(ctx, up(ctx, s), 100, rel_tol=1e-14, out_info=info)
+    assert info["max_bond"] == 2 and info["discarded_norm"] <= 1e-13 * np.linalg.norm(tt.full(s))
+    info = {}
+    qtt.mps_hadamard_round(ctx, up(ctx, y), up(ctx, y), 8, out_info=info)
+    assert info["discarded_norm"] == -1.0
+
+
 @pytest.mark.parametrize("ordering", ["interleaved", "sequential"])
 def test_apply_fd_operator_exact(ctx, ordering):
     """Curvilinear D_x of a smooth field without truncation equals the dense product."""
@@ -159,22 +194,28 @@ def cg_mode(ctx, request):
 
 
 def test_poisson_solve_matches_oracle_als(ctx, cg_mode):
-    """ALS (Sec. II.A.4) with the same sweeps / CG budget as the oracle."""
+    """ALS (Sec. II.A.4) under the true-residual stop rule, same options as the oracle: the same
+    sweep count, status and CG count, the residual to 1e-8 of itself, the solution at 1e-10."""
     from paper_2507_05222_gb300 import qtt
     ne, nx = 4, 4
     ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, "interleaved")
     n = ne + nx
     b = inputs.random_cores(n, 4, seed=80)
     x0 = inputs.random_cores(n, 8, seed=81, scale=0.1)
-    ref, cg_ref = tt.als(ops.Ap, [("vec", 1.0, b)], x0, sweeps=2, cg_iters=15, cg_tol=1e-12)
+    opts = (8, 1e-10, 200, 1e-2, 0.1)
+    ref, ir = tt.als(ops.Ap, [("vec", 1.0, b)], x0, *opts[:1], opts[2], opts[3], opts[1], opts[4])
     g = up(ctx, x0)
-    cg, res = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.Ap), up(ctx, b), g, 2, 15, 1e-12)
-    assert cg == cg_ref
-    assert rel(down(ctx, g), tt.full(ref)) < 1e-9
+    gi = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.Ap), up(ctx, b), g, *opts)
+    assert (gi["sweeps"], gi["status"]) == (ir["sweeps"], ir["status"])
+    assert abs(gi["cg_iters"] - ir["cg_iters"]) <= 2
+    assert abs(gi["rel_residual"] - ir["rel_residual"]) <= 1e-8 * ir["rel_residual"]
+    assert gi["rc"] == (0 if ir["status"] == tt.CONVERGED else -4)
+    assert rel(down(ctx, g), tt.full(ref)) < TOL
 
 
 def test_poisson_solve_full_rank_exact(ctx, cg_mode):
-    """At full bond dimension the ALS solution equals the dense solve (J-weighted Poisson)."""
+    """At full bond dimension the ALS solution equals the dense solve (J-weighted Poisson) and the
+    solve stops as converged on its true residual."""
     from paper_2507_05222_gb300 import qtt
     ne, nx = 3, 4
     ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, "interleaved")
@@ -182,19 +223,54 @@ def test_poisson_solve_full_rank_exact(ctx, cg_mode):
     b = inputs.random_cores(n, 4, seed=82)
     x0 = inputs.random_cores(n, 16, seed=83, scale=0.1)
     g = up(ctx, x0)
-    cg, res = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.Ap), up(ctx, b), g, 6, 300, 1e-15)
+    gi = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.Ap), up(ctx, b), g, 10, 1e-12, 300, 1e-3, 0.0)
     ref = np.linalg.solve(tt.full_mpo(ops.Ap), tt.full(b))
-    assert rel(down(ctx, g), ref) < 1e-10
-    assert res < 1e-10
+    assert gi["status"] == 0 and gi["rc"] == 0 and gi["rel_residual"] <= 1e-12
+    A = tt.full_mpo(ops.Ap)
+    x = down(ctx, g)
+    assert abs(gi["rel_residual"] - np.linalg.norm(A @ x - tt.full(b)) / np.linalg.norm(tt.full(b))) < 1e-14
+    assert rel(x, ref) < 1e-10
+
+
+def test_poisson_solve_statuses(ctx):
+    """Stop-rule outcomes through the C ABI: out of sweeps returns QTT_ERR_NOT_CONVERGED with the
+    last iterate (equal to the oracle's after the same sweeps); a stall at the bond's floor
+    likewise; a start at the solution takes no sweep; max_sweeps = 0 returns the warm start."""
+    from paper_2507_05222_gb300 import qtt
+    ne = nx = 4
+    ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, "interleaved")
+    n = ne + nx
+    rhs = inputs.random_cores(n, 16, seed=35)
+    x0 = inputs.random_cores(n, 4, seed=36, scale=0.1)
+    A = qtt.MPO.from_cores(ctx, ops.Ap)
+    g = up(ctx, x0)
+    gi = qtt.poisson_solve(ctx, A, up(ctx, rhs), g, 2, 1e-14, 500, 1e-3, 0.0)
+    ref, ir = tt.als(ops.Ap, [("vec", 1.0, rhs)], x0, 2, 500, 1e-3, 1e-14, 0.0)
+    assert gi["rc"] == -4 and gi["status"] == 2 == ir["status"] and gi["sweeps"] == 2
+    assert rel(down(ctx, g), tt.full(ref)) < TOL
+    with pytest.raises(qtt.QttError) as e:
+        qtt.poisson_solve(ctx, A, up(ctx, rhs), up(ctx, x0), 2, 1e-14, 500, 1e-3, 0.0, check=True)
+    assert e.value.code == -4
+    g = up(ctx, x0)
+    gi = qtt.poisson_solve(ctx, A, up(ctx, rhs), g, 30, 1e-12, 500, 1e-3, 0.05)
+    ref, ir = tt.als(ops.Ap, [("vec", 1.0, rhs)], x0, 30, 500, 1e-3, 1e-12, 0.05)
+    assert gi["status"] == 1 == ir["status"] and gi["sweeps"] == ir["sweeps"] and gi["rc"] == -4
+    assert rel(down(ctx, g), tt.full(ref)) < TOL
+    xe = tt.tt_svd(np.linalg.solve(tt.full_mpo(ops.Ap), tt.full(rhs)), n, 2, 256)
+    g = up(ctx, xe)
+    gi = qtt.poisson_solve(ctx, A, up(ctx, rhs), g, 5, 1e-10, 10, 1e-3, 0.1)
+    assert gi["status"] == 0 and gi["sweeps"] == 0 and gi["cg_iters"] == 0 and gi["rc"] == 0
+    g = up(ctx, x0)
+    gi = qtt.poisson_solve(ctx, A, up(ctx, rhs), g, 0, 1e-10, 10, 1e-3, 0.1)
+    assert gi["status"] == 2 and gi["sweeps"] == 0 and rel(down(ctx, g), tt.full(x0)) < 1e-14
 
 
 def test_poisson_solve_tensor_core_cg_equals_fp64(ctx):
     """ALS local solves at bonds 64 (n = 12, the middle sites hold 64 x 2 x 64 cores): the
     cooperative CG with both contractions as digit-split tensor-core products (mode 3) against
     the same kernel structure on the FP64 pipe (mode 2), the per-stage kernels (mode 1) and the
-    default mix (mode 0: tensor cores at the full-bond sites).
-    The CG runs unconverged to its budget, so the results agree to the rounding-order level
-    amplified by the solve (~1e3), and the iteration counts agree."""
+    default mix (mode 0: tensor cores at the full-bond sites), each solve run to its true-residual
+    stop rule: the same sweep counts and statuses, solutions within 1e-10."""
     from paper_2507_05222_gb300 import qtt
     ne, nx = 6, 6
     ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, "interleaved")
@@ -206,16 +282,17 @@ def test_poisson_solve_tensor_core_cg_equals_fp64(ctx):
         for mode in (3, 2, 1, 0):
             ctx.set_cg_mode(mode)
             g = up(ctx, x0)
-            cg, res = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.Ap), up(ctx, b), g, 2, 20, 1e-12)
-            out.append((down(ctx, g), cg, res))
+            gi = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.Ap), up(ctx, b), g, 8, 1e-11, 300, 1e-2, 0.1)
+            out.append((down(ctx, g), gi))
     finally:
         ctx.set_cg_mode(0)
-    (x_tc, cg_tc, r_tc), (x_64, cg_64, r_64), (x_ps, cg_ps, r_ps), (x_d, cg_d, r_d) = out
+    (x_tc, i_tc), (x_64, i_64), (x_ps, i_ps), (x_d, i_d) = out
     assert rel(x_64, x_ps) < 1e-10
     assert rel(x_tc, x_64) < 1e-10
     assert rel(x_d, x_64) < 1e-10
-    assert abs(cg_tc - cg_64) <= 2 and abs(cg_64 - cg_ps) <= 2 and abs(cg_d - cg_64) <= 2
-    assert abs(r_tc - r_64) <= 1e-6 * r_64
+    for i in (i_tc, i_ps, i_d):
+        assert (i["sweeps"], i["status"]) == (i_64["sweeps"], i_64["status"])
+        assert abs(i["rel_residual"] - i_64["rel_residual"]) <= 1e-6 * i_64["rel_residual"] + 1e-14
 
 
 def test_field_reorder(ctx):

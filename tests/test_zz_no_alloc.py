@@ -6,6 +6,7 @@ next.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
+from oracle import tt
 from paper_2507_05222_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -23,9 +24,12 @@ def test_noalloc_dot_matches_mps_dot_twice():
     from paper_2507_05222_gb300 import qtt
     ctx = qtt.Context(0)
     stream = torch.cuda.current_stream().cuda_stream
-    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    full = [1, 4, 16, 64, 128, 128, 128, 128, 64, 16, 4, 1]     # d = 4, bonds at the 128 limit
     cases = [(inputs.random_cores(12, 24, seed=101), inputs.random_cores(12, 17, seed=102)),
-             (inputs.random_cores(12, 9, seed=103), inputs.random_cores(12, 128, seed=104, scale=0.1))]
+             (inputs.random_cores(12, 9, seed=103), inputs.random_cores(12, 128, seed=104, scale=0.1)),
+             (inputs.random_cores(11, 128, seed=105, d=4, bonds=full, scale=0.1),
+              inputs.random_cores(11, 128, seed=106, d=4, bonds=full, scale=0.1))]
+    out = torch.zeros(len(cases), dtype=torch.float64, device="cuda")
     keep = []
     for i, (a, b) in enumerate(cases):
         da, db = _dev(torch, a), _dev(torch, b)
@@ -34,7 +38,8 @@ def test_noalloc_dot_matches_mps_dot_twice():
         bb = [b[0].shape[0]] + [c.shape[2] for c in b]
         torch.cuda.synchronize()
         free_before = torch.cuda.mem_get_info()[0]
-        qtt.mps_dot_noalloc(12, 2, ab, da.data_ptr(), bb, db.data_ptr(), out.data_ptr() + 8 * i, stream)
+        n, d = len(a), a[0].shape[1]
+        qtt.mps_dot_noalloc(n, d, ab, da.data_ptr(), bb, db.data_ptr(), out.data_ptr() + 8 * i, stream)
         torch.cuda.synchronize()
         assert torch.cuda.mem_get_info()[0] == free_before
         ref = qtt.mps_dot(ctx, qtt.MPS.from_cores(ctx, a), qtt.MPS.from_cores(ctx, b))
@@ -42,6 +47,7 @@ def test_noalloc_dot_matches_mps_dot_twice():
         na = np.sqrt(qtt.mps_dot(ctx, qtt.MPS.from_cores(ctx, a), qtt.MPS.from_cores(ctx, a)))
         nb = np.sqrt(qtt.mps_dot(ctx, qtt.MPS.from_cores(ctx, b), qtt.MPS.from_cores(ctx, b)))
         assert abs(got - ref) <= 1e-12 * na * nb
+        assert abs(got - tt.dot(a, b)) <= 1e-12 * na * nb      # the FP64 oracle's overlap
 
 
 def test_noalloc_rejects_bond_above_limit():
