@@ -25,6 +25,19 @@ namespace qtt {
 
 namespace {
 
+// Descending order with ties broken by index, NaN placed after every number: a strict total
+// order, so the rank-counting sorts below always produce a permutation (with NaN values
+// compared plainly, every comparison is false and several entries would share one rank).
+__device__ __forceinline__ bool sort_before(double a, int ia, double b, int ib) {
+  const bool na = isnan(a), nb = isnan(b);
+  if (na || nb) return (na == nb) ? ia < ib : nb;
+  return a > b || (a == b && ia < ib);
+}
+
+}  // namespace
+
+namespace {
+
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -500,7 +513,7 @@ __global__ void __launch_bounds__(256) k_svd_jacobi(int m, int n, const double* 
   for (int c = tid; c < n; c += nt) {
     int rank = 0;
     for (int o = 0; o < n; ++o)
-      if (nrm[o] > nrm[c] || (nrm[o] == nrm[c] && o < c)) ++rank;
+      if (sort_before(nrm[o], o, nrm[c], c)) ++rank;
     order[rank] = c;
   }
   __syncthreads();
@@ -755,7 +768,7 @@ __global__ void __launch_bounds__(1024) k_sort_eig(int n, const double* __restri
   for (int c = tid; c < n; c += nt) {
     int rank = 0;
     for (int o = 0; o < n; ++o)
-      if (lam[o] > lam[c] || (lam[o] == lam[c] && o < c)) ++rank;
+      if (sort_before(lam[o], o, lam[c], c)) ++rank;
     ord[rank] = c;
   }
   __syncthreads();

@@ -496,6 +496,31 @@ def test_forces_closed_forms():
     assert abs(cl + np.pi * g.D) < 1e-12 and abs(cd) < 1e-12
 
 
+def test_forces_viscous_closed_form():
+    """App. F / eq:liftdrag, viscous part: for u = c (r - r_w), v = 0 (zero on the wall, no
+    pressure) the wall stress sigma = -(2/(3Re)) div v I + (1/Re)(grad v + grad v^T) has
+    traction t_x = (c/Re)((4/3) cos^2 + sin^2) on the outward normal, so C_D = 2 (7/3) pi c r_w / Re
+    and C_L = 0; the same field in v gives that C_L and C_D = 0.  The one-sided second-order wall
+    derivative converges to it at second order (a wrong factor, sign or a dropped divergence
+    term changes the limit by 15-60 %)."""
+    Re, c = 100.0, 0.7
+    errs = []
+    for n in (6, 7, 8):
+        g = fd.Grid(n, 6, 40.0)
+        case = fd.Case(g, Re, 2e-3)
+        rr, _ = g.nodes()
+        rw = g.r(-1)
+        f = c * (rr - rw)
+        z = np.zeros_like(f)
+        want = 2 * (7 / 3) * np.pi * c * rw / Re
+        cd, cl = fd.forces(case, f, z, z)
+        cd2, cl2 = fd.forces(case, z, f, z)
+        assert abs(cl) < 1e-15 and abs(cd2) < 1e-15
+        assert abs(cl2 - cd) <= 1e-14 * abs(cd)
+        errs.append(abs(cd / want - 1))
+    assert errs[0] < 2e-3 and errs[1] < errs[0] / 3.5 and errs[2] < errs[1] / 3.5
+
+
 def test_strouhal_from_zero_crossings():
     """eq:st: St = f D / U from the lift oscillation."""
     t = np.arange(0, 50, 0.013)
