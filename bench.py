@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 
 # Solve options (max_sweeps, rel_tol, cg_max_iter, cg_tol, stall): the stop rule of include/qtt.h.
 WORKLOAD = dict(workload="cylinder_qtt_step_2^20_chi64", n_eta=10, n_xi=10, ordering="interleaved", R=40.0,
-                Re=200.0, dt=8e-4, chi=64, fit_sweeps=1, mom=(6, 1e-10, 100, 1e-2, 0.1),
+                Re=200.0, dt=8e-4, chi=64, fit_sweeps=1, mom=(6, 1e-8, 100, 1e-2, 0.1),
                 poi=(12, 1e-10, 500, 1e-2, 0.1), seed=7)
 METRIC = "QTT fractional steps/s at 2^20 cells, chi=64, fixed oracle error; % TC/HBM roof"
 # FP64 ALU peak: 152 SMs x 2 FP64 FMA per clock (measured per SM) x 2 flops x 2.07 GHz.

@@ -40,7 +40,7 @@ class SolveOpts:
 class StepOpts:
     chi: int
     fit_sweeps: int = 1
-    mom: SolveOpts = field(default_factory=lambda: SolveOpts(6, 1e-10, 100))
+    mom: SolveOpts = field(default_factory=lambda: SolveOpts(6, 1e-8, 100))
     poi: SolveOpts = field(default_factory=lambda: SolveOpts(12, 1e-10, 500))
 
 

@@ -77,7 +77,7 @@ def solve_opts(max_sweeps: int, rel_tol: float, cg_max_iter: int, cg_tol: float 
 
 
 # Step defaults (the oracle's StepOpts has the same): momentum and Poisson solve options.
-MOM_DEFAULT = (6, 1e-10, 100, 1e-2, 0.1)
+MOM_DEFAULT = (6, 1e-8, 100, 1e-2, 0.1)
 POI_DEFAULT = (12, 1e-10, 500, 1e-2, 0.1)
 
 

