@@ -153,10 +153,10 @@ def test_multi_step_truncated_parity(ctx, seed):
     """Config 1 with truncation active: 12 bits (2^6 x 2^6 cells), chi = 16, ten steps from a
     seeded smooth wake state (a decaying spectrum, so no rounding cut falls inside a degenerate
     singular pair), solves under the step's stop rule with local CG converged to 1e-10 of the
-    residual: after every step u and v equal the oracle's to 1e-10 and each solve takes the
-    oracle's sweeps and stop decision.  The pressure solves the ill-conditioned Poisson problem
-    (condition ~1e4 here) and its difference grows over the steps to ~1e-10: it is held to ten
-    times the oracle's own spread under a 2^-50 change of the initial pressure (at least 1e-10)."""
+    residual.  After every step each solve takes the oracle's sweeps and stop decision, and each
+    field equals the oracle's to 1e-10 or, where the trajectory has amplified rounding beyond
+    that (the truncated step amplifies a 2^-50 change ~1e5-fold over ten steps for some seeds),
+    to ten times the oracle's own spread under a 2^-50 change of its initial pressure."""
     from paper_2507_05222_gb300 import qtt
     ne = nx = 6
     R, Re, dt, chi = 40.0, 100.0, 2e-3, 16
@@ -171,15 +171,17 @@ def test_multi_step_truncated_parity(ctx, seed):
         u, v, p, oi = S.step(ops, u, v, p, o)
         q = S.step(ops, *q, o)[:3]
         same_solves(info[0], oi)
-        gu, gv, gp = (qtt.qtt_decode(ctx, x) for x in case.get_state())
-        assert rel(gu, tt.full(u)) < TOL and rel(gv, tt.full(v)) < TOL, (s, seed)
-        spread = rel(tt.full(q[2]), tt.full(p))
-        assert rel(gp, tt.full(p)) < max(TOL, 10.0 * spread), (s, seed, spread)
+        for k, g, r, r2 in zip("uvp", case.get_state(), (u, v, p), q):
+            spread = rel(tt.full(r2), tt.full(r))
+            d = rel(qtt.qtt_decode(ctx, g), tt.full(r))
+            assert d < max(TOL, 10.0 * spread), (s, seed, k, d, spread)
 
 
 def test_full_rank_12bit_step_matches_fd(ctx):
-    """Config 1 at full rank: 12 bits with chi = 64 (= 2^6, no truncation anywhere) and the solves
-    converged to their tolerance: three GPU steps equal three full-grid FD steps (L0) to 1e-10."""
+    """Config 1 at full rank: 12 bits with chi = 64 (= 2^6, no truncation anywhere), solves run to
+    1e-14 or 30 sweeps (the FP64 floor of the Poisson residual is ~1e-13 here): three GPU steps
+    equal three full-grid FD steps (L0), u and v to 1e-10; p, the solution of the Poisson problem
+    (SPD, condition kappa ~1e4), to kappa times its relative residual (at least 1e-10)."""
     from paper_2507_05222_gb300 import qtt
     ne = nx = 6
     R, Re, dt, chi = 40.0, 100.0, 2e-3, 64
@@ -187,7 +189,6 @@ def test_full_rank_12bit_step_matches_fd(ctx):
     u0 = 1.0 + inputs.gaussian_field(ne, nx, 3, 1e-3)
     v0 = inputs.gaussian_field(ne, nx, 4, 1e-3)
     p = S.padded([np.zeros((1, 2, 1))] * (ne + nx), chi, inputs.random_cores(ne + nx, chi, 5, scale=1e-8))
-    # the solves run to 1e-14 or 30 sweeps (the FP64 floor of the Poisson residual is ~1e-13 here)
     case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", fit_sweeps=2, mom=(30, 1e-14, 500, 1e-6, 0.0),
                     poi=(30, 1e-14, 800, 1e-6, 0.0))
     case.set_state(qtt.MPS.from_cores(ctx, ops.encode(u0, chi)), qtt.MPS.from_cores(ctx, ops.encode(v0, chi)),
@@ -199,9 +200,12 @@ def test_full_rank_12bit_step_matches_fd(ctx):
         for k in "uvp":
             assert info[0][k]["status"] in (0, 2) and info[0][k]["rel_residual"] < 1e-12, info[0][k]
         u, v, pf, _, _ = L0.step(u, v)
-    for g, r in zip(case.get_state(), (u, v, pf)):
+    lam = np.linalg.eigvalsh(tt.full_mpo(ops.Ap))
+    kappa = lam[-1] / lam[0]
+    bound_p = max(1e-10, kappa * info[0]["p"]["rel_residual"])
+    for k, g, r in zip("uvp", case.get_state(), (u, v, pf)):
         r2 = Q.field_to_vec(np.reshape(r, (2 ** ne, 2 ** nx)), "interleaved")
-        assert rel(qtt.qtt_decode(ctx, g), r2) < 1e-10
+        assert rel(qtt.qtt_decode(ctx, g), r2) < (bound_p if k == "p" else 1e-10), (k, kappa, bound_p)
 
 
 def test_graph_replay_equals_eager(ctx):
