@@ -217,7 +217,23 @@ def run_ours(args, cfg):
         print(json.dumps({"graph_phase_ms": graph_phases, "eager_phase_ms": case.phase_ms(),
                           "eager_kernel_ms_by_phase": ctx.profile_phases()}))
         return
+    if args.cg_probe:
+        # one Poisson ALS solve of the workload's pressure operator with the timed options, launched
+        # kernel by kernel between cudaProfilerStart/Stop: every CG launch is a caller-stream solve
+        # (one CTA per SM), the full-bond sites in the middle of each sweep
+        A = case.operator(5)
+        rhs = qtt.mpo_apply_round(ctx, case.operator(6), gu, chi)
+        x = gp.copy()
+        qtt.poisson_solve(ctx, A, rhs, x.copy(), 1, 1e-10, cfg["poi"][2], cfg["poi"][3], cfg["poi"][4])
+        ctx.sync()
+        qtt.profiler_range(True)
+        qtt.poisson_solve(ctx, A, rhs, x, 2, 1e-10, cfg["poi"][2], cfg["poi"][3], cfg["poi"][4])
+        ctx.sync()
+        qtt.profiler_range(False)
+        return
     if args.profile_one_step:
+        if args.eager:
+            case.use_graph(False)
         qtt.fractional_step(ctx, case, 1, check=False)
         ctx.sync()
         qtt.profiler_range(True)
@@ -365,6 +381,76 @@ def run_ours(args, cfg):
         dist.destroy_process_group()
 
 
+def kernel_sweep(args):
+    """Config-2 kernel sweep: y = round_chi(M x) for random normalised MPS x of L = 20 sites
+    (N(0, 1) cores, bond profile min(2^k, 2^(20-k), chi), seeds 0..9) and the FD gradient and
+    Laplacian MPOs of the 2^10 x 2^10 case (D_x and the weighted Poisson operator A_p), for each
+    chi: microseconds per product (CUDA events, median over the seeds, L2 flushed between
+    products), the discarded norm against the oracle's TT-SVD value, and the reconstructed
+    product against the oracle's on a sample of entries (random MPS have flat spectra, so the
+    rounding cuts fall between nearly equal singular values and only the discarded norm is
+    pinned there).  Prints one JSON line per (operator, chi)."""
+    import torch
+    from paper_2507_05222_gb300 import inputs, qtt
+    from oracle import tt
+    torch.cuda.set_device(0)
+    ctx = qtt.Context(0)
+    case = qtt.Case(ctx, 10, 10, 40.0, 200.0, 8e-4, 16, "interleaved")
+    ops = {"D_x": case.operator(0), "A_p": case.operator(5)}
+    flush = torch.empty(int(256 * 2 ** 20 // 4), dtype=torch.float32, device="cuda")
+    n = 20
+    rows = []
+    for name, M in ops.items():
+        Mc = M.cores()
+        for chi in args.sweep_chi:
+            times, disc, dref, par = [], [], [], []
+            for seed in range(args.sweep_seeds):
+                x = inputs.random_cores(n, chi, seed)
+                nrm = np.sqrt(tt.dot(x, x))
+                x = [x[0] / nrm] + x[1:]
+                gx = qtt.MPS.from_cores(ctx, x)
+                qtt.mpo_apply_round(ctx, M, gx, chi)          # warm-up (kernel attributes, pool)
+                flush.fill_(float(seed))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(ctx.stream)
+                y = qtt.mpo_apply_round(ctx, M, gx, chi)
+                e1.record(ctx.stream)
+                torch.cuda.synchronize()
+                times.append(1e3 * e0.elapsed_time(e1))
+                info = {}
+                qtt.mpo_apply_round(ctx, M, gx, chi, out_info=info)
+                disc.append(info["discarded_norm"])
+                if seed < args.sweep_oracle_seeds:
+                    ref_info = {}
+                    yr = tt.round_tt(tt.mpo_mps(Mc, x), chi, info=ref_info)
+                    dref.append(ref_info["discarded_norm"])
+                    # sampled entries of both reconstructions (2^20 entries: 4096 sampled indices)
+                    idx = inputs.rng(1000 + seed).integers(0, 2 ** n, 4096)
+                    yc = y.cores()
+
+                    def entries(cores):
+                        out = np.empty(len(idx))
+                        for j, q in enumerate(idx):
+                            v = np.ones(1)
+                            for k, c in enumerate(cores):
+                                v = v @ c[:, (q >> (n - 1 - k)) & 1, :]
+                            out[j] = v[0]
+                        return out
+                    a, b = entries(yc), entries(yr)
+                    par.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+            line = {"kernel_sweep": "mpo_apply_round", "operator": name, "L": n, "chi": chi,
+                    "operator_max_bond": max(M.bonds()), "seeds": args.sweep_seeds,
+                    "us_per_product_median": float(np.median(times)), "us_per_product_min": float(min(times)),
+                    "discarded_norm_median": float(np.median(disc)),
+                    "discarded_norm_vs_oracle_max_rel": (max(abs(d - r) / r for d, r in zip(disc, dref))
+                                                         if dref else None),
+                    "sampled_entries_vs_oracle_max_rel": max(par) if par else None,
+                    "oracle_seeds": len(dref)}
+            rows.append(line)
+            print(json.dumps(line), flush=True)
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,12 +463,25 @@ def main():
     ap.add_argument("--chi", type=int, default=None)
     ap.add_argument("--profile-one-step", action="store_true",
                     help="set up, one warm-up step, then one step between cudaProfilerStart/Stop (for ncu)")
-    ap.add_argument("--gemm-mode", type=int, default=None, choices=(0, 1),
-                    help="0: large products on the tensor cores (digit-split FP64); 1: FP64 pipe")
+    ap.add_argument("--gemm-mode", type=int, default=None, choices=(0, 1, 2, 3),
+                    help="0: large products on the tensor cores (digit-split FP64, default kernel); 1: FP64 pipe; "
+                         "2: digit products on mma.sync; 3: digit products on tcgen05")
     ap.add_argument("--cg-mode", type=int, default=None, choices=(0, 1, 2, 3),
                     help="ALS local solves: 0 one cooperative kernel, tensor-core contractions at full-bond sites "
                          "(default); 1 one kernel per stage; 2 one FP64 cooperative kernel; 3 tensor cores wherever "
                          "the cooperative kernel fits")
+    ap.add_argument("--cg-probe", action="store_true",
+                    help="set up, then one Poisson solve launched kernel by kernel between cudaProfilerStart/Stop "
+                         "(for ncu captures of the CG kernel)")
+    ap.add_argument("--kernel-sweep", action="store_true",
+                    help="config-2 sweep: mpo_apply_round on random 20-site MPS, chi in --sweep-chi (one JSON line "
+                         "per operator and chi; no bench line)")
+    ap.add_argument("--sweep-chi", type=int, nargs="+", default=[16, 32, 64])
+    ap.add_argument("--sweep-seeds", type=int, default=10)
+    ap.add_argument("--sweep-oracle-seeds", type=int, default=2)
+    ap.add_argument("--eager", action="store_true",
+                    help="with --profile-one-step: launch the step kernel by kernel (ncu cannot profile kernel "
+                         "nodes of graphs with conditional nodes)")
     ap.add_argument("--phase-breakdown", action="store_true",
                     help="print kernel-class time by step phase (diagnostic; no bench line)")
     ap.add_argument("--kernel-probe", action="store_true",
@@ -393,6 +492,9 @@ def main():
         cfg.update(n_eta=args.n, n_xi=args.n, workload=f"cylinder_qtt_step_2^{2 * args.n}_chi{args.chi or cfg['chi']}")
     if args.chi is not None:
         cfg.update(chi=args.chi, workload=f"cylinder_qtt_step_2^{cfg['n_eta'] + cfg['n_xi']}_chi{args.chi}")
+    if args.kernel_sweep:
+        kernel_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args, cfg)
     else:

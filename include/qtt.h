@@ -260,13 +260,15 @@ int qtt_sym_eig(qtt_ctx* ctx, int n, const double* S, double* w, double* V);
 int qtt_qr(qtt_ctx* ctx, int m, int n, int trans, const double* A, double* Q, double* R, int path);
 /* C = A B for row-major host matrices A (m x k), B (k x n), C (m x n); synchronous.  The product
  * behind every core contraction of the sweeps (Sec. II.A).  path 0 uses the context's mode (see
- * qtt_ctx_set_gemm_mode), 1 forces the FP64 pipe, 2 forces the tensor-core product: every row
+ * qtt_ctx_set_gemm_mode), 1 forces the FP64 pipe, 2 and 3 force the tensor-core product: every row
  * of A and column of B is split into seven 8-bit digits scaled by a power of two, digit products
  * are summed exactly in FP32 on the bf16 tensor cores and combined in FP64 (Ozaki scheme; error
- * ~2^-53 max_k|A_ik| sum_k|B_kj|). */
+ * ~2^-53 max_k|A_ik| sum_k|B_kj|) -- with warp-level mma.sync (2) or with tcgen05.mma on
+ * TMA-staged tiles and tensor-memory accumulators (3); both give bit-identical results. */
 int qtt_dgemm(qtt_ctx* ctx, int m, int n, int k, const double* A, const double* B, double* C, int path);
 /* Matrix products of the whole library: mode 0 (default) sends products of at least 2^23
- * multiply-adds to the tensor cores (digit-split FP64), mode 1 keeps every product on the FP64 pipe.
+ * multiply-adds to the tensor cores (digit-split FP64), mode 1 keeps every product on the FP64
+ * pipe, modes 2 and 3 are mode 0 with the digit products on mma.sync (2) or tcgen05 (3).
  * Takes effect for work enqueued afterwards (a captured step keeps its kernels). */
 int qtt_ctx_set_gemm_mode(qtt_ctx* ctx, int mode);
 /* Self-check of the QR's Householder scalars: the maximum relative errors of its Newton-Raphson

@@ -583,13 +583,21 @@ int qtt_dgemm(qtt_ctx* ctx, int m, int n, int k, const double* A, const double* 
   QTT_CHECK_ARG(m >= 1 && n >= 1 && k >= 1 && int64_t(m) * k <= (int64_t(1) << 26) &&
                     int64_t(k) * n <= (int64_t(1) << 26) && int64_t(m) * n <= (int64_t(1) << 26),
                 "dgemm: sizes must be >= 1 with each operand at most 2^26 values");
-  QTT_CHECK_ARG(path >= 0 && path <= 2, "dgemm: path must be 0, 1 or 2");
+  QTT_CHECK_ARG(path >= 0 && path <= 3, "dgemm: path must be 0, 1, 2 or 3");
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   DBuf dA(&c, size_t(m) * k), dB(&c, size_t(k) * n), dC(&c, size_t(m) * n);
   QTT_CUDA(cudaMemcpyAsync(dA.p, A, size_t(m) * k * sizeof(double), cudaMemcpyHostToDevice, c.stream));
   QTT_CUDA(cudaMemcpyAsync(dB.p, B, size_t(k) * n * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-  if (path == 2) {
-    gemm_ozaki(c, 1, m, n, k, 1.0, dA.p, 0, k, 1, dB.p, 0, n, 1, 0.0, dC.p, 0, n, 1);
+  if (path >= 2) {
+    const int saved = c.gemm_mode;
+    c.gemm_mode = path;          // 2: digit products on mma.sync, 3: on tcgen05
+    try {
+      gemm_ozaki(c, 1, m, n, k, 1.0, dA.p, 0, k, 1, dB.p, 0, n, 1, 0.0, dC.p, 0, n, 1);
+    } catch (...) {
+      c.gemm_mode = saved;
+      throw;
+    }
+    c.gemm_mode = saved;
   } else {
     const int saved = c.gemm_mode;
     if (path == 1) c.gemm_mode = 1;
@@ -609,7 +617,9 @@ int qtt_dgemm(qtt_ctx* ctx, int m, int n, int k, const double* A, const double* 
 int qtt_ctx_set_gemm_mode(qtt_ctx* ctx, int mode) {
   API_BEGIN
   QTT_CHECK_ARG(ctx, "ctx is null");
-  QTT_CHECK_ARG(mode == 0 || mode == 1, "gemm mode must be 0 (tensor cores for large products) or 1 (FP64 pipe)");
+  QTT_CHECK_ARG(mode >= 0 && mode <= 3,
+                "gemm mode must be 0 (tensor cores for large products), 1 (FP64 pipe), 2 (digit products on "
+                "mma.sync) or 3 (digit products on tcgen05)");
   reinterpret_cast<Ctx*>(ctx)->gemm_mode = mode;
   API_END
 }

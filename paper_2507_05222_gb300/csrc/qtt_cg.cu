@@ -856,7 +856,7 @@ struct TcPlan {
 };
 
 bool tc_plan(const Ctx& c, int r0, int r1, int w0, int w1, int d, TcPlan& p) {
-  if (&c != c.root || c.root->gemm_mode != 0) return false;
+  if (&c != c.root || c.root->gemm_mode == 1) return false;
   if (!(r0 >= 1 && r1 >= 1 && r0 <= TC_MAX_KPA && r1 <= CGP_MAX_BOND && w0 >= 1 && w1 >= 1 && w0 <= CGP_MAX_W &&
         w1 <= CGP_MAX_W && d >= 1 && d <= CGP_MAX_D))
     return false;

@@ -498,7 +498,7 @@ void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, 
     contract_direct(c, a, A, B, C);
     return;
   }
-  if (c.root->gemm_mode == 0 && batch * M * N * K >= (int64_t(1) << 23) && M >= 16 && N >= 16 && K >= 16) {
+  if (c.root->gemm_mode != 1 && batch * M * N * K >= (int64_t(1) << 23) && M >= 16 && N >= 16 && K >= 16) {
     gemm_ozaki(c, batch, M, N, K, alpha, A, sAb, sAm, sAk, B, sBb, sBk, sBn, beta, C, sCb, sCm, sCn);
     return;
   }

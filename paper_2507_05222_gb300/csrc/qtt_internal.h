@@ -147,7 +147,8 @@ struct Ctx {
   // 1 = one kernel per contraction and CG update (read from the root context).
   int cg_mode = 0;
   // Matrix products: 0 = products of >= 2^23 multiply-adds on the tensor cores (digit
-  // splitting, see qtt_ozaki.cu), the rest on the FP64 pipe; 1 = everything on the FP64 pipe.
+  // splitting, see qtt_ozaki.cu; engine kDigitProductsOnTc05), the rest on the FP64 pipe;
+  // 1 = everything on the FP64 pipe; 2 = digit products on mma.sync; 3 = digit products on tcgen05.
   int gemm_mode = 0;
   // Per-tile arrival counters of split-K GEMMs on this context's stream (kTileCounters ints,
   // zero between launches: the last CTA of a tile resets its counter).
@@ -245,6 +246,14 @@ void gemm_ozaki(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double a
                 int64_t sAm, int64_t sAk, const double* B, int64_t sBb, int64_t sBk, int64_t sBn, double beta,
                 double* C, int64_t sCb, int64_t sCm, int64_t sCn);
 void init_ozaki_attributes();   // kernel attributes, once (before any stream capture)
+// The digit products of gemm_ozaki on the fifth-generation tensor cores (qtt_tc05.cu): the
+// engine of gemm mode 0 when true (mode 3 forces it, mode 2 forces the mma.sync kernel).
+constexpr bool kDigitProductsOnTc05 = false;
+void init_tc05_attributes();     // kernel attributes and the tensor-map encoder, once
+bool tc05_fits(int64_t Kp);
+void oz_gemm_tc05(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t Kp, int splits, int64_t ksplit,
+                  const void* As, const int* ea, const void* Bs, const int* eb, double alpha, double beta, double* C,
+                  int64_t sCb, int64_t sCm, int64_t sCn, double* W);
 // Seven bf16 digit slices out[s][r][Kp] and scale exponents ex[r] of the R rows of X (K values
 // each, strides sR, sK), as the tensor-core products use them (qtt_ozaki.cu).
 void oz_split_rows(Ctx& c, int64_t R, int64_t K, int64_t Kp, const double* X, int64_t sR, int64_t sK, void* out,

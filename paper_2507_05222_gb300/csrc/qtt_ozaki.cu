@@ -278,10 +278,16 @@ void gemm_ozaki(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double a
   QTT_CHECK_ARG(grid.y <= 65535 && grid.z <= 65535, "gemm_ozaki: grid too large");
   DBuf Wb;
   if (splits > 1) Wb.reset(&c, size_t(splits) * batch * M * N);
-  k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(kc), c.stream>>>(M, N, Kp, kc, int(splits), ksplit, batch, As, ea, Bs,
-                                                               eb, alpha, beta, C, sCb, sCm, sCn,
-                                                               splits > 1 ? Wb.p : nullptr, c.guard);
-  after_launch(c, "oz_gemm");
+  const int mode = c.root->gemm_mode;
+  if ((mode == 3 || (mode == 0 && kDigitProductsOnTc05)) && !c.guard && tc05_fits(Kp)) {
+    oz_gemm_tc05(c, batch, M, N, Kp, int(splits), ksplit, As, ea, Bs, eb, alpha, beta, C, sCb, sCm, sCn,
+                 splits > 1 ? Wb.p : nullptr);
+  } else {
+    k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(kc), c.stream>>>(M, N, Kp, kc, int(splits), ksplit, batch, As, ea, Bs,
+                                                                 eb, alpha, beta, C, sCb, sCm, sCn,
+                                                                 splits > 1 ? Wb.p : nullptr, c.guard);
+    after_launch(c, "oz_gemm");
+  }
   if (splits > 1) {
     const int64_t total = batch * M * N;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 4096);

@@ -89,3 +89,48 @@ def test_dispatch_of_large_products(ctx):
         finally:
             ctx.set_gemm_mode(0)
         assert np.all(np.abs(C - ref) <= 2 * fp64_bound(A, B) + 4 * bound(A, B))
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 32, 64), (130, 70, 64), (256, 128, 384), (1000, 48, 200), (17, 33, 17),
+                                   (300, 31, 1000), (64, 4096, 128), (4096, 128, 64), (129, 257, 4100)])
+def test_tcgen05_digit_products_equal_mma_sync(ctx, m, n, k):
+    """The digit products on the fifth-generation tensor cores (tcgen05.mma on TMA-staged 128-byte
+    swizzled tiles, seven tensor-memory accumulators, path 3) add the same exact integers as the
+    warp-level mma.sync kernel (path 2): the results are bit-identical, on tile-ragged shapes, k
+    spanning several 64-wide chunks and split k, and they meet the scheme's own bound."""
+    from paper_2507_05222_gb300 import qtt
+    g = inputs.rng(m * 7 + n * 3 + k)
+    A = g.standard_normal((m, k)) * np.exp(g.uniform(-8, 8, (m, 1)))
+    B = g.standard_normal((k, n)) * np.exp(g.uniform(-8, 8, (1, n)))
+    c2 = qtt.qtt_dgemm(ctx, A, B, path=2)
+    c3 = qtt.qtt_dgemm(ctx, A, B, path=3)
+    assert np.array_equal(c2, c3)
+    err = np.abs(c3 - exact(A, B)).astype(np.float64)
+    assert np.all(err <= bound(A, B))
+
+
+def test_tcgen05_step_equals_mma_sync_step(ctx):
+    """A whole step at chi = 64 (12 bits) with every large product on the tcgen05 kernel equals the
+    step with the mma.sync kernel bit for bit (same exact group sums, same kernels otherwise)."""
+    from oracle import qtt_ops as Q, step as S
+    from paper_2507_05222_gb300 import qtt
+    ne = nx = 6
+    chi = 64
+    ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, "interleaved")
+    u0, v0 = inputs.wake_field(ne, nx, 3)
+    u, v = ops.encode(u0, chi), ops.encode(v0, chi)
+    p = S.padded([np.zeros((1, 2, 1))] * (ne + nx), chi, inputs.random_cores(ne + nx, chi, 5, scale=1e-8))
+    out = []
+    try:
+        for mode in (2, 3):
+            ctx.set_gemm_mode(mode)
+            case = qtt.Case(ctx, ne, nx, 40.0, 100.0, 2e-3, chi, "interleaved")
+            case.set_state(*(qtt.MPS.from_cores(ctx, x) for x in (u, v, p)))
+            info = case.fractional_step(2, check=False)
+            out.append(([qtt.qtt_decode(ctx, x) for x in case.get_state()], info))
+    finally:
+        ctx.set_gemm_mode(0)
+    (a, ia), (b, ib) = out
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert [r["p"]["sweeps"] for r in ia] == [r["p"]["sweeps"] for r in ib]
