@@ -136,7 +136,8 @@ const char* qtt_last_error(void);
 int qtt_profiler_range(int start);
 /* Number of kernels this context has launched so far (all entry points). */
 int64_t qtt_ctx_kernel_launches(qtt_ctx* ctx);
-/* Bytes currently held by the context's device pool (in use + cached). */
+/* Bytes currently held by the device pools of the context and its worker streams (in use,
+ * cached, and the scratch arenas of captured step graphs). */
 size_t qtt_ctx_pool_bytes(qtt_ctx* ctx);
 /* Per-kernel-class timing.  Synchronises the stream, then writes, for classes 0 FP64 GEMM,
  * 1 Householder QR, 2 Jacobi eigensolver, 3 CG update, 4 other, and the phases of
@@ -275,6 +276,21 @@ int qtt_ctx_set_gemm_mode(qtt_ctx* ctx, int mode);
  * reciprocal (err2[0]) and reciprocal square root (err2[1]) against CUDA's correctly rounded
  * 1/x and 1/sqrt(x) over the n positive host values x.  Synchronous. */
 int qtt_check_recip(qtt_ctx* ctx, int n, const double* x, double* err2);
+/* GEMM autotuner (the contractions that reach the batched GEMM: core products of the
+ * environments, the fits and the local solves outside the cooperative CG kernels).  on = 1:
+ * every GEMM shape met for the first time (gemm mode, batch, M, N, K, strides, beta != 0) is
+ * timed under each candidate engine -- the FP64-pipe kernel at tile sizes 64, 32 and 16, with
+ * the cost model's split-K and unsplit, and the digit-split tensor-core product where the
+ * shape allows it (gemm mode != 1, M, N, K >= 16) -- on a stream of the tuner's own over
+ * scratch operands, and the fastest is kept; this also happens while a step graph is being
+ * captured, the captured step then using the picks.  Shapes already in the table use their
+ * pick whether tuning is on or off (on = 0); on = -1 clears the table and turns tuning off.
+ * Results of a tuned product differ from the cost model's only in rounding order. */
+int qtt_ctx_set_autotune(qtt_ctx* ctx, int on);
+/* The tuner's table: *count = number of tuned shapes; up to max_rows rows of 9 int64 are
+ * written to rows: batch, M, N, K, engine (0 FP64 tiles, 1 digit-split tensor-core product,
+ * -1 not tunable), tile, k splits, time of the pick (ns), time of the cost model's choice (ns). */
+int qtt_ctx_autotune_table(qtt_ctx* ctx, int max_rows, int64_t* rows, int* count);
 /* <a, b> into *out_host (synchronous). */
 int mps_dot(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, double* out_host);
 
@@ -332,6 +348,19 @@ int qtt_case_get_vector(qtt_case* c, int which, qtt_mps** out);
  * checked over all steps whether or not per_step is given. */
 int fractional_step(qtt_ctx* ctx, qtt_case* c, int nsteps, int with_forces,
                     qtt_step_info* per_step);
+/* Advance several independent cases (Sec. III.C each; the rotating-wall cases of Sec. IV.B
+ * differ only in their parameters) by nsteps fractional steps each, and block the host until
+ * all have finished.  Each case's step is its captured CUDA graph (captured here when missing),
+ * replayed on a stream of its own, so that the cases' kernels share the GPU concurrently; every
+ * graph owns its scratch memory and split-K counters, and results are bit-identical to stepping
+ * each case alone with fractional_step.  cases: ncases distinct cases of ctx, all in graph
+ * replay mode (qtt_case_use_graph); they may differ in grid, chi, Re, dt, rotation and solver
+ * options.  per_step (may be NULL): ncases * nsteps records, case-major (case i, step s at
+ * i * nsteps + s).  status (may be NULL): ncases return codes, each as fractional_step would
+ * return it for that case.  Returns the most severe of them (QTT_ERR_TIMEOUT over
+ * QTT_ERR_NONFINITE over the others); the argument checks fail with QTT_ERR_ARG before any work. */
+int fractional_step_batch(qtt_ctx* ctx, int ncases, qtt_case* const* cases, int nsteps, int with_forces,
+                          qtt_step_info* per_step, int* status);
 /* Replay mode of fractional_step.  enable != 0 (the default): the first call captures one
  * step as a CUDA graph on an internal stream (ordered after the context stream by events)
  * and every step replays it; the graph is dropped when the state is set again.  enable = 0:

@@ -104,12 +104,16 @@ __global__ void k_diag_core(const double* __restrict__ A, int r0, int d, int r1,
   }
 }
 
-// *acc += sum of the discarded eigenvalues w[bk..nv) of a Gram rounding cut (sigma^2 each).
-__global__ void k_disc_add(const double* w, int nv, int bk, double* acc) {
+// *acc += the discarded weight of a Gram rounding cut: trace(rho) minus the kept eigenvalues
+// w[0..bk) (sigma^2 each).  The kept eigenpairs are refined to FP64 and their sum is
+// insensitive to how the discarded subspace is resolved, which the discarded eigenvalues
+// themselves (FP32 Jacobi, not refined) are not.
+__global__ void k_disc_add(const double* rho, const double* w, int nv, int bk, double* acc) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double s = 0.0;
-  for (int i = bk; i < nv; ++i) s += fmax(w[i], 0.0);
-  *acc += s;
+  double tr = 0.0, kept = 0.0;
+  for (int i = 0; i < nv; ++i) tr += rho[int64_t(i) * nv + i];
+  for (int i = 0; i < bk; ++i) kept += w[i];
+  *acc += fmax(tr - kept, 0.0);
 }
 
 __global__ void k_add_value(double* acc, double v) {
@@ -124,9 +128,9 @@ __global__ void k_sqrt(const double* in, double* out) {
 
 // Discarded weight of one rounding cut, added to the context's accumulator when a caller asked
 // for it (qtt_round_info.discarded_norm).
-static void add_discarded(Ctx& c, const double* w_dev, int nv, int bk) {
+static void add_discarded(Ctx& c, const double* rho_dev, const double* w_dev, int nv, int bk) {
   if (!c.disc_acc || bk >= nv) return;
-  k_disc_add<<<1, 1, 0, c.stream>>>(w_dev, nv, bk, c.disc_acc);
+  k_disc_add<<<1, 1, 0, c.stream>>>(rho_dev, w_dev, nv, bk, c.disc_acc);
   after_launch(c, "disc_add");
 }
 
@@ -415,7 +419,7 @@ qtt_mps* round_gram(Ctx& c, const qtt_mps* y, int chi, double eps) {
     einsum(c, "Asc,AtD->sctD", 1.0, tv(T.p, {a0, d, c1}), tv(Z.p, {a0, d, c1}), 0.0, tv(rho.p, {d, c1, d, c1}));
     eigh(c, nv, rho.p, w.p, V.p, std::min(std::min(chi, m[k]), nv));
     int bk = choose_rank(c, w.p, nv, chi, eps, std::min(m[k], nv));
-    add_discarded(c, w.p, nv, bk);
+    add_discarded(c, rho.p, w.p, nv, bk);
     out[k].reset(&c, size_t(bk) * nv);
     top_vectors_as_core(c, V.p, nv, bk, out[k].p);
     // P_k = Z V[:, :bk]  (a0 x bk)
@@ -496,7 +500,7 @@ qtt_mps* apply_round_gram(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, d
            tv(rho.p, {d, c1, d, c1}));
     eigh(c, nv, rho.p, wv.p, V.p, std::min(std::min(chi, mstruct[k]), nv));
     int bk = choose_rank(c, wv.p, nv, chi, eps, std::min(mstruct[k], nv));
-    add_discarded(c, wv.p, nv, bk);
+    add_discarded(c, rho.p, wv.p, nv, bk);
     out[k].reset(&c, size_t(bk) * nv);
     top_vectors_as_core(c, V.p, nv, bk, out[k].p);
     DBuf Pn(&c, size_t(w0) * a0 * bk);
@@ -870,7 +874,7 @@ qtt_mps* encode_dense(Ctx& c, const double* dense_dev, int n, int d, int chi, do
     int strct = int(std::min<int64_t>(rows, nv));
     eigh(c, nv, rho.p, w.p, V.p, std::min(chi, strct));
     int bk = choose_rank(c, w.p, nv, chi, eps, strct);
-    add_discarded(c, w.p, nv, bk);
+    add_discarded(c, rho.p, w.p, nv, bk);
     out[k].reset(&c, size_t(bk) * nv);
     top_vectors_as_core(c, V.p, nv, bk, out[k].p);
     DBuf nxt(&c, size_t(rows) * bk);

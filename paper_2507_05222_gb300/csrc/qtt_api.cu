@@ -198,6 +198,7 @@ void qtt_ctx_destroy(qtt_ctx* ctx) {
       cudaEventDestroy(pr.e1);
     }
   free_tile_counters(*c);
+  free_autotuner(*c);
   if (c->prof.dev_flops) cudaFree(c->prof.dev_flops);
   if (c->side) cudaStreamDestroy(c->side);
   delete c->pool;
@@ -222,7 +223,13 @@ int qtt_profiler_range(int start) {
 
 int64_t qtt_ctx_kernel_launches(qtt_ctx* ctx) { return ctx ? reinterpret_cast<Ctx*>(ctx)->launches : 0; }
 
-size_t qtt_ctx_pool_bytes(qtt_ctx* ctx) { return ctx ? reinterpret_cast<Ctx*>(ctx)->pool->held() : 0; }
+size_t qtt_ctx_pool_bytes(qtt_ctx* ctx) {
+  if (!ctx) return 0;
+  const Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  size_t b = c->pool->held();
+  for (const Ctx* w : c->workers) b += w->pool->held();
+  return b;
+}
 
 int qtt_ctx_profile(qtt_ctx* ctx, int on, double* ms_out, double* flops_out, int64_t* launches_out) {
   API_BEGIN
@@ -624,6 +631,28 @@ int qtt_ctx_set_gemm_mode(qtt_ctx* ctx, int mode) {
   API_END
 }
 
+int qtt_ctx_set_autotune(qtt_ctx* ctx, int on) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx, "ctx is null");
+  QTT_CHECK_ARG(on == 0 || on == 1 || on == -1, "autotune: on must be 1, 0 or -1 (clear the table)");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  if (on == -1) {
+    c.tuned.clear();
+    c.autotune = false;
+  } else {
+    c.autotune = on == 1;
+  }
+  API_END
+}
+
+int qtt_ctx_autotune_table(qtt_ctx* ctx, int max_rows, int64_t* rows, int* count) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && count, "autotune_table: null argument");
+  QTT_CHECK_ARG(max_rows >= 0 && (max_rows == 0 || rows), "autotune_table: rows needed for max_rows > 0");
+  *count = int(autotune_table(*reinterpret_cast<Ctx*>(ctx), max_rows, rows));
+  API_END
+}
+
 int qtt_check_recip(qtt_ctx* ctx, int n, const double* x, double* err2) {
   API_BEGIN
   QTT_CHECK_ARG(ctx && x && err2 && n >= 1 && n <= (1 << 24), "check_recip: arguments");
@@ -778,6 +807,51 @@ int qtt_case_get_vector(qtt_case* h, int which, qtt_mps** out) {
   API_END
 }
 
+// Reads the device records of nsteps steps of one case: fills per_step (may be null), adds the
+// replayed kernels to the launch count, returns the most severe outcome over the steps
+// (timeout, non-finite, out of sweeps) with its message in msg.
+static int read_step_records(Ctx& c, Case& cs, const double* hrec, int nsteps, bool forces, qtt_step_info* per_step,
+                             const char* who, std::string& msg) {
+  int rc = QTT_OK;
+  for (int s = 0; s < nsteps; ++s) {
+    const double* r = &hrec[size_t(s) * kStepRecDoubles];
+    AlsCtl h[3];
+    std::memcpy(h, r, sizeof(h));
+    const int finite = r[kStepRecFinite] != 0.0;
+    if (per_step) {
+      fill_solve_info(h[0], &per_step[s].u);
+      fill_solve_info(h[1], &per_step[s].v);
+      fill_solve_info(h[2], &per_step[s].p);
+      per_step[s].finite = finite;
+      per_step[s].cd = forces ? r[kStepRecForces] : 0.0;
+      per_step[s].cl = forces ? r[kStepRecForces + 1] : 0.0;
+    }
+    if (cs.use_graph) c.root->launches += cs.graph_launches + int64_t(h[0].sweeps) * cs.body_launches[0] +
+                                          int64_t(h[1].sweeps) * cs.body_launches[1] +
+                                          int64_t(h[2].sweeps) * cs.body_launches[2];
+    for (int i = 0; i < 3; ++i) {
+      const int e = solve_status_code(h[i].status, true);
+      const char* which[3] = {"u momentum", "v momentum", "Poisson"};
+      if (e != QTT_OK && (rc == QTT_OK || e == QTT_ERR_TIMEOUT || (e == QTT_ERR_NONFINITE && rc != QTT_ERR_TIMEOUT))) {
+        rc = e;
+        msg = std::string(who) + ": " + which[i] + " solve of step " + std::to_string(s) + ": " +
+              solve_status_text(h[i]);
+      }
+    }
+    if (!finite && rc != QTT_ERR_TIMEOUT) {
+      rc = QTT_ERR_NONFINITE;
+      msg = std::string(who) + ": the new velocity of step " + std::to_string(s) + " is not finite";
+    }
+  }
+  return rc;
+}
+
+// more severe of two outcomes: timeout > non-finite > any other error > OK
+static int more_severe(int a, int b) {
+  auto rank = [](int e) { return e == QTT_OK ? 0 : e == QTT_ERR_TIMEOUT ? 3 : e == QTT_ERR_NONFINITE ? 2 : 1; };
+  return rank(b) > rank(a) ? b : a;
+}
+
 int fractional_step(qtt_ctx* ctx, qtt_case* h, int nsteps, int with_forces, qtt_step_info* per_step) {
   API_BEGIN
   QTT_CHECK_ARG(ctx && h, "fractional_step: null argument");
@@ -796,41 +870,59 @@ int fractional_step(qtt_ctx* ctx, qtt_case* h, int nsteps, int with_forces, qtt_
   std::vector<double> hrec(size_t(nsteps) * kStepRecDoubles);
   QTT_CUDA(cudaMemcpyAsync(hrec.data(), rec.p, hrec.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   QTT_CUDA(cudaStreamSynchronize(c.stream));
-  int rc = QTT_OK;
   std::string msg;
-  for (int s = 0; s < nsteps; ++s) {
-    const double* r = &hrec[size_t(s) * kStepRecDoubles];
-    AlsCtl h[3];
-    std::memcpy(h, r, sizeof(h));
-    const int finite = r[kStepRecFinite] != 0.0;
-    if (per_step) {
-      fill_solve_info(h[0], &per_step[s].u);
-      fill_solve_info(h[1], &per_step[s].v);
-      fill_solve_info(h[2], &per_step[s].p);
-      per_step[s].finite = finite;
-      per_step[s].cd = forces ? r[kStepRecForces] : 0.0;
-      per_step[s].cl = forces ? r[kStepRecForces + 1] : 0.0;
-    }
-    if (cs.use_graph) c.root->launches += cs.graph_launches + int64_t(h[0].sweeps) * cs.body_launches[0] +
-                                          int64_t(h[1].sweeps) * cs.body_launches[1] +
-                                          int64_t(h[2].sweeps) * cs.body_launches[2];
-    // the most severe outcome over all steps: timeout, non-finite, out of sweeps
-    for (int i = 0; i < 3; ++i) {
-      const int e = solve_status_code(h[i].status, true);
-      const char* which[3] = {"u momentum", "v momentum", "Poisson"};
-      if (e != QTT_OK && (rc == QTT_OK || e == QTT_ERR_TIMEOUT || (e == QTT_ERR_NONFINITE && rc != QTT_ERR_TIMEOUT))) {
-        rc = e;
-        msg = std::string("fractional_step: ") + which[i] + " solve of step " + std::to_string(s) + ": " +
-              solve_status_text(h[i]);
-      }
-    }
-    if (!finite && rc != QTT_ERR_TIMEOUT) {
-      rc = QTT_ERR_NONFINITE;
-      msg = "fractional_step: the new velocity of step " + std::to_string(s) + " is not finite";
+  const int rc = read_step_records(c, cs, hrec.data(), nsteps, forces, per_step, "fractional_step", msg);
+  if (rc != QTT_OK) {
+    set_last_error(msg);
+    return rc;
+  }
+  API_END
+}
+
+int fractional_step_batch(qtt_ctx* ctx, int ncases, qtt_case* const* cases, int nsteps, int with_forces,
+                          qtt_step_info* per_step, int* status) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && cases && ncases >= 1, "fractional_step_batch: null argument or ncases < 1");
+  QTT_CHECK_ARG(nsteps >= 0, "fractional_step_batch: nsteps >= 0");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  std::vector<Case*> cs;
+  for (int i = 0; i < ncases; ++i) {
+    QTT_CHECK_ARG(cases[i] && cases[i]->ctx == &c, "fractional_step_batch: every case must belong to ctx");
+    Case* p = cases[i]->cs;
+    QTT_CHECK_ARG(p->u && p->v && p->p, "fractional_step_batch: state not set");
+    QTT_CHECK_ARG(p->use_graph, "fractional_step_batch: every case must replay its step graph");
+    for (Case* q : cs) QTT_CHECK_ARG(q != p, "fractional_step_batch: a case appears twice");
+    cs.push_back(p);
+  }
+  if (status)
+    for (int i = 0; i < ncases; ++i) status[i] = QTT_OK;
+  if (nsteps == 0) {
+    set_last_error("");
+    return QTT_OK;
+  }
+  const bool forces = with_forces && per_step;
+  const int64_t nrec = int64_t(ncases) * nsteps * kStepRecDoubles;
+  DBuf rec(&c, size_t(nrec));
+  fill(c, rec.p, nrec, 0.0);
+  run_steps_batch(c, cs, nsteps, forces, rec.p);
+  std::vector<double> hrec(static_cast<size_t>(nrec));
+  QTT_CUDA(cudaMemcpyAsync(hrec.data(), rec.p, hrec.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  int rc = QTT_OK;
+  std::string first;
+  for (int i = 0; i < ncases; ++i) {
+    std::string msg;
+    const std::string who = "fractional_step_batch: case " + std::to_string(i);
+    const int e = read_step_records(c, *cs[i], hrec.data() + int64_t(i) * nsteps * kStepRecDoubles, nsteps, forces,
+                                    per_step ? per_step + int64_t(i) * nsteps : nullptr, who.c_str(), msg);
+    if (status) status[i] = e;
+    if (more_severe(rc, e) != rc) {
+      rc = e;
+      first = msg;
     }
   }
   if (rc != QTT_OK) {
-    set_last_error(msg);
+    set_last_error(first);
     return rc;
   }
   API_END

@@ -331,8 +331,8 @@ void Case::drop_graph() {
     gexec = nullptr;
     graph = nullptr;
     if (ctx) {
-      ctx->pool->release_capture();
-      for (Ctx* w : ctx->workers) w->pool->release_capture();
+      ctx->pool->release_capture(this);
+      for (Ctx* w : ctx->workers) w->pool->release_capture(this);
     }
   }
 }
@@ -345,6 +345,8 @@ Case::~Case() {
   for (auto& e : ph_ev)
     if (e) cudaEventDestroy(e);
   if (rec) cudaFree(rec);
+  for (int* t : tile_ctr)
+    if (t) cudaFree(t);
   for (qtt_mpo* m : {Dx, Dz, Dxp, Dzp, H, Ap, Px, Pz, Jdiag})
     if (m) free_mpo(m);
   for (qtt_mps* x : {bcx_u, bcz_u, bcx_v, bcz_v, JbcLap_u, JbcLap_v, bcdiv_w, absJ, u, v, p})
@@ -663,11 +665,30 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
   if (!cs.ev_in) QTT_CUDA(cudaEventCreateWithFlags(&cs.ev_in, cudaEventDisableTiming));
   if (!cs.ev_out) QTT_CUDA(cudaEventCreateWithFlags(&cs.ev_out, cudaEventDisableTiming));
   if (!cs.rec) QTT_CUDA(cudaMalloc(&cs.rec, kStepRecDoubles * sizeof(double)));
+  // The graph's own split-K tile counters and pool arena (one per case, for the context and
+  // each worker), so that the graphs of different cases may replay concurrently.
+  std::vector<Ctx*> tree{&c};
+  for (Ctx* w : c.workers) tree.push_back(w);
+  while (cs.tile_ctr.size() < tree.size()) {
+    int* t = nullptr;
+    QTT_CUDA(cudaMalloc(&t, kTileCounters * sizeof(int)));
+    cs.tile_ctr.push_back(t);
+    QTT_CUDA(cudaMemsetAsync(t, 0, kTileCounters * sizeof(int), c.stream));
+  }
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  std::vector<int*> saved_ctr;
+  for (size_t i = 0; i < tree.size(); ++i) {
+    saved_ctr.push_back(tree[i]->tile_ctr);
+    tree[i]->tile_ctr = cs.tile_ctr[i];
+  }
+  auto restore_ctr = [&]() {
+    for (size_t i = 0; i < tree.size(); ++i) tree[i]->tile_ctr = saved_ctr[i];
+  };
   cudaStream_t saved = c.stream;
   const bool prof_on = c.root->prof.on;
   c.root->prof.on = false;   // no timing events inside a graph
-  c.pool->begin_capture();
-  for (Ctx* w : c.workers) w->pool->begin_capture();
+  c.pool->begin_capture(&cs);
+  for (Ctx* w : c.workers) w->pool->begin_capture(&cs);
   c.stream = cs.gstream;
   const int64_t n0 = c.root->launches;
   for (int i = 0; i < 5; ++i)
@@ -685,6 +706,7 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
     c.stream = saved;
     c.pool->end_capture();
     for (Ctx* w : c.workers) w->pool->end_capture();
+    restore_ctr();
     c.root->prof.on = prof_on;
     c.root->launches = n0;
     throw;
@@ -694,6 +716,7 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
   c.stream = saved;
   c.pool->end_capture();
   for (Ctx* w : c.workers) w->pool->end_capture();
+  restore_ctr();
   c.root->prof.on = prof_on;
   cs.graph_launches = c.root->launches - n0 - cs.body_launches[0] - cs.body_launches[1] - cs.body_launches[2];
   c.root->launches = n0;
@@ -715,6 +738,27 @@ void run_steps(Ctx& c, Case& cs, int nsteps, bool with_forces, double* rec_all) 
     QTT_CUDA(cudaEventRecord(cs.ev_out, cs.gstream));
     QTT_CUDA(cudaStreamWaitEvent(c.stream, cs.ev_out, 0));
     copy(c, rec_all + int64_t(kStepRecDoubles) * s, cs.rec, kStepRecDoubles);
+  }
+}
+
+void run_steps_batch(Ctx& c, const std::vector<Case*>& cases, int nsteps, bool with_forces, double* rec_all) {
+  // every graph first (captures are host work on the context's streams), then the replays:
+  // one stream per case, ordered after the context stream, step s of every case enqueued
+  // before step s + 1 of any
+  for (Case* cs : cases)
+    if (!cs->gexec || cs->graph_forces != with_forces) capture(c, *cs, with_forces);
+  QTT_CUDA(cudaEventRecord(cases[0]->ev_in, c.stream));
+  for (Case* cs : cases) QTT_CUDA(cudaStreamWaitEvent(cs->gstream, cases[0]->ev_in, 0));
+  for (int s = 0; s < nsteps; ++s)
+    for (size_t i = 0; i < cases.size(); ++i) {
+      Case& cs = *cases[i];
+      QTT_CUDA(cudaGraphLaunch(cs.gexec, cs.gstream));
+      double* dst = rec_all + (int64_t(i) * nsteps + s) * kStepRecDoubles;
+      QTT_CUDA(cudaMemcpyAsync(dst, cs.rec, kStepRecDoubles * sizeof(double), cudaMemcpyDeviceToDevice, cs.gstream));
+    }
+  for (Case* cs : cases) {
+    QTT_CUDA(cudaEventRecord(cs->ev_out, cs->gstream));
+    QTT_CUDA(cudaStreamWaitEvent(c.stream, cs->ev_out, 0));
   }
 }
 

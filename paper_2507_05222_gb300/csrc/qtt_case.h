@@ -31,6 +31,7 @@ struct Case {
   int64_t graph_launches = 0;       // kernels of one replay outside the ALS sweep loops
   int64_t body_launches[3] = {0, 0, 0};  // kernels of one sweep of the u, v and p solves
   double* rec = nullptr;            // kStepRecDoubles doubles of device memory (cudaMalloc, once)
+  std::vector<int*> tile_ctr;       // the graph's split-K tile counters (context, then workers)
   // Phase boundaries of the last step (timing events; external event nodes inside the graph):
   // start, after the MPO-MPS products, after the right sides + momentum, after the Poisson
   // solve, after the projection.
@@ -54,6 +55,10 @@ void step(Ctx& c, Case& cs, double* rec, bool with_forces);
 // nsteps steps, replaying the captured graph when cs.use_graph; records into rec_all (device,
 // kStepRecDoubles per step).
 void run_steps(Ctx& c, Case& cs, int nsteps, bool with_forces, double* rec_all);
+// nsteps steps of every case (graph replays only), the cases' graphs replayed concurrently on
+// their own streams; records into rec_all (device, case-major: case i, step s at
+// (i * nsteps + s) * kStepRecDoubles).  The cases must be distinct.
+void run_steps_batch(Ctx& c, const std::vector<Case*>& cases, int nsteps, bool with_forces, double* rec_all);
 void case_forces(Ctx& c, Case& cs, double* out_dev);
 void read_row(Ctx& c, const Case& cs, const qtt_mps* x, int64_t I, double* row_dev);
 // *flag = 0 if any of x[0..n) is NaN or Inf (left untouched otherwise).

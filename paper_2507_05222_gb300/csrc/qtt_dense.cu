@@ -45,10 +45,11 @@ void* Pool::raw_alloc(size_t bytes) {
 void* Pool::get(size_t bytes) {
   size_t cls = size_class(bytes);
   if (capturing_) {
-    auto ci = cap_free_.find(cls);
-    if (ci != cap_free_.end()) {
+    auto& arena = cap_free_[capturing_];
+    auto ci = arena.find(cls);
+    if (ci != arena.end()) {
       void* p = ci->second;
-      cap_free_.erase(ci);
+      arena.erase(ci);
       live_[p] = cls;
       return p;
     }
@@ -61,7 +62,7 @@ void* Pool::get(size_t bytes) {
     cur_ += cls;
     cur_left_ -= cls;
     live_[p] = cls;
-    cap_owned_[p] = cls;
+    cap_owned_[p] = capturing_;
     return p;
   }
   auto it = free_blocks_.lower_bound(cls);
@@ -89,8 +90,9 @@ void Pool::put(void* p) {
   if (it == live_.end()) return;
   size_t cls = it->second;
   live_.erase(it);
-  if (cap_owned_.count(p)) {
-    cap_free_.insert({cls, p});   // reserved for the graph: reused only by a capture
+  auto own = cap_owned_.find(p);
+  if (own != cap_owned_.end()) {
+    cap_free_[own->second].insert({cls, p});   // reserved for its graph: reused only by its captures
     return;
   }
   if (capturing_) {
@@ -101,12 +103,12 @@ void Pool::put(void* p) {
   free_blocks_.insert({cls, p});
 }
 
-void Pool::begin_capture() {
-  capturing_ = true;
+void Pool::begin_capture(const void* owner) {
+  capturing_ = owner;
 }
 
 void Pool::end_capture() {
-  capturing_ = false;
+  capturing_ = nullptr;
   for (void* p : deferred_) {
     auto it = live_.find(p);
     if (it != live_.end()) {
@@ -117,15 +119,21 @@ void Pool::end_capture() {
   deferred_.clear();
 }
 
-void Pool::release_capture() {
-  for (auto& kv : cap_free_) free_blocks_.insert(kv);
-  cap_free_.clear();
-  // arena blocks still live (held by objects created during the capture) stay with their owners
+void Pool::release_capture(const void* owner) {
+  auto a = cap_free_.find(owner);
+  if (a != cap_free_.end()) {
+    for (auto& kv : a->second) {
+      free_blocks_.insert(kv);
+      cap_owned_.erase(kv.second);
+    }
+    cap_free_.erase(a);
+  }
+  // arena blocks still live (held by objects created during the capture) stay with their
+  // holders and return to the ordinary free list when those are freed
   for (auto it = cap_owned_.begin(); it != cap_owned_.end();) {
-    if (!live_.count(it->first)) it = cap_owned_.erase(it);
+    if (it->second == owner) it = cap_owned_.erase(it);
     else ++it;
   }
-  cap_owned_.clear();
 }
 
 DBuf::DBuf(Ctx* c, size_t count) { reset(c, count); }
@@ -467,6 +475,197 @@ void contract_direct(Ctx& c, DirectArgs& a, const double* A, const double* B, do
 
 }  // namespace
 
+namespace {
+
+struct GemmArgs {
+  int64_t batch, M, N, K;
+  double alpha;
+  const double* A;
+  int64_t sAb, sAm, sAk;
+  const double* B;
+  int64_t sBb, sBk, sBn;
+  double beta;
+  double* C;
+  int64_t sCb, sCm, sCn;
+};
+
+struct Plan {
+  int T;
+  int64_t splits, kchunk;
+  double cost;
+};
+
+// FP64-pipe tile plan of tile size T with a given number of k splits (0: the split-K choice of
+// the cost model below).
+Plan plan_fp64(const Ctx& c, const GemmArgs& g, int T, int64_t want_splits) {
+  const int64_t target = 2 * int64_t(c.num_sms);
+  Plan p;
+  p.T = T;
+  const int64_t tiles = ((g.M + T - 1) / T) * ((g.N + T - 1) / T) * g.batch;
+  int64_t splits = 1;
+  if (want_splits > 0) {
+    splits = want_splits;
+  } else if (tiles < target && g.K > 2 * GK) {
+    int64_t want = (target + tiles - 1) / tiles;
+    int64_t maxs = (g.K + 2 * GK - 1) / (2 * GK);   // at least 32 k per split
+    splits = std::max<int64_t>(1, std::min<int64_t>(want, maxs));
+  }
+  int64_t kchunk = (g.K + splits - 1) / splits;
+  kchunk = (kchunk + GK - 1) / GK * GK;
+  splits = (g.K + kchunk - 1) / kchunk;
+  p.splits = splits;
+  p.kchunk = kchunk;
+  const int64_t per_sm = (tiles * splits + c.num_sms - 1) / c.num_sms;
+  p.cost = double(per_sm) * T * T * double(kchunk) / 2.0 + (splits > 1 ? 3000.0 : 0.0);
+  return p;
+}
+
+// Tile and split-K choice of the cost model.  On GB300 an SM retires 2 FP64 FMAs per cycle, so
+// the FP64 pipe, not shared-memory or L2 traffic, bounds these kernels at any tile size >= 16:
+// the time is about the FMA load of the busiest SM, ceil(CTAs / SMs) T^2 kchunk / 2 cycles,
+// plus one more launch when K is split.  Each tile size is planned with split-K up to two CTAs
+// per SM (at least 2 GK of k per split); the cheapest plan wins, ties going to the larger tile.
+Plan heuristic_plan(const Ctx& c, const GemmArgs& g) {
+  Plan best = plan_fp64(c, g, 64, 0);
+  for (int T : {32, 16}) {
+    Plan p = plan_fp64(c, g, T, 0);
+    if (p.cost < best.cost * 0.97) best = p;
+  }
+  return best;
+}
+
+void launch_fp64(Ctx& c, const GemmArgs& g, const Plan& best) {
+  const int T = best.T;
+  const int splits = int(best.splits);
+  const int64_t kchunk = best.kchunk;
+  const int64_t batch = g.batch, M = g.M, N = g.N, K = g.K;
+  ProfScope ps(c, KC_GEMM, 2.0 * double(batch) * double(M) * double(N) * double(K));
+  dim3 grid(unsigned((N + T - 1) / T), unsigned((M + T - 1) / T), unsigned(batch * splits));
+  QTT_CHECK_ARG(grid.y <= 65535 && grid.z <= 65535, "gemm grid too large");
+  dim3 block(16, 16);
+  DBuf W;
+  if (splits > 1) W.reset(&c, size_t(splits) * batch * M * N);
+  double* Wp = splits > 1 ? W.p : nullptr;
+  const int64_t ntiles = int64_t(grid.x) * grid.y * batch;
+  int* ctr = (splits > 1 && c.tile_ctr && ntiles <= kTileCounters) ? c.tile_ctr : nullptr;
+  if (T == 64)
+    k_gemm<64><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, g.alpha, g.A, g.sAb, g.sAm, g.sAk, g.B,
+                                             g.sBb, g.sBk, g.sBn, g.beta, g.C, g.sCb, g.sCm, g.sCn, Wp, ctr, c.guard);
+  else if (T == 32)
+    k_gemm<32><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, g.alpha, g.A, g.sAb, g.sAm, g.sAk, g.B,
+                                             g.sBb, g.sBk, g.sBn, g.beta, g.C, g.sCb, g.sCm, g.sCn, Wp, ctr, c.guard);
+  else
+    k_gemm<16><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, g.alpha, g.A, g.sAb, g.sAm, g.sAk, g.B,
+                                             g.sBb, g.sBk, g.sBn, g.beta, g.C, g.sCb, g.sCm, g.sCn, Wp, ctr, c.guard);
+  after_launch(c, "gemm");
+  if (splits > 1 && !ctr) {
+    k_splitk_reduce<<<grid_for(batch * M * N, 256), 256, 0, c.stream>>>(batch, M, N, splits, g.alpha, W.p, g.beta,
+                                                                        g.C, g.sCb, g.sCm, g.sCn, c.guard);
+    after_launch(c, "splitk_reduce");
+  }
+}
+
+GemmKey gemm_key(const Ctx& c, const GemmArgs& g) {
+  return GemmKey{int64_t(c.root->gemm_mode), g.batch, g.M, g.N, g.K, g.sAb, g.sAm, g.sAk, g.sBb, g.sBk, g.sBn,
+                 g.sCb, g.sCm, g.sCn, g.beta == 0.0 ? 0 : 1};
+}
+
+// Largest element offset + 1 of a strided view (non-negative strides).
+int64_t view_span(int64_t n0, int64_t s0, int64_t n1, int64_t s1, int64_t n2, int64_t s2) {
+  return (n0 - 1) * s0 + (n1 - 1) * s1 + (n2 - 1) * s2 + 1;
+}
+
+// Times every candidate engine of one GEMM shape and returns the fastest: the FP64-pipe kernel
+// at tile sizes 64, 32 and 16 (split-K as the cost model plans it, and unsplit), and the
+// digit-split tensor-core product where the shape allows it.  The trials run on the tuner's
+// own stream (outside any capture, so a step being captured is not disturbed) over scratch
+// operands of the same shape and strides filled with constants; each candidate runs once to
+// warm up, then three times between events, and keeps its fastest time.
+GemmPick tune_gemm(Ctx& c, const GemmArgs& g, bool oz_ok) {
+  Ctx& r = *c.root;
+  GemmPick none{-1, 0, 0, 0.0, 0.0};
+  if (g.sAb < 0 || g.sAm < 0 || g.sAk < 0 || g.sBb < 0 || g.sBk < 0 || g.sBn < 0 || g.sCb < 0 || g.sCm < 0 ||
+      g.sCn < 0)
+    return none;   // negative strides: the cost model decides
+  if (!r.tune_stream) {
+    QTT_CUDA(cudaStreamCreateWithFlags(&r.tune_stream, cudaStreamNonBlocking));
+    QTT_CUDA(cudaMalloc(&r.tune_ctr, kTileCounters * sizeof(int)));
+    QTT_CUDA(cudaMemsetAsync(r.tune_ctr, 0, kTileCounters * sizeof(int), r.tune_stream));
+    QTT_CUDA(cudaEventCreate(&r.tune_ev[0]));
+    QTT_CUDA(cudaEventCreate(&r.tune_ev[1]));
+  }
+  const int64_t na = view_span(g.batch, g.sAb, g.M, g.sAm, g.K, g.sAk);
+  const int64_t nb = view_span(g.batch, g.sBb, g.K, g.sBk, g.N, g.sBn);
+  const int64_t nc = view_span(g.batch, g.sCb, g.M, g.sCm, g.N, g.sCn);
+  const size_t need = size_t(na + nb + nc);
+  if (need > r.tune_cap) {
+    QTT_CUDA(cudaStreamSynchronize(r.tune_stream));
+    if (r.tune_buf) QTT_CUDA(cudaFree(r.tune_buf));
+    r.tune_buf = nullptr;
+    r.tune_cap = 0;
+    QTT_CUDA(cudaMalloc(&r.tune_buf, need * sizeof(double)));
+    r.tune_cap = need;
+  }
+  // a context of its own for the trials: the tuner's stream, pool and counters, no guard, no
+  // profiling (a block of the context's pool may still be in use by work queued on its stream)
+  if (!r.tune_pool) r.tune_pool = new Pool(r.alloc_fn, r.free_fn, r.alloc_user);
+  Ctx t;
+  t.device = c.device;
+  t.stream = r.tune_stream;
+  t.pool = r.tune_pool;
+  t.num_sms = c.num_sms;
+  t.root = &t;
+  t.gemm_mode = r.gemm_mode;
+  t.tile_ctr = r.tune_ctr;
+  double* A = r.tune_buf;
+  double* B = A + na;
+  double* C = B + nb;
+  fill(t, A, na, 0.75);
+  fill(t, B, nb, -1.25);
+  fill(t, C, nc, 0.5);
+  GemmArgs h = g;
+  h.A = A; h.B = B; h.C = C;
+  auto time_of = [&](auto&& launch) {
+    launch();
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      QTT_CUDA(cudaEventRecord(r.tune_ev[0], t.stream));
+      launch();
+      QTT_CUDA(cudaEventRecord(r.tune_ev[1], t.stream));
+      QTT_CUDA(cudaEventSynchronize(r.tune_ev[1]));
+      float ms = 0.f;
+      QTT_CUDA(cudaEventElapsedTime(&ms, r.tune_ev[0], r.tune_ev[1]));
+      best = std::min(best, ms);
+    }
+    return double(best) * 1e6;   // ns
+  };
+  GemmPick pick{0, 64, 0, 1e300, 0.0};
+  const Plan def = heuristic_plan(t, h);
+  for (int T : {64, 32, 16}) {
+    Plan pm = plan_fp64(t, h, T, 0);
+    for (int64_t sp : {pm.splits, int64_t(1)}) {
+      const Plan p = plan_fp64(t, h, T, sp);
+      const double ns = time_of([&] { launch_fp64(t, h, p); });
+      if (p.T == def.T && p.splits == def.splits) pick.default_ns = ns;
+      if (ns < pick.best_ns) pick = GemmPick{0, p.T, p.splits, ns, pick.default_ns};
+      if (pm.splits == 1) break;
+    }
+  }
+  if (oz_ok) {
+    const double ns = time_of([&] {
+      gemm_ozaki(t, h.batch, h.M, h.N, h.K, h.alpha, h.A, h.sAb, h.sAm, h.sAk, h.B, h.sBb, h.sBk, h.sBn, h.beta, h.C,
+                 h.sCb, h.sCm, h.sCn);
+    });
+    if (h.batch * h.M * h.N * h.K >= (int64_t(1) << 23)) pick.default_ns = ns;   // the cost model's engine
+    if (ns < pick.best_ns) pick = GemmPick{1, 0, 0, ns, pick.default_ns};
+  }
+  QTT_CUDA(cudaStreamSynchronize(t.stream));
+  r.tune_trials += 1;
+  return pick;
+}
+
+}  // namespace
+
 void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
           int64_t sAb, int64_t sAm, int64_t sAk, const double* B, int64_t sBb, int64_t sBk,
           int64_t sBn, double beta, double* C, int64_t sCb, int64_t sCm, int64_t sCn) {
@@ -498,72 +697,62 @@ void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, 
     contract_direct(c, a, A, B, C);
     return;
   }
-  if (c.root->gemm_mode != 1 && batch * M * N * K >= (int64_t(1) << 23) && M >= 16 && N >= 16 && K >= 16) {
+  const GemmArgs g{batch, M, N, K, alpha, A, sAb, sAm, sAk, B, sBb, sBk, sBn, beta, C, sCb, sCm, sCn};
+  const bool oz_ok = c.root->gemm_mode != 1 && M >= 16 && N >= 16 && K >= 16;
+  Ctx& r = *c.root;
+  if (r.autotune || !r.tuned.empty()) {
+    const GemmKey key = gemm_key(c, g);
+    auto it = r.tuned.find(key);
+    if (it == r.tuned.end() && r.autotune) it = r.tuned.emplace(key, tune_gemm(c, g, oz_ok)).first;
+    if (it != r.tuned.end()) {
+      const GemmPick& pk = it->second;
+      if (pk.engine == 1 && oz_ok) {
+        gemm_ozaki(c, batch, M, N, K, alpha, A, sAb, sAm, sAk, B, sBb, sBk, sBn, beta, C, sCb, sCm, sCn);
+        return;
+      }
+      if (pk.engine == 0) {
+        launch_fp64(c, g, plan_fp64(c, g, pk.T, pk.splits));
+        return;
+      }
+    }
+  }
+  if (oz_ok && batch * M * N * K >= (int64_t(1) << 23)) {
     gemm_ozaki(c, batch, M, N, K, alpha, A, sAb, sAm, sAk, B, sBb, sBk, sBn, beta, C, sCb, sCm, sCn);
     return;
   }
-  // Tile and split-K choice.  On GB300 an SM retires 2 FP64 FMAs per cycle, so the FP64 pipe,
-  // not shared-memory or L2 traffic, bounds these kernels at any tile size >= 16: the time is
-  // about the FMA load of the busiest SM, ceil(CTAs / SMs) T^2 kchunk / 2 cycles, plus one more
-  // launch when K is split.  Each tile size is planned with split-K up to two CTAs per SM
-  // (at least 2 GK of k per split); the cheapest plan wins, ties going to the larger tile.
-  const int64_t target = 2 * int64_t(c.num_sms);
-  struct Plan {
-    int T;
-    int64_t splits, kchunk;
-    double cost;
-  };
-  auto plan = [&](int T) {
-    Plan p;
-    p.T = T;
-    int64_t tiles = ((M + T - 1) / T) * ((N + T - 1) / T) * batch;
-    int64_t splits = 1;
-    if (tiles < target && K > 2 * GK) {
-      int64_t want = (target + tiles - 1) / tiles;
-      int64_t maxs = (K + 2 * GK - 1) / (2 * GK);   // at least 32 k per split
-      splits = std::max<int64_t>(1, std::min<int64_t>(want, maxs));
+  launch_fp64(c, g, heuristic_plan(c, g));
+}
+
+// ------------------------------------------------------------------ GEMM autotuner
+
+void free_autotuner(Ctx& c) {
+  if (c.tune_stream) cudaStreamSynchronize(c.tune_stream);
+  if (c.tune_buf) cudaFree(c.tune_buf);
+  if (c.tune_ctr) cudaFree(c.tune_ctr);
+  for (auto& e : c.tune_ev)
+    if (e) cudaEventDestroy(e);
+  if (c.tune_stream) cudaStreamDestroy(c.tune_stream);
+  delete c.tune_pool;
+  c.tune_pool = nullptr;
+  c.tune_buf = nullptr;
+  c.tune_ctr = nullptr;
+  c.tune_stream = nullptr;
+  c.tune_cap = 0;
+}
+
+int64_t autotune_table(Ctx& c, int64_t max_rows, int64_t* rows) {
+  Ctx& r = *c.root;
+  int64_t i = 0;
+  for (const auto& kv : r.tuned) {
+    if (rows && i < max_rows) {
+      int64_t* o = rows + i * kTuneRow;
+      o[0] = kv.first[1]; o[1] = kv.first[2]; o[2] = kv.first[3]; o[3] = kv.first[4];
+      o[4] = kv.second.engine; o[5] = kv.second.T; o[6] = kv.second.splits;
+      o[7] = int64_t(kv.second.best_ns); o[8] = int64_t(kv.second.default_ns);
     }
-    int64_t kchunk = (K + splits - 1) / splits;
-    kchunk = (kchunk + GK - 1) / GK * GK;
-    splits = (K + kchunk - 1) / kchunk;
-    p.splits = splits;
-    p.kchunk = kchunk;
-    const int64_t per_sm = (tiles * splits + c.num_sms - 1) / c.num_sms;
-    p.cost = double(per_sm) * T * T * double(kchunk) / 2.0 + (splits > 1 ? 3000.0 : 0.0);
-    return p;
-  };
-  Plan best = plan(64);
-  for (int T : {32, 16}) {
-    Plan p = plan(T);
-    if (p.cost < best.cost * 0.97) best = p;
+    ++i;
   }
-  const int T = best.T;
-  const int splits = int(best.splits);
-  const int64_t kchunk = best.kchunk;
-  ProfScope ps(c, KC_GEMM, 2.0 * double(batch) * double(M) * double(N) * double(K));
-  dim3 grid(unsigned((N + T - 1) / T), unsigned((M + T - 1) / T), unsigned(batch * splits));
-  QTT_CHECK_ARG(grid.y <= 65535 && grid.z <= 65535, "gemm grid too large");
-  dim3 block(16, 16);
-  DBuf W;
-  if (splits > 1) W.reset(&c, size_t(splits) * batch * M * N);
-  double* Wp = splits > 1 ? W.p : nullptr;
-  const int64_t ntiles = int64_t(grid.x) * grid.y * batch;
-  int* ctr = (splits > 1 && c.tile_ctr && ntiles <= kTileCounters) ? c.tile_ctr : nullptr;
-  if (T == 64)
-    k_gemm<64><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
-                                             sBn, beta, C, sCb, sCm, sCn, Wp, ctr, c.guard);
-  else if (T == 32)
-    k_gemm<32><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
-                                             sBn, beta, C, sCb, sCm, sCn, Wp, ctr, c.guard);
-  else
-    k_gemm<16><<<grid, block, 0, c.stream>>>(M, N, K, kchunk, splits, batch, alpha, A, sAb, sAm, sAk, B, sBb, sBk,
-                                             sBn, beta, C, sCb, sCm, sCn, Wp, ctr, c.guard);
-  after_launch(c, "gemm");
-  if (splits > 1 && !ctr) {
-    k_splitk_reduce<<<grid_for(batch * M * N, 256), 256, 0, c.stream>>>(batch, M, N, splits, alpha, W.p, beta, C,
-                                                                        sCb, sCm, sCn, c.guard);
-    after_launch(c, "splitk_reduce");
-  }
+  return i;
 }
 
 // ------------------------------------------------------------------ permute / elementwise

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <array>
 #include <map>
 #include <stdexcept>
 #include <string>
@@ -47,13 +48,15 @@ class Pool {
   void put(void* p);
   size_t held() const { return held_; }
   // CUDA-graph capture: blocks handed out while capturing form an arena owned by the graph
-  // (they are reused among themselves during the capture and never handed to anyone else
-  // afterwards); blocks from before the capture that are freed during it return to the
-  // ordinary free list only when the capture ends.  release_capture() gives the arena back
-  // once the graph is destroyed and its last replay has finished.
-  void begin_capture();
+  // being captured (key: its owner, one arena per captured case), reused among themselves
+  // by later captures of the same owner and never handed to anyone else, so the graphs of
+  // different cases may replay concurrently.  Blocks from before the capture that are freed
+  // during it return to the ordinary free list only when the capture ends.
+  // release_capture(owner) gives that owner's arena back once its graph is destroyed and its
+  // last replay has finished.
+  void begin_capture(const void* owner);
   void end_capture();
-  void release_capture();
+  void release_capture(const void* owner);
 
  private:
   static size_t size_class(size_t bytes);
@@ -63,9 +66,9 @@ class Pool {
   void* user_;
   std::multimap<size_t, void*> free_blocks_;  // class size -> block
   std::map<void*, size_t> live_;              // block -> class size
-  bool capturing_ = false;
-  std::multimap<size_t, void*> cap_free_;     // free blocks of the graph arena
-  std::map<void*, size_t> cap_owned_;         // every block of the graph arena
+  const void* capturing_ = nullptr;           // owner of the capture in progress
+  std::map<const void*, std::multimap<size_t, void*>> cap_free_;  // owner -> free arena blocks
+  std::map<void*, const void*> cap_owned_;    // every arena block -> its owner
   std::vector<void*> deferred_;
   std::vector<std::pair<void*, size_t>> chunks_;
   char* cur_ = nullptr;
@@ -122,6 +125,18 @@ struct Profiler {
   double* dev_flops = nullptr;
 };
 
+// GEMM autotuner (qtt_dense.cu): shape key (gemm mode, batch, M, N, K, the nine strides,
+// beta != 0) and the engine picked for it by timing.
+using GemmKey = std::array<int64_t, 15>;
+struct GemmPick {
+  int engine;          // 0 FP64-pipe tiles, 1 digit-split tensor-core product, -1 not tuned
+  int T;               // FP64 tile size
+  int64_t splits;      // FP64 k splits
+  double best_ns;      // time of the pick
+  double default_ns;   // time of the cost model's choice
+};
+constexpr int kTuneRow = 9;   // batch, M, N, K, engine, T, splits, best_ns, default_ns
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -160,7 +175,23 @@ struct Ctx {
   // Limit of every bounded device wait (grid barriers of the cooperative CG), read from root.
   unsigned long long wait_ns = 2000000000ull;
   Profiler prof;
+  // GEMM autotuner (root context): when autotune is on, a GEMM shape met for the first time is
+  // timed under every candidate engine on tune_stream and the fastest is kept in tuned; shapes
+  // in tuned use their pick whether or not tuning is still on (also inside graph captures).
+  bool autotune = false;
+  std::map<GemmKey, GemmPick> tuned;
+  int64_t tune_trials = 0;
+  cudaStream_t tune_stream = nullptr;
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+  int* tune_ctr = nullptr;
+  double* tune_buf = nullptr;
+  size_t tune_cap = 0;
+  Pool* tune_pool = nullptr;   // scratch of the trials: used on tune_stream only (the pools are stream-ordered)
 };
+// Rows of the autotuner's table (kTuneRow int64 each, at most max_rows written); returns the
+// number of tuned shapes.
+int64_t autotune_table(Ctx& c, int64_t max_rows, int64_t* rows);
+void free_autotuner(Ctx& c);
 
 constexpr int kTileCounters = 16384;
 void init_tile_counters(Ctx& c);   // allocate and zero c.tile_ctr (outside stream capture of c.stream)

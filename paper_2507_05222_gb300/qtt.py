@@ -137,6 +137,9 @@ _SIGS = {
     "qtt_case_get_operator": (I, [P, I, C.POINTER(P)]),
     "qtt_case_get_vector": (I, [P, I, C.POINTER(P)]),
     "fractional_step": (I, [P, P, I, I, C.POINTER(qtt_step_info)]),
+    "qtt_ctx_set_autotune": (I, [P, I]),
+    "qtt_ctx_autotune_table": (I, [P, I, C.POINTER(C.c_int64), IP]),
+    "fractional_step_batch": (I, [P, I, C.POINTER(P), I, I, C.POINTER(qtt_step_info), IP]),
     "qtt_case_forces": (I, [P, P, DP, DP]),
     "qtt_case_use_graph": (I, [P, I]),
     "qtt_case_phase_ms": (I, [P, DP]),
@@ -239,6 +242,18 @@ class Context:
     def set_wait_limit(self, seconds: float):
         """Limit of every bounded device wait (grid barriers of the cooperative CG), default 2 s."""
         _check(lib().qtt_ctx_set_wait_limit(self.h, float(seconds)))
+
+    def set_autotune(self, on: int):
+        """1: tune GEMM shapes met from now on; 0: stop tuning (picks stay in use); -1: clear."""
+        _check(lib().qtt_ctx_set_autotune(self.h, int(on)))
+
+    def autotune_table(self) -> list[dict]:
+        n = C.c_int()
+        _check(lib().qtt_ctx_autotune_table(self.h, 0, None, C.byref(n)))
+        rows = np.zeros((max(n.value, 1), 9), dtype=np.int64)
+        _check(lib().qtt_ctx_autotune_table(self.h, n.value, rows.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(n)))
+        keys = ("batch", "M", "N", "K", "engine", "tile", "splits", "best_ns", "default_ns")
+        return [dict(zip(keys, (int(v) for v in r))) for r in rows[:n.value]]
 
     def set_gemm_mode(self, mode: int):
         """0 (default): large products on the tensor cores (digit-split FP64); 1: FP64 pipe only."""
@@ -619,7 +634,9 @@ def fractional_step(ctx: Context, case: Case, nsteps: int = 1, with_forces: bool
     p, ``finite``, C_D, C_L; plus cg_u, cg_v, cg_p) or None.  A non-zero return code raises when
     ``check`` (the exception carries the records as ``.records``)."""
     if not info:
-        _check(lib().fractional_step(ctx.h, case.h, nsteps, 0, None))
+        rc = lib().fractional_step(ctx.h, case.h, nsteps, 0, None)
+        if rc != 0 and check:
+            raise QttError(rc, lib().qtt_last_error().decode())
         return None
     recs = (qtt_step_info * max(nsteps, 1))()
     rc = lib().fractional_step(ctx.h, case.h, nsteps, 1 if with_forces else 0, recs)
@@ -630,6 +647,31 @@ def fractional_step(ctx: Context, case: Case, nsteps: int = 1, with_forces: bool
         err.records = out
         raise err
     return out
+
+
+def fractional_step_batch(ctx: Context, cases, nsteps: int = 1, with_forces: bool = False, info: bool = True,
+                          check: bool = True):
+    """Advance every case of ``cases`` by ``nsteps`` fractional steps, their step graphs replayed
+    concurrently.  Returns (records, statuses): records[i] is the list of per-step dicts of case
+    i (as fractional_step returns them; None when ``info`` is false), statuses[i] its return code.
+    The most severe non-zero code raises when ``check`` (the exception carries ``.records`` and
+    ``.statuses``)."""
+    n = len(cases)
+    hs = (P * n)(*[cs.h for cs in cases])
+    status = np.zeros(n, dtype=np.int32)
+    recs = (qtt_step_info * max(n * nsteps, 1))() if info else None
+    rc = lib().fractional_step_batch(ctx.h, n, hs, nsteps, 1 if (with_forces and info) else 0, recs,
+                                     status.ctypes.data_as(IP))
+    out = None
+    if info:
+        out = [[dict(u=_solve_dict(r.u), v=_solve_dict(r.v), p=_solve_dict(r.p), finite=r.finite, cd=r.cd,
+                     cl=r.cl, cg_u=r.u.cg_iters, cg_v=r.v.cg_iters, cg_p=r.p.cg_iters, rc=int(status[i]))
+                for r in recs[i * nsteps:(i + 1) * nsteps]] for i in range(n)]
+    if rc != 0 and check:
+        err = QttError(rc, lib().qtt_last_error().decode())
+        err.records, err.statuses = out, [int(v) for v in status]
+        raise err
+    return out, [int(v) for v in status]
 
 
 def qtt_strouhal(t, cl) -> float:
