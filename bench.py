@@ -183,6 +183,8 @@ def run_ours(args, cfg):
         ctx.set_gemm_mode(args.gemm_mode)
     if args.cg_mode is not None:
         ctx.set_cg_mode(args.cg_mode)
+    if args.precision != "fp64":
+        ctx.set_precision(args.precision)
     ne, nx, chi = cfg["n_eta"], cfg["n_xi"], cfg["chi"]
     case = qtt.Case(ctx, ne, nx, cfg["R"], cfg["Re"], cfg["dt"], chi, cfg["ordering"], fit_sweeps=cfg["fit_sweeps"],
                     mom=cfg["mom"], poi=cfg["poi"])
@@ -352,7 +354,7 @@ def run_ours(args, cfg):
     if rank == 0:
         line = {"metric": METRIC, "value": job_throughput(world, step_ms * 1e-3), "unit": "steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else f"f64+{args.precision}-contractions", "data": "synthetic",
                 "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering")}
                 | {"mom_solve": list(cfg["mom"]), "poisson_solve": list(cfg["poi"]), "fit_sweeps": cfg["fit_sweeps"],
                    "state": f"wake_field seed {cfg['seed']}", "l2": "256 MB buffer written between timed steps",
@@ -500,6 +502,47 @@ def batch_run(args):
     return line
 
 
+def precision_drift(args, cfg):
+    """Reduced contraction precision against FP64 on the timed workload: the same start state
+    advanced --drift-steps steps once with FP64 contractions and once at --precision, C_D and
+    C_L after every step, the relative drift of both, the relative difference of the final
+    fields, the solve outcomes and the step times (graph replays).  One JSON line."""
+    import torch
+    from paper_2507_05222_gb300 import qtt
+    torch.cuda.set_device(0)
+    out = {"precision_drift": args.precision, "workload": cfg["workload"], "steps": args.drift_steps}
+    fields = {}
+    for prec in ("fp64", args.precision):
+        ctx = qtt.Context(0)
+        ctx.set_precision(prec)
+        ne, nx, chi = cfg["n_eta"], cfg["n_xi"], cfg["chi"]
+        case = qtt.Case(ctx, ne, nx, cfg["R"], cfg["Re"], cfg["dt"], chi, cfg["ordering"],
+                        fit_sweeps=cfg["fit_sweeps"], mom=cfg["mom"], poi=cfg["poi"])
+        u0, v0, pad = initial_fields(cfg)
+        gu = qtt.qtt_encode(ctx, qtt.qtt_field_to_vector(ctx, u0, cfg["ordering"]), ne + nx, chi)
+        gv = qtt.qtt_encode(ctx, qtt.qtt_field_to_vector(ctx, v0, cfg["ordering"]), ne + nx, chi)
+        case.set_state(gu, gv, qtt.MPS.from_cores(ctx, pad))
+        cd, cl, st, ms = [], [], [], []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for s in range(args.drift_steps):
+            e0.record(ctx.stream)
+            r = qtt.fractional_step(ctx, case, 1, with_forces=True, check=False)[0]
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            cd.append(r["cd"]); cl.append(r["cl"]); st.append([r[k]["status"] for k in "uvp"])
+        fields[prec] = [qtt.qtt_decode(ctx, g) for g in case.get_state()]
+        out[prec] = {"cd": cd, "cl": cl, "ms_per_step_median": float(np.median(ms[1:] if len(ms) > 1 else ms)),
+                     "statuses_last": st[-1]}
+    a, b = out["fp64"], out[args.precision]
+    with np.errstate(all="ignore"):
+        out["max_rel_drift_cd"] = float(np.nanmax(np.abs(np.array(b["cd"]) - a["cd"]) / np.abs(a["cd"])))
+        out["max_rel_drift_cl"] = float(np.nanmax(np.abs(np.array(b["cl"]) - a["cl"]) / np.abs(a["cl"]).max()))
+        out["final_field_rel_diff"] = [float(np.linalg.norm(x - y) / np.linalg.norm(x))
+                                       for x, y in zip(fields["fp64"], fields[args.precision])]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -533,6 +576,12 @@ def main():
     ap.add_argument("--batch-max-bits", type=int, default=10)
     ap.add_argument("--batch-seed", type=int, default=4)
     ap.add_argument("--autotune", action="store_true", help="tune the GEMM shapes during the warm-up")
+    ap.add_argument("--precision", default="fp64", choices=("fp64", "fp32", "tf32", "bf16"),
+                    help="contraction precision of the step (reduced: digit-split products keeping 3/2/1 digits; "
+                         "the Poisson solve, divergence, decompositions and local CG stay FP64)")
+    ap.add_argument("--drift-steps", type=int, default=0,
+                    help="precision study: this many steps at FP64 and at --precision from the same state, C_D/C_L "
+                         "drift and final field difference (one JSON line; no bench line)")
     ap.add_argument("--sweep-seeds", type=int, default=10)
     ap.add_argument("--eager", action="store_true",
                     help="with --profile-one-step: launch the step kernel by kernel (ncu cannot profile kernel "
@@ -552,6 +601,9 @@ def main():
         return
     if args.batch:
         batch_run(args)
+        return
+    if args.drift_steps:
+        precision_drift(args, cfg)
         return
     if args.impl == "reference":
         run_reference(args, cfg)

@@ -67,12 +67,29 @@ typedef struct qtt_case qtt_case;
 typedef void* (*qtt_alloc_fn)(size_t bytes, void* user);
 typedef void (*qtt_free_fn)(void* ptr, void* user);
 
+/* Contraction precision (the precision study of Sec. IV.C's cost breakdown: the contractions
+ * are the dominant cost).  QTT_PREC_FP64: every product is FP64 (FP64 pipe, or the exact
+ * seven-digit split on the tensor cores).  The reduced modes run every core contraction that
+ * reaches the batched GEMM (M, N, K >= 16) as a digit-split bf16 tensor-core product keeping
+ * the leading digits of each operand (8-bit balanced digits, rounded to nearest relative to
+ * the row's or column's largest entry) with exact integer accumulation: QTT_PREC_FP32 3 digits
+ * (24 bits, relative error ~2^-24 of |A||B|), QTT_PREC_TF32 2 digits (16 bits, ~2^-16; finer
+ * than TF32's 11), QTT_PREC_BF16 1 digit (8 bits, ~2^-8).  FP64 is kept for the small direct
+ * contractions, the QR and eigen decompositions of the rounding (and their refinement
+ * products), the local CG solves, and in the step for the divergence and the Poisson solve. */
+#define QTT_PREC_FP64 0
+#define QTT_PREC_FP32 1
+#define QTT_PREC_TF32 2
+#define QTT_PREC_BF16 3
+
 /* Truncation rule of every rounding (Sec. II: keep the first chi singular values, or those
  * above a threshold): keep k = min(chi_max, structural rank, #{sigma_i > rel_tol sigma_1});
- * rel_tol = 0 keeps the structural count (fixed bond profile min(2^k, 2^(n-k), chi_max)). */
+ * rel_tol = 0 keeps the structural count (fixed bond profile min(2^k, 2^(n-k), chi_max)).
+ * prec: QTT_PREC_* of the contractions of the call (0: FP64). */
 typedef struct {
   int chi_max;
   double rel_tol;
+  int prec;
 } qtt_trunc;
 
 typedef struct {
@@ -287,6 +304,10 @@ int qtt_check_recip(qtt_ctx* ctx, int n, const double* x, double* err2);
  * pick whether tuning is on or off (on = 0); on = -1 clears the table and turns tuning off.
  * Results of a tuned product differ from the cost model's only in rounding order. */
 int qtt_ctx_set_autotune(qtt_ctx* ctx, int on);
+/* Contraction precision (QTT_PREC_*) of the fractional steps and solves run on this context
+ * (the operations taking a qtt_trunc use its prec field instead).  Read when a step graph is
+ * captured: set it before a case's first step, or call qtt_case_set_state again after. */
+int qtt_ctx_set_precision(qtt_ctx* ctx, int prec);
 /* The tuner's table: *count = number of tuned shapes; up to max_rows rows of 9 int64 are
  * written to rows: batch, M, N, K, engine (0 FP64 tiles, 1 digit-split tensor-core product,
  * -1 not tunable), tile, k splits, time of the pick (ns), time of the cost model's choice (ns). */

@@ -47,6 +47,7 @@ void check_mps(const qtt_mps* x, const char* what) {
 void check_trunc(const qtt_trunc& t) {
   if (t.chi_max < 1) throw Error(QTT_ERR_ARG, "trunc: chi_max must be >= 1");
   if (!(t.rel_tol >= 0.0) || !std::isfinite(t.rel_tol)) throw Error(QTT_ERR_ARG, "trunc: rel_tol must be >= 0");
+  prec_digits(t.prec);
 }
 
 void check_solve_opts(const qtt_solve_opts& o, const char* what) {
@@ -479,6 +480,7 @@ int qtt_round(qtt_ctx* ctx, const qtt_mps* x, qtt_trunc tr, qtt_mps** out, qtt_r
   check_mps(x, "round");
   check_trunc(tr);
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  DigitsScope prec(c, prec_digits(tr.prec));
   DiscScope disc(c, info != nullptr);
   qtt_mps* y = round_any(c, x, tr.chi_max, tr.rel_tol);
   fill_info(c, y, info, &disc);
@@ -496,6 +498,7 @@ int mps_axpby_round(qtt_ctx* ctx, double alpha, const qtt_mps* x, double beta, c
   QTT_CHECK_ARG(std::isfinite(alpha) && std::isfinite(beta), "axpby: non-finite coefficient");
   check_trunc(tr);
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  DigitsScope prec(c, prec_digits(tr.prec));
   std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> s(direct_sum(c, alpha, x, beta, y), free_mps);
   DiscScope disc(c, info != nullptr);
   qtt_mps* z = round_any(c, s.get(), tr.chi_max, tr.rel_tol);
@@ -512,6 +515,7 @@ int mpo_apply_round(qtt_ctx* ctx, const qtt_mpo* M, const qtt_mps* x, qtt_trunc 
   QTT_CHECK_ARG(M->n == x->n && M->d == x->d, "apply: operator and vector differ in n or d");
   check_trunc(tr);
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  DigitsScope prec(c, prec_digits(tr.prec));
   qtt_mps* y;
   DiscScope disc(c, info != nullptr);
   if (tr.rel_tol > 0.0) {
@@ -535,6 +539,7 @@ int mps_hadamard_round(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, qtt_tru
   QTT_CHECK_ARG(sweeps >= 0 && sweeps <= 1000, "hadamard: sweeps in [0, 1000]");
   check_trunc(tr);
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  DigitsScope prec(c, prec_digits(tr.prec));
   qtt_mps* y;
   bool canonical;
   if (init) {
@@ -642,6 +647,13 @@ int qtt_ctx_set_autotune(qtt_ctx* ctx, int on) {
   } else {
     c.autotune = on == 1;
   }
+  API_END
+}
+
+int qtt_ctx_set_precision(qtt_ctx* ctx, int prec) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx, "ctx is null");
+  reinterpret_cast<Ctx*>(ctx)->digits = prec_digits(prec);
   API_END
 }
 

@@ -633,7 +633,10 @@ void step(Ctx& c, Case& cs, double* rec, bool with_forces) {
   ph.reset(new ProfScope(c, KC_PH_POI));
   std::vector<Term> pr = {Term::mpo(1.0, cs.Px, us.get()), Term::mpo(1.0, cs.Pz, vs.get())};
   if (cs.bcdiv_w) pr.push_back(Term::vec(1.0, cs.bcdiv_w));
-  als(c, cs.Ap, pr, cs.p, P.poi, true, ctl + 2, &cs.body_launches[2]);
+  {
+    DigitsScope fp64(c, kDigitsFP64);   // the divergence and the Poisson solve stay FP64 at any precision
+    als(c, cs.Ap, pr, cs.p, P.poi, true, ctl + 2, &cs.body_launches[2]);
+  }
   // projection v = v* - dt grad_h p (one fit each, warm start v*)
   cs.mark(c, 3);
   ph.reset(new ProfScope(c, KC_PH_PROJ));

@@ -567,7 +567,7 @@ void launch_fp64(Ctx& c, const GemmArgs& g, const Plan& best) {
 
 GemmKey gemm_key(const Ctx& c, const GemmArgs& g) {
   return GemmKey{int64_t(c.root->gemm_mode), g.batch, g.M, g.N, g.K, g.sAb, g.sAm, g.sAk, g.sBb, g.sBk, g.sBn,
-                 g.sCb, g.sCm, g.sCn, g.beta == 0.0 ? 0 : 1};
+                 g.sCb, g.sCm, g.sCn, g.beta == 0.0 ? 0 : 1, int64_t(c.root->digits)};
 }
 
 // Largest element offset + 1 of a strided view (non-negative strides).
@@ -616,6 +616,7 @@ GemmPick tune_gemm(Ctx& c, const GemmArgs& g, bool oz_ok) {
   t.num_sms = c.num_sms;
   t.root = &t;
   t.gemm_mode = r.gemm_mode;
+  t.digits = r.digits;
   t.tile_ctr = r.tune_ctr;
   double* A = r.tune_buf;
   double* B = A + na;
@@ -700,6 +701,10 @@ void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, 
   const GemmArgs g{batch, M, N, K, alpha, A, sAb, sAm, sAk, B, sBb, sBk, sBn, beta, C, sCb, sCm, sCn};
   const bool oz_ok = c.root->gemm_mode != 1 && M >= 16 && N >= 16 && K >= 16;
   Ctx& r = *c.root;
+  if (r.digits < kDigitsFP64 && M >= 16 && N >= 16 && K >= 16) {   // reduced contraction precision
+    gemm_ozaki(c, batch, M, N, K, alpha, A, sAb, sAm, sAk, B, sBb, sBk, sBn, beta, C, sCb, sCm, sCn);
+    return;
+  }
   if (r.autotune || !r.tuned.empty()) {
     const GemmKey key = gemm_key(c, g);
     auto it = r.tuned.find(key);
@@ -724,6 +729,16 @@ void gemm(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, 
 }
 
 // ------------------------------------------------------------------ GEMM autotuner
+
+int prec_digits(int prec) {
+  switch (prec) {
+    case QTT_PREC_FP64: return kDigitsFP64;
+    case QTT_PREC_FP32: return 3;
+    case QTT_PREC_TF32: return 2;
+    case QTT_PREC_BF16: return 1;
+    default: throw Error(QTT_ERR_ARG, "precision must be QTT_PREC_FP64, _FP32, _TF32 or _BF16");
+  }
+}
 
 void free_autotuner(Ctx& c) {
   if (c.tune_stream) cudaStreamSynchronize(c.tune_stream);

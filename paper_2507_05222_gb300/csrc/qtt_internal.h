@@ -126,8 +126,8 @@ struct Profiler {
 };
 
 // GEMM autotuner (qtt_dense.cu): shape key (gemm mode, batch, M, N, K, the nine strides,
-// beta != 0) and the engine picked for it by timing.
-using GemmKey = std::array<int64_t, 15>;
+// beta != 0, digits) and the engine picked for it by timing.
+using GemmKey = std::array<int64_t, 16>;
 struct GemmPick {
   int engine;          // 0 FP64-pipe tiles, 1 digit-split tensor-core product, -1 not tuned
   int T;               // FP64 tile size
@@ -165,6 +165,10 @@ struct Ctx {
   // splitting, see qtt_ozaki.cu; engine kDigitProductsOnTc05), the rest on the FP64 pipe;
   // 1 = everything on the FP64 pipe; 2 = digit products on mma.sync; 3 = digit products on tcgen05.
   int gemm_mode = 0;
+  // Digits of each operand the digit-split products keep (read from the root): kDigitsFP64 =
+  // exact FP64 products; 3, 2, 1 = the reduced contraction precisions (QTT_PREC_FP32, _TF32,
+  // _BF16), which also send every batched GEMM with M, N, K >= 16 to the digit-split product.
+  int digits = 7;
   // Per-tile arrival counters of split-K GEMMs on this context's stream (kTileCounters ints,
   // zero between launches: the last CTA of a tile resets its counter).
   int* tile_ctr = nullptr;
@@ -194,6 +198,17 @@ int64_t autotune_table(Ctx& c, int64_t max_rows, int64_t* rows);
 void free_autotuner(Ctx& c);
 
 constexpr int kTileCounters = 16384;
+constexpr int kDigitsFP64 = 7;
+int prec_digits(int prec);   // QTT_PREC_* -> digits (throws QTT_ERR_ARG for another value)
+
+// Sets the root context's contraction digits for a scope (FP64 regions inside a reduced-
+// precision step: eigen and QR refinement products, the Poisson phase).
+struct DigitsScope {
+  Ctx& r;
+  int saved;
+  DigitsScope(Ctx& c, int d) : r(*c.root), saved(c.root->digits) { r.digits = d; }
+  ~DigitsScope() { r.digits = saved; }
+};
 void init_tile_counters(Ctx& c);   // allocate and zero c.tile_ctr (outside stream capture of c.stream)
 void free_tile_counters(Ctx& c);
 

@@ -860,6 +860,7 @@ static void qr_cluster_shape(int m, int n, int& nb, int& cs) {
 
 void qr(Ctx& c, int count, int m, int n, int trans, const double* A, int64_t in_stride, double* Q, int64_t q_stride,
         double* R, int64_t r_stride, int path) {
+  DigitsScope fp64(c, kDigitsFP64);   // the decompositions and their refinement products stay FP64
   if (count <= 0 || n <= 0 || m <= 0) return;
   init_kernel_attributes();
   int kk = std::min(m, n);
@@ -899,6 +900,7 @@ void check_recip(Ctx& c, int n, const double* x_dev, double* err_dev) {
 
 // Accurate SVD of small matrices: G (m x n, m >= n) = U diag(s) V^T.
 void svd_small(Ctx& c, int m, int n, const double* G, double* U, double* s, double* V) {
+  DigitsScope fp64(c, kDigitsFP64);   // the decompositions and their refinement products stay FP64
   QTT_CHECK_ARG(m >= n, "svd: needs m >= n");
   size_t sm = (size_t(m) * n + size_t(n) * n + n) * sizeof(double) + n * sizeof(int);
   if (sm > 220 * 1024) throw Error(QTT_ERR_UNSUPPORTED, "svd: matrix too large for one CTA");
@@ -968,6 +970,7 @@ constexpr float JAC_TOL2_FULL = QTT_JAC_TOL2_FULL;
 constexpr float JAC_TOL2_TAIL = QTT_JAC_TOL2_TAIL;
 
 void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep) {
+  DigitsScope fp64(c, kDigitsFP64);   // the decompositions and their refinement products stay FP64
   QTT_CHECK_ARG(n >= 1, "eigh: n >= 1");
   if (keep <= 0 || keep > n) keep = n;
   if (n > 160) throw Error(QTT_ERR_UNSUPPORTED, "eigh: n > 160 not supported");

@@ -59,7 +59,7 @@ __global__ void k_oz_rowexp(int64_t batch, int64_t R, int64_t K, const double* _
 // fastest when X is contiguous along k, else r fastest, so that the reads coalesce.
 __global__ void k_oz_digits(int64_t batch, int64_t R, int64_t K, int64_t Kp, const double* __restrict__ X, int64_t sB,
                             int64_t sR, int64_t sK, const int* __restrict__ ex, __nv_bfloat16* __restrict__ out,
-                            const int* __restrict__ guard) {
+                            const int* __restrict__ guard, int P) {
   if (guard && *guard == 0) return;
   const int64_t total = batch * R * Kp;
   const bool kfast = (sK == 1) || (sR != 1);
@@ -83,7 +83,7 @@ __global__ void k_oz_digits(int64_t batch, int64_t R, int64_t K, int64_t Kp, con
     for (int s = OZ_S - 1; s >= 1; --s) {
       const long long dg = ((F + 128) & 255) - 128;
       F = (F - dg) >> 8;
-      o[int64_t(s) * R * Kp] = __float2bfloat16_rn(float(dg));
+      if (s < P) o[int64_t(s) * R * Kp] = __float2bfloat16_rn(float(dg));
     }
     o[0] = __float2bfloat16_rn(float(F));   // |F| <= 128
   }
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(OZ_THREADS)
     k_oz_gemm(int64_t M, int64_t N, int64_t Kp, int kc, int splits, int64_t ksplit, int64_t batch,
               const __nv_bfloat16* __restrict__ As, const int* __restrict__ ea, const __nv_bfloat16* __restrict__ Bs,
               const int* __restrict__ eb, double alpha, double beta, double* __restrict__ C, int64_t sCb, int64_t sCm,
-              int64_t sCn, double* __restrict__ W, const int* __restrict__ guard) {
+              int64_t sCn, double* __restrict__ W, const int* __restrict__ guard, int P) {
   if (guard && *guard == 0) return;
   extern __shared__ __align__(16) unsigned char oz_smem[];
   const int lds = kc + 8;
@@ -126,14 +126,14 @@ __global__ void __launch_bounds__(OZ_THREADS)
     const int kw = int(kend - k0 < int64_t(kc) ? kend - k0 : int64_t(kc));   // multiple of 16
     const int v8 = kw / 8;                                                    // 16-byte vectors per row
     __syncthreads();
-    for (int idx = threadIdx.x; idx < OZ_S * OZ_BM * v8; idx += OZ_THREADS) {
+    for (int idx = threadIdx.x; idx < P * OZ_BM * v8; idx += OZ_THREADS) {
       const int s = idx / (OZ_BM * v8), rem = idx - s * OZ_BM * v8, row = rem / v8, c8 = rem - row * v8;
       const int64_t gm = m0 + row;
       const bool in = gm < M;
       cp_async16(sA + (size_t(s) * OZ_BM + row) * lds + c8 * 8,
                  in ? As + ((b * OZ_S + s) * M + gm) * Kp + k0 + c8 * 8 : As, in);
     }
-    for (int idx = threadIdx.x; idx < OZ_S * OZ_BN * v8; idx += OZ_THREADS) {
+    for (int idx = threadIdx.x; idx < P * OZ_BN * v8; idx += OZ_THREADS) {
       const int s = idx / (OZ_BN * v8), rem = idx - s * OZ_BN * v8, row = rem / v8, c8 = rem - row * v8;
       const int64_t gn = n0 + row;
       const bool in = gn < N;
@@ -143,13 +143,13 @@ __global__ void __launch_bounds__(OZ_THREADS)
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    for (int t = 2; t <= OZ_S + 1; ++t) {
+    for (int t = 2; t <= P + 1; ++t) {
       float c32[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) c32[i][q] = 0.f;
-      const int s_lo = max(1, t - OZ_S), s_hi = min(OZ_S, t - 1);
+      const int s_lo = max(1, t - P), s_hi = min(P, t - 1);
       for (int s = s_lo; s <= s_hi; ++s) {
         const int u = t - s;
         const __nv_bfloat16* a_base = sA + (size_t(s - 1) * OZ_BM + warp * 16) * lds;
@@ -241,6 +241,7 @@ void gemm_ozaki(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double a
                 double* C, int64_t sCb, int64_t sCm, int64_t sCn) {
   QTT_CHECK_ARG(batch >= 1 && M >= 1 && N >= 1 && K >= 1, "gemm_ozaki: empty product");
   init_ozaki_attributes();
+  const int P = c.root->digits;   // digits of each operand the product uses (7: FP64-exact)
   const int64_t Kp = (K + 15) / 16 * 16;
   const int kc = int(std::min<int64_t>(OZ_KC, Kp));
   // digit slices (bf16) and exponents, carved from the pool in doubles
@@ -259,10 +260,10 @@ void gemm_ozaki(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double a
     after_launch(c, "oz_rowexp_b");
     const int64_t ta = batch * M * Kp, tb = batch * N * Kp;
     k_oz_digits<<<unsigned(std::min<int64_t>((ta + 255) / 256, 8192)), 256, 0, c.stream>>>(batch, M, K, Kp, A, sAb,
-                                                                                          sAm, sAk, ea, As, c.guard);
+                                                                                          sAm, sAk, ea, As, c.guard, P);
     after_launch(c, "oz_digits_a");
     k_oz_digits<<<unsigned(std::min<int64_t>((tb + 255) / 256, 8192)), 256, 0, c.stream>>>(batch, N, K, Kp, B, sBb,
-                                                                                          sBn, sBk, eb, Bs, c.guard);
+                                                                                          sBn, sBk, eb, Bs, c.guard, P);
     after_launch(c, "oz_digits_b");
   }
   // Split K (in whole chunks) until the grid covers the SMs once: this kernel holds one CTA per
@@ -279,13 +280,13 @@ void gemm_ozaki(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double a
   DBuf Wb;
   if (splits > 1) Wb.reset(&c, size_t(splits) * batch * M * N);
   const int mode = c.root->gemm_mode;
-  if ((mode == 3 || (mode == 0 && kDigitProductsOnTc05)) && !c.guard && tc05_fits(Kp)) {
+  if (P == OZ_S && (mode == 3 || (mode == 0 && kDigitProductsOnTc05)) && !c.guard && tc05_fits(Kp)) {
     oz_gemm_tc05(c, batch, M, N, Kp, int(splits), ksplit, As, ea, Bs, eb, alpha, beta, C, sCb, sCm, sCn,
                  splits > 1 ? Wb.p : nullptr);
   } else {
     k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(kc), c.stream>>>(M, N, Kp, kc, int(splits), ksplit, batch, As, ea, Bs,
                                                                  eb, alpha, beta, C, sCb, sCm, sCn,
-                                                                 splits > 1 ? Wb.p : nullptr, c.guard);
+                                                                 splits > 1 ? Wb.p : nullptr, c.guard, P);
     after_launch(c, "oz_gemm");
   }
   if (splits > 1) {
@@ -305,7 +306,7 @@ void oz_split_rows(Ctx& c, int64_t R, int64_t K, int64_t Kp, const double* X, in
   after_launch(c, "oz_rowexp");
   const int64_t t = R * Kp;
   k_oz_digits<<<unsigned(std::min<int64_t>((t + 255) / 256, 8192)), 256, 0, c.stream>>>(
-      1, R, K, Kp, X, 0, sR, sK, ex, static_cast<__nv_bfloat16*>(out), c.guard);
+      1, R, K, Kp, X, 0, sR, sK, ex, static_cast<__nv_bfloat16*>(out), c.guard, OZ_S);
   after_launch(c, "oz_digits");
 }
 

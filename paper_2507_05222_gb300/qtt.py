@@ -33,7 +33,10 @@ class QttError(RuntimeError):
 
 
 class qtt_trunc(C.Structure):
-    _fields_ = [("chi_max", C.c_int), ("rel_tol", C.c_double)]
+    _fields_ = [("chi_max", C.c_int), ("rel_tol", C.c_double), ("prec", C.c_int)]
+
+
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 
 
 class qtt_round_info(C.Structure):
@@ -138,6 +141,7 @@ _SIGS = {
     "qtt_case_get_vector": (I, [P, I, C.POINTER(P)]),
     "fractional_step": (I, [P, P, I, I, C.POINTER(qtt_step_info)]),
     "qtt_ctx_set_autotune": (I, [P, I]),
+    "qtt_ctx_set_precision": (I, [P, I]),
     "qtt_ctx_autotune_table": (I, [P, I, C.POINTER(C.c_int64), IP]),
     "fractional_step_batch": (I, [P, I, C.POINTER(P), I, I, C.POINTER(qtt_step_info), IP]),
     "qtt_case_forces": (I, [P, P, DP, DP]),
@@ -242,6 +246,10 @@ class Context:
     def set_wait_limit(self, seconds: float):
         """Limit of every bounded device wait (grid barriers of the cooperative CG), default 2 s."""
         _check(lib().qtt_ctx_set_wait_limit(self.h, float(seconds)))
+
+    def set_precision(self, prec: str):
+        """Contraction precision of the steps and solves on this context: fp64, fp32, tf32, bf16."""
+        _check(lib().qtt_ctx_set_precision(self.h, PREC[prec]))
 
     def set_autotune(self, on: int):
         """1: tune GEMM shapes met from now on; 0: stop tuning (picks stay in use); -1: clear."""
@@ -402,8 +410,8 @@ class MPO:
 
 # ------------------------------------------------------------------ operations (C-ABI names)
 
-def _trunc(chi, rel_tol):
-    return qtt_trunc(int(chi), float(rel_tol))
+def _trunc(chi, rel_tol, prec="fp64"):
+    return qtt_trunc(int(chi), float(rel_tol), PREC[prec])
 
 
 def _info_ptr(out_info):
@@ -453,37 +461,39 @@ def qtt_vector_to_field(ctx: Context, vec, n_eta: int, n_xi: int, ordering: str)
     return out.reshape(2 ** n_eta, 2 ** n_xi)
 
 
-def qtt_round(ctx: Context, x: MPS, chi: int, rel_tol: float = 0.0, out_info=None) -> MPS:
+def qtt_round(ctx: Context, x: MPS, chi: int, rel_tol: float = 0.0, out_info=None, prec: str = "fp64") -> MPS:
     """TT-rounding; ``out_info`` (a dict, optional) receives max_bond, norm, discarded_norm."""
     h = P()
     ri = _round_info(out_info)
-    _check(lib().qtt_round(ctx.h, x.h, _trunc(chi, rel_tol), C.byref(h), _info_ptr(ri)))
+    _check(lib().qtt_round(ctx.h, x.h, _trunc(chi, rel_tol, prec), C.byref(h), _info_ptr(ri)))
     _fill_round(ri)
     return MPS(ctx, h)
 
 
 def mps_axpby_round(ctx: Context, alpha: float, x: MPS, beta: float, y: MPS, chi: int, rel_tol: float = 0.0,
-                    out_info=None) -> MPS:
+                    out_info=None, prec: str = "fp64") -> MPS:
     h = P()
     ri = _round_info(out_info)
-    _check(lib().mps_axpby_round(ctx.h, alpha, x.h, beta, y.h, _trunc(chi, rel_tol), C.byref(h), _info_ptr(ri)))
+    _check(lib().mps_axpby_round(ctx.h, alpha, x.h, beta, y.h, _trunc(chi, rel_tol, prec), C.byref(h),
+                                 _info_ptr(ri)))
     _fill_round(ri)
     return MPS(ctx, h)
 
 
-def mpo_apply_round(ctx: Context, M: MPO, x: MPS, chi: int, rel_tol: float = 0.0, out_info=None) -> MPS:
+def mpo_apply_round(ctx: Context, M: MPO, x: MPS, chi: int, rel_tol: float = 0.0, out_info=None,
+                    prec: str = "fp64") -> MPS:
     h = P()
     ri = _round_info(out_info)
-    _check(lib().mpo_apply_round(ctx.h, M.h, x.h, _trunc(chi, rel_tol), C.byref(h), _info_ptr(ri)))
+    _check(lib().mpo_apply_round(ctx.h, M.h, x.h, _trunc(chi, rel_tol, prec), C.byref(h), _info_ptr(ri)))
     _fill_round(ri)
     return MPS(ctx, h)
 
 
 def mps_hadamard_round(ctx: Context, a: MPS, b: MPS, chi: int, sweeps: int = 2, init: MPS | None = None,
-                       out_info=None) -> MPS:
+                       out_info=None, prec: str = "fp64") -> MPS:
     h = P()
     ri = _round_info(out_info)
-    _check(lib().mps_hadamard_round(ctx.h, a.h, b.h, _trunc(chi, 0.0), init.h if init is not None else None,
+    _check(lib().mps_hadamard_round(ctx.h, a.h, b.h, _trunc(chi, 0.0, prec), init.h if init is not None else None,
                                     sweeps, C.byref(h), _info_ptr(ri)))
     _fill_round(ri)
     return MPS(ctx, h)
