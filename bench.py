@@ -43,6 +43,8 @@ WORKLOAD = dict(workload="cylinder_qtt_step_2^20_chi64", n_eta=10, n_xi=10, orde
 METRIC = "QTT fractional steps/s at 2^20 cells, chi=64, fixed oracle error; % TC/HBM roof"
 # FP64 ALU peak: 152 SMs x 2 FP64 FMA per clock (measured per SM) x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes of one full-bond cooperative CG launch, from the ncu capture of bench.py --cg-probe
+CG_LAUNCH_DRAM_BYTES = 721408
 # Bound on the GPU-oracle difference of one step (relative, per field), derived from the
 # converged step's own sensitivity at this size: a 2^-50 relative change of the initial
 # pressure moves the oracle's step by up to 1.7e-7 (v), so a difference within ten times that
@@ -365,7 +367,11 @@ def run_ours(args, cfg):
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": CG_LAUNCH_DRAM_BYTES,
+                             "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of one full-bond "
+                                              "k_cg_persistent launch (ncu --set full, --cg-probe; environments and "
+                                              "operator L2-resident): 721 KB read, 0 written",
+                             "flops_per_step": cg["flops"], "ms_eager_step": cg["ms"],
                              "kernel": "ALS local CG solves (k_cg_persistent on the FP64 pipe, k_cg_tc with digit-split "
                                        "tensor-core contractions at full-bond sites), FP64-equivalent flops counted "
                                        "on the device, over their summed CUDA-event time in one eager step",
