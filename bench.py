@@ -549,6 +549,120 @@ def precision_drift(args, cfg):
     print(json.dumps(out), flush=True)
 
 
+def warm_start_study(args):
+    """Learned Poisson warm start (the growth direction standing in for the paper's unspecified
+    preconditioner of the Poisson sweeps): a rotating-cylinder case (rate 1, Re = 100, 2^10 x
+    2^10 cells, chi = 64, dt = 1e-3) is spun up from the synthetic wake state, then --ws-train
+    steps record (u, v, p, the last pressure change) before each step and the change of the
+    pressure change over it, restricted to the 2^7 x 2^7 coarse grid on the device; a 4-layer,
+    32-channel network is trained on them (Adam, on the device).  Over --ws-test further steps
+    each state is then advanced three ways from the same (u, v, p): the Poisson solve
+    warm-started from the previous pressure (the plain start), from the linear extrapolation
+    2 p^m - p^(m-1), and from that extrapolation plus the network's prolonged prediction of its
+    error compressed to rank 16.  Reports the Poisson sweeps and CG iterations of each, the step
+    times (eager), the prediction error on the test states, and the largest difference between
+    the answers (all run to the same stop rule).  One JSON line."""
+    import torch
+    from paper_2507_05222_gb300 import inputs, qtt
+    torch.cuda.set_device(0)
+    ctx = qtt.Context(0)
+    ne = nx = 10
+    chi, lv, Hc = 64, 3, 2 ** 7
+    case = qtt.Case(ctx, ne, nx, WORKLOAD["R"], 100.0, 1e-3, chi, "interleaved", rot=1.0,
+                    fit_sweeps=WORKLOAD["fit_sweeps"], mom=WORKLOAD["mom"], poi=WORKLOAD["poi"])
+    u0, v0 = inputs.wake_field(ne, nx, 11)
+    enc = lambda f, c: qtt.qtt_encode(ctx, qtt.qtt_field_to_vector(ctx, f, "interleaved"), ne + nx, c)
+    field = lambda g: qtt.qtt_vector_to_field(ctx, qtt.qtt_decode(ctx, g), ne, nx, "interleaved")
+    case.set_state(enc(u0, chi), enc(v0, chi), qtt.MPS.from_cores(ctx, inputs.random_cores(ne + nx, chi, 13, scale=1e-8)))
+    qtt.fractional_step(ctx, case, args.ws_spinup, info=False, check=False)
+
+    def coarse_state():
+        u, v, p = case.get_state()
+        return (np.stack([qtt.grid_restrict(ctx, field(g), lv) for g in (u, v, p)]), (u, v, p))
+
+    # samples: inputs u, v, p and the last pressure change p^m - p^(m-1) on the coarse grid,
+    # target the next change p^(m+1) - p^m
+    xs, ys = [], []
+    t0 = time.time()
+    x_prev, _ = coarse_state()
+    qtt.fractional_step(ctx, case, 1, info=False, check=False)
+    for _ in range(args.ws_train):
+        x, _ = coarse_state()
+        qtt.fractional_step(ctx, case, 1, info=False, check=False)
+        pn = case.get_state()[2]
+        ys.append(qtt.grid_restrict(ctx, field(pn), lv) - x[2] - (x[2] - x_prev[2]))
+        xs.append(np.concatenate([x, (x[2] - x_prev[2])[None]]))
+        x_prev = x
+    data_s = time.time() - t0
+    X, Y = np.stack(xs), np.stack(ys)[:, None]
+    width, depth, cin = 32, 4, 4
+    g = inputs.rng(21)
+    init = []
+    for k in range(depth):
+        ci, co = (cin if k == 0 else width), (1 if k == depth - 1 else width)
+        init += [g.standard_normal(co * ci * 9) * np.sqrt(2.0 / (ci * 9)), np.zeros(co)]
+    net = qtt.NN(ctx, cin, width, depth, np.concatenate(init))
+    mom = [qtt.field_moments(ctx, X[:, c]) for c in range(cin)]
+    shift = [m for m, _ in mom]
+    scale = [1.0 / max(np.sqrt(max(r * r - m * m, 0.0)), 1e-30) for m, r in mom]
+    out_scale = qtt.field_moments(ctx, Y)[1]
+    net.set_scaling(shift, scale, out_scale)
+    t0 = time.time()
+    losses = []
+    order = inputs.rng(22).permutation(len(X))
+    for it in range(args.ws_iters):
+        idx = order[(it * 8) % len(X):(it * 8) % len(X) + 8]
+        if len(idx) == 0:
+            idx = order[:8]
+        losses.append(net.train_step(X[idx], Y[idx], 1e-3 if it < 0.8 * args.ws_iters else 2e-4))
+    train_s = time.time() - t0
+    # evaluation, eager steps (the warm start changes every step)
+    case.use_graph(False)
+    rec = {"plain": [], "learned": [], "extrapolated": []}
+    pred_err, answer_diff = [], []
+    p_prev, xc_prev = None, x_prev
+    for _ in range(args.ws_test):
+        x, (u, v, p) = coarse_state()
+        starts = {"plain": p.copy()}
+        dpc = net.predict(np.concatenate([x, (x[2] - xc_prev[2])[None]])[None])[0, 0]
+        dp = enc(qtt.grid_prolong(ctx, dpc, lv), 16)
+        if p_prev is not None:
+            starts["extrapolated"] = qtt.mps_axpby_round(ctx, 2.0, p, -1.0, p_prev, chi)
+            starts["learned"] = qtt.mps_axpby_round(ctx, 1.0, starts["extrapolated"], 1.0, dp, chi)
+        results = {}
+        for name, p0 in starts.items():
+            case.set_state(u.copy(), v.copy(), p0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            r = qtt.fractional_step(ctx, case, 1, check=False)[0]
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            rec[name].append((r["p"]["sweeps"], r["cg_p"], e0.elapsed_time(e1), r["p"]["status"]))
+            results[name] = case.get_state()
+        true_dp = qtt.grid_restrict(ctx, field(results["plain"][2]), lv) - x[2] - (x[2] - xc_prev[2])
+        pred_err.append(float(np.linalg.norm(dpc - true_dp) / max(np.linalg.norm(true_dp), 1e-300)))
+        ref = [field(gq) for gq in results["plain"]]
+        for name in results:
+            if name != "plain":
+                answer_diff.append(max(float(np.linalg.norm(field(a) - b) / np.linalg.norm(b))
+                                       for a, b in zip(results[name], ref)))
+        p_prev, xc_prev = p, x
+        case.set_state(*results["plain"])
+    summary = {k: {"poisson_sweeps_mean": float(np.mean([a[0] for a in v])) if v else None,
+                   "poisson_cg_mean": float(np.mean([a[1] for a in v])) if v else None,
+                   "step_ms_median": float(np.median([a[2] for a in v])) if v else None,
+                   "steps": len(v)} for k, v in rec.items()}
+    line = {"warm_start_study": "rotating cylinder rate 1, Re 100, 2^10 x 2^10, chi 64, dt 1e-3",
+            "train_pairs": len(X), "train_iters": args.ws_iters, "coarse_grid": [Hc, Hc],
+            "network": {"layers": depth, "channels": width, "inputs": "u, v, p, last p change (coarse)",
+                        "output": "next p change minus the last (correction to the extrapolation)"},
+            "loss_first20": float(np.mean(losses[:20])), "loss_last20": float(np.mean(losses[-20:])),
+            "test_prediction_rel_error_median": float(np.median(pred_err)),
+            "max_rel_answer_difference": max(answer_diff) if answer_diff else None,
+            "data_s": data_s, "train_s": train_s, **summary}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -585,6 +699,12 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=("fp64", "fp32", "tf32", "bf16"),
                     help="contraction precision of the step (reduced: digit-split products keeping 3/2/1 digits; "
                          "the Poisson solve, divergence, decompositions and local CG stay FP64)")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="learned Poisson warm start study (one JSON line; no bench line)")
+    ap.add_argument("--ws-spinup", type=int, default=10)
+    ap.add_argument("--ws-train", type=int, default=60)
+    ap.add_argument("--ws-iters", type=int, default=600)
+    ap.add_argument("--ws-test", type=int, default=12)
     ap.add_argument("--drift-steps", type=int, default=0,
                     help="precision study: this many steps at FP64 and at --precision from the same state, C_D/C_L "
                          "drift and final field difference (one JSON line; no bench line)")
@@ -610,6 +730,9 @@ def main():
         return
     if args.drift_steps:
         precision_drift(args, cfg)
+        return
+    if args.warm_start:
+        warm_start_study(args)
         return
     if args.impl == "reference":
         run_reference(args, cfg)

@@ -382,6 +382,50 @@ int fractional_step(qtt_ctx* ctx, qtt_case* c, int nsteps, int with_forces,
  * QTT_ERR_NONFINITE over the others); the argument checks fail with QTT_ERR_ARG before any work. */
 int fractional_step_batch(qtt_ctx* ctx, int ncases, qtt_case* const* cases, int nsteps, int with_forces,
                           qtt_step_info* per_step, int* status);
+/* -------------------------------------------------------- learned warm start (growth direction)
+ * A convolutional network on a coarse (eta, xi) grid that predicts the next step's pressure
+ * change from the fields a step starts from; its prediction, prolonged to the fine grid and
+ * compressed to a low-rank MPS, warm-starts the Poisson solve in place of the previous
+ * pressure (which stays the fallback).  Stands in for the preconditioner of the Poisson sweeps
+ * that the paper leaves unspecified (Sec. IV.C, App. G); the converged residual is required
+ * either way, so the step's answer does not depend on it.
+ * Network: `depth` 3 x 3 convolutions c_in -> width -> ... -> width -> 1 with bias and ReLU after
+ * every layer but the last; zero padding in eta (first axis), periodic in xi (second axis);
+ * NCHW FP32 tensors.  Parameters: one FP32 vector, layer by layer, weights (c_out, c_in, 3, 3)
+ * row-major then bias (c_out); the caller draws the initial values.  Training: mean squared
+ * error, Adam (beta1 0.9, beta2 0.999, eps 1e-8).  Inputs are mapped (x - shift_c) scale_c per
+ * channel and the network predicts y / out_scale (qtt_nn_set_scaling; identity by default). */
+typedef struct qtt_nn qtt_nn;
+/* Number of parameters of the network (-1 for invalid sizes). */
+int64_t qtt_nn_param_count(int c_in, int width, int depth);
+/* 1 <= c_in <= 64, 1 <= width <= 256, 1 <= depth <= 16; params: host, qtt_nn_param_count values. */
+int qtt_nn_create(qtt_ctx* ctx, int c_in, int width, int depth, const float* params, qtt_nn** out);
+int qtt_nn_free(qtt_nn* nn);
+/* Current parameters / gradient of the last training step (host, param_count values). */
+int qtt_nn_get_params(const qtt_nn* nn, float* dst);
+int qtt_nn_get_grad(const qtt_nn* nn, float* dst);
+/* Per-channel input affine (c_in values each, host) and output scale (finite, non-zero). */
+int qtt_nn_set_scaling(qtt_nn* nn, const float* in_shift, const float* in_scale, float out_scale);
+/* y (B x H x W) = network(x (B x c_in x H x W)) x out_scale; kinds QTT_HOST or QTT_DEVICE;
+ * synchronous. */
+int qtt_nn_predict(qtt_nn* nn, int B, int H, int W, const float* x, int xkind, float* y, int ykind);
+/* One Adam step of learning rate lr on the mean squared error between network(x) and
+ * y / out_scale (x: B x c_in x H x W, y: B x H x W, both of pointer kind `kind`); *loss (may be
+ * NULL) receives the loss before the step.  QTT_ERR_NONFINITE if the loss is not finite. */
+int qtt_nn_train_step(qtt_nn* nn, int B, int H, int W, const float* x, const float* y, int kind, float lr,
+                      float* loss);
+/* Grid transfers between a fine (Hc 2^levels) x (Wc 2^levels) FP64 field and its coarse
+ * Hc x Wc FP32 image (both row-major, eta the first axis): restriction averages each
+ * 2^levels x 2^levels block; prolongation applies `levels` cell-centred bilinear doublings
+ * (fine cell 2I takes 3/4 of coarse cell I and 1/4 of I - 1, cell 2I + 1 3/4 of I and 1/4 of
+ * I + 1, clamped at the ends of eta, periodic in xi).  0 <= levels <= 12; synchronous. */
+int qtt_grid_restrict(qtt_ctx* ctx, int Hc, int Wc, int levels, const double* fine, int fkind, float* coarse,
+                      int ckind);
+int qtt_grid_prolong(qtt_ctx* ctx, int Hc, int Wc, int levels, const float* coarse, int ckind, double* fine,
+                     int fkind);
+/* Mean and root mean square of n FP32 values (fixed summation order); synchronous. */
+int qtt_field_moments(qtt_ctx* ctx, int64_t n, const float* x, int kind, double* mean, double* rms);
+
 /* Replay mode of fractional_step.  enable != 0 (the default): the first call captures one
  * step as a CUDA graph on an internal stream (ordered after the context stream by events)
  * and every step replays it; the graph is dropped when the state is set again.  enable = 0:

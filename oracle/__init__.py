@@ -9,6 +9,7 @@ imports the CUDA library.
 * ``tt``      -- L1: plain TT algebra (TT-SVD, rounding, sums, mat-vec, Hadamard, fit, ALS).
 * ``qtt_ops`` -- L1: analytic QTT grid fields, metric terms, FD operators, boundary vectors.
 * ``step``    -- L1: the QTT fractional step built from the above.
+* ``nn``      -- the learned Poisson warm start: network, loss, Adam step, grid transfers.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test (tests/test_oracle_*.py)
 against the paper's worked example, closed forms, brute force or L0.

@@ -10,6 +10,7 @@
 
 #include "qtt_algebra.h"
 #include "qtt_case.h"
+#include "qtt_nn.h"
 
 namespace qtt {
 
@@ -937,6 +938,150 @@ int fractional_step_batch(qtt_ctx* ctx, int ncases, qtt_case* const* cases, int 
     set_last_error(first);
     return rc;
   }
+  API_END
+}
+
+// ---------------------------------------------------------------- learned warm start
+
+int64_t qtt_nn_param_count(int c_in, int width, int depth) {
+  if (c_in < 1 || width < 1 || depth < 1) return -1;
+  return nn_param_count(c_in, width, depth);
+}
+
+int qtt_nn_create(qtt_ctx* ctx, int c_in, int width, int depth, const float* params, qtt_nn** out) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && params && out, "nn_create: null argument");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  std::unique_ptr<Net> net(new Net(c, c_in, width, depth, params));
+  qtt_nn* h = new qtt_nn;
+  h->ctx = &c;
+  h->net = net.release();
+  *out = h;
+  API_END
+}
+
+int qtt_nn_free(qtt_nn* nn) {
+  API_BEGIN
+  if (nn) {
+    delete nn->net;
+    delete nn;
+  }
+  API_END
+}
+
+int qtt_nn_get_params(const qtt_nn* nn, float* dst) {
+  API_BEGIN
+  QTT_CHECK_ARG(nn && dst, "nn_get_params: null argument");
+  Net& n = *nn->net;
+  QTT_CUDA(cudaMemcpyAsync(dst, n.params, size_t(n.nparam) * sizeof(float), cudaMemcpyDeviceToHost, n.ctx->stream));
+  QTT_CUDA(cudaStreamSynchronize(n.ctx->stream));
+  API_END
+}
+
+int qtt_nn_get_grad(const qtt_nn* nn, float* dst) {
+  API_BEGIN
+  QTT_CHECK_ARG(nn && dst, "nn_get_grad: null argument");
+  Net& n = *nn->net;
+  QTT_CUDA(cudaMemcpyAsync(dst, n.grad, size_t(n.nparam) * sizeof(float), cudaMemcpyDeviceToHost, n.ctx->stream));
+  QTT_CUDA(cudaStreamSynchronize(n.ctx->stream));
+  API_END
+}
+
+int qtt_nn_set_scaling(qtt_nn* nn, const float* in_shift, const float* in_scale, float out_scale) {
+  API_BEGIN
+  QTT_CHECK_ARG(nn && in_shift && in_scale, "nn_set_scaling: null argument");
+  nn->net->set_scaling(in_shift, in_scale, out_scale);
+  API_END
+}
+
+static void check_nn_shape(const Net& n, int B, int H, int W) {
+  QTT_CHECK_ARG(B >= 1 && H >= 1 && W >= 1 && int64_t(B) * std::max(n.c_in, n.width) * H * W <= (int64_t(1) << 30),
+                "nn: B, H, W >= 1 and at most 2^30 activations per layer");
+}
+
+int qtt_nn_predict(qtt_nn* nn, int B, int H, int W, const float* x, int xkind, float* y, int ykind) {
+  API_BEGIN
+  QTT_CHECK_ARG(nn && x && y, "nn_predict: null argument");
+  Net& n = *nn->net;
+  check_nn_shape(n, B, H, W);
+  Ctx& c = *n.ctx;
+  const int64_t nx = int64_t(B) * n.c_in * H * W, ny = int64_t(B) * H * W;
+  DBuf xb(&c, size_t((nx + 1) / 2)), yb(&c, size_t((ny + 1) / 2));
+  float* xd = reinterpret_cast<float*>(xb.p);
+  float* yd = reinterpret_cast<float*>(yb.p);
+  QTT_CUDA(cudaMemcpyAsync(xd, x, size_t(nx) * sizeof(float), kind_in(xkind), c.stream));
+  n.predict(B, H, W, xd, yd);
+  QTT_CUDA(cudaMemcpyAsync(y, yd, size_t(ny) * sizeof(float), kind_out(ykind), c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  API_END
+}
+
+int qtt_nn_train_step(qtt_nn* nn, int B, int H, int W, const float* x, const float* y, int kind, float lr,
+                      float* loss) {
+  API_BEGIN
+  QTT_CHECK_ARG(nn && x && y, "nn_train_step: null argument");
+  QTT_CHECK_ARG(std::isfinite(lr) && lr > 0.f, "nn_train_step: lr must be positive");
+  Net& n = *nn->net;
+  check_nn_shape(n, B, H, W);
+  Ctx& c = *n.ctx;
+  const int64_t nx = int64_t(B) * n.c_in * H * W, ny = int64_t(B) * H * W;
+  DBuf xb(&c, size_t((nx + 1) / 2)), yb(&c, size_t((ny + 1) / 2)), lb(&c, 1);
+  float* xd = reinterpret_cast<float*>(xb.p);
+  float* yd = reinterpret_cast<float*>(yb.p);
+  QTT_CUDA(cudaMemcpyAsync(xd, x, size_t(nx) * sizeof(float), kind_in(kind), c.stream));
+  QTT_CUDA(cudaMemcpyAsync(yd, y, size_t(ny) * sizeof(float), kind_in(kind), c.stream));
+  const float l = n.train_step(B, H, W, xd, yd, lr, reinterpret_cast<float*>(lb.p));
+  if (loss) *loss = l;
+  if (!std::isfinite(l)) throw Error(QTT_ERR_NONFINITE, "nn_train_step: the loss is not finite");
+  API_END
+}
+
+int qtt_grid_restrict(qtt_ctx* ctx, int Hc, int Wc, int levels, const double* fine, int fkind, float* coarse,
+                      int ckind) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && fine && coarse, "grid_restrict: null argument");
+  QTT_CHECK_ARG(Hc >= 1 && Wc >= 1 && levels >= 0 && levels <= 12 &&
+                    (int64_t(Hc) * Wc << (2 * levels)) <= (int64_t(1) << 32),
+                "grid_restrict: Hc, Wc >= 1, 0 <= levels <= 12, at most 2^32 fine values");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  const int64_t nf = int64_t(Hc) * Wc << (2 * levels), nc = int64_t(Hc) * Wc;
+  DBuf fb(&c, size_t(nf)), cb(&c, size_t((nc + 1) / 2));
+  QTT_CUDA(cudaMemcpyAsync(fb.p, fine, size_t(nf) * sizeof(double), kind_in(fkind), c.stream));
+  grid_restrict(c, Hc, Wc, levels, fb.p, reinterpret_cast<float*>(cb.p));
+  QTT_CUDA(cudaMemcpyAsync(coarse, cb.p, size_t(nc) * sizeof(float), kind_out(ckind), c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  API_END
+}
+
+int qtt_grid_prolong(qtt_ctx* ctx, int Hc, int Wc, int levels, const float* coarse, int ckind, double* fine,
+                     int fkind) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && fine && coarse, "grid_prolong: null argument");
+  QTT_CHECK_ARG(Hc >= 1 && Wc >= 1 && levels >= 0 && levels <= 12 &&
+                    (int64_t(Hc) * Wc << (2 * levels)) <= (int64_t(1) << 32),
+                "grid_prolong: Hc, Wc >= 1, 0 <= levels <= 12, at most 2^32 fine values");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  const int64_t nf = int64_t(Hc) * Wc << (2 * levels), nc = int64_t(Hc) * Wc;
+  DBuf fb(&c, size_t(nf)), cb(&c, size_t((nc + 1) / 2));
+  QTT_CUDA(cudaMemcpyAsync(cb.p, coarse, size_t(nc) * sizeof(float), kind_in(ckind), c.stream));
+  grid_prolong(c, Hc, Wc, levels, reinterpret_cast<float*>(cb.p), fb.p);
+  QTT_CUDA(cudaMemcpyAsync(fine, fb.p, size_t(nf) * sizeof(double), kind_out(fkind), c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  API_END
+}
+
+int qtt_field_moments(qtt_ctx* ctx, int64_t n, const float* x, int kind, double* mean, double* rms) {
+  API_BEGIN
+  QTT_CHECK_ARG(ctx && x && mean && rms && n >= 1, "field_moments: null argument or n < 1");
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  DBuf xb(&c, size_t((n + 1) / 2)), ob(&c, 2);
+  QTT_CUDA(cudaMemcpyAsync(xb.p, x, size_t(n) * sizeof(float), kind_in(kind), c.stream));
+  field_moments(c, n, reinterpret_cast<float*>(xb.p), ob.p);
+  double h[2];
+  QTT_CUDA(cudaMemcpyAsync(h, ob.p, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
+  QTT_CUDA(cudaStreamSynchronize(c.stream));
+  *mean = h[0];
+  *rms = h[1];
   API_END
 }
 

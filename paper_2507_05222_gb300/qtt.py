@@ -92,6 +92,7 @@ P = C.c_void_p
 I, D, L, S = C.c_int, C.c_double, C.c_int64, C.c_size_t
 DP = C.POINTER(C.c_double)
 IP = C.POINTER(C.c_int)
+FLP = C.POINTER(C.c_float)
 
 _SIGS = {
     "qtt_ctx_create": (I, [C.POINTER(P), I, P, ALLOC_FN, FREE_FN, P]),
@@ -148,6 +149,17 @@ _SIGS = {
     "qtt_case_use_graph": (I, [P, I]),
     "qtt_case_phase_ms": (I, [P, DP]),
     "qtt_strouhal": (I, [DP, DP, I, DP]),
+    "qtt_nn_param_count": (L, [I, I, I]),
+    "qtt_nn_create": (I, [P, I, I, I, FLP, C.POINTER(P)]),
+    "qtt_nn_free": (I, [P]),
+    "qtt_nn_get_params": (I, [P, FLP]),
+    "qtt_nn_get_grad": (I, [P, FLP]),
+    "qtt_nn_set_scaling": (I, [P, FLP, FLP, C.c_float]),
+    "qtt_nn_predict": (I, [P, I, I, I, FLP, I, FLP, I]),
+    "qtt_nn_train_step": (I, [P, I, I, I, FLP, FLP, I, C.c_float, FLP]),
+    "qtt_grid_restrict": (I, [P, I, I, I, DP, I, FLP, I]),
+    "qtt_grid_prolong": (I, [P, I, I, I, FLP, I, DP, I]),
+    "qtt_field_moments": (I, [P, L, FLP, I, DP, DP]),
 }
 
 
@@ -682,6 +694,89 @@ def fractional_step_batch(ctx: Context, cases, nsteps: int = 1, with_forces: boo
         err.records, err.statuses = out, [int(v) for v in status]
         raise err
     return out, [int(v) for v in status]
+
+
+def _fp(a: np.ndarray):
+    return a.ctypes.data_as(FLP)
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+class NN:
+    """The learned warm start's network (FP32, on the context's device)."""
+
+    def __init__(self, ctx: Context, c_in: int, width: int, depth: int, params):
+        self.ctx, self.c_in, self.width, self.depth = ctx, c_in, width, depth
+        p = _f32(params)
+        if p.size != self.param_count(c_in, width, depth):
+            raise ValueError("params: wrong size")
+        h = P()
+        _check(lib().qtt_nn_create(ctx.h, c_in, width, depth, _fp(p), C.byref(h)))
+        self.h = h
+
+    @staticmethod
+    def param_count(c_in: int, width: int, depth: int) -> int:
+        return int(lib().qtt_nn_param_count(c_in, width, depth))
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.param_count(self.c_in, self.width, self.depth), dtype=np.float32)
+        _check(lib().qtt_nn_get_params(self.h, _fp(out)))
+        return out
+
+    def grad(self) -> np.ndarray:
+        out = np.zeros(self.param_count(self.c_in, self.width, self.depth), dtype=np.float32)
+        _check(lib().qtt_nn_get_grad(self.h, _fp(out)))
+        return out
+
+    def set_scaling(self, shift, scale, out_scale: float):
+        _check(lib().qtt_nn_set_scaling(self.h, _fp(_f32(shift)), _fp(_f32(scale)), float(out_scale)))
+
+    def predict(self, x) -> np.ndarray:
+        x = _f32(x)
+        B, _, H, W = x.shape
+        y = np.zeros((B, 1, H, W), dtype=np.float32)
+        _check(lib().qtt_nn_predict(self.h, B, H, W, _fp(x), QTT_HOST, _fp(y), QTT_HOST))
+        return y
+
+    def train_step(self, x, y, lr: float) -> float:
+        x, y = _f32(x), _f32(y)
+        B, _, H, W = x.shape
+        loss = C.c_float()
+        _check(lib().qtt_nn_train_step(self.h, B, H, W, _fp(x), _fp(y), QTT_HOST, float(lr), C.byref(loss)))
+        return float(loss.value)
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                lib().qtt_nn_free(self.h)
+            self.h = None
+        except Exception:
+            pass
+
+
+def grid_restrict(ctx: Context, fine, levels: int) -> np.ndarray:
+    f = np.ascontiguousarray(np.asarray(fine, dtype=np.float64))
+    Hc, Wc = f.shape[0] >> levels, f.shape[1] >> levels
+    out = np.zeros((Hc, Wc), dtype=np.float32)
+    _check(lib().qtt_grid_restrict(ctx.h, Hc, Wc, levels, _dp(f), QTT_HOST, _fp(out), QTT_HOST))
+    return out
+
+
+def grid_prolong(ctx: Context, coarse, levels: int) -> np.ndarray:
+    c = _f32(coarse)
+    Hc, Wc = c.shape
+    out = np.zeros((Hc << levels, Wc << levels))
+    _check(lib().qtt_grid_prolong(ctx.h, Hc, Wc, levels, _fp(c), QTT_HOST, _dp(out), QTT_HOST))
+    return out
+
+
+def field_moments(ctx: Context, x) -> tuple[float, float]:
+    a = _f32(x).ravel()
+    m, r = C.c_double(), C.c_double()
+    _check(lib().qtt_field_moments(ctx.h, a.size, _fp(a), QTT_HOST, C.byref(m), C.byref(r)))
+    return m.value, r.value
 
 
 def qtt_strouhal(t, cl) -> float:
