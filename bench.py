@@ -131,7 +131,7 @@ def oracle_start(cfg):
     u, v = ops.encode(u0, cfg["chi"]), ops.encode(v0, cfg["chi"])
     p = S.padded([np.zeros((1, 2, 1))] * (cfg["n_eta"] + cfg["n_xi"]), cfg["chi"], pad)
     o = S.StepOpts(chi=cfg["chi"], fit_sweeps=cfg["fit_sweeps"], mom=S.SolveOpts(*cfg["mom"]),
-                   poi=S.SolveOpts(*cfg["poi"]))
+                   poi=S.SolveOpts(*cfg["poi"]), poisson_warm=cfg.get("poisson_warm", "previous"))
     return ops, (u, v, p), o
 
 
@@ -142,8 +142,10 @@ def oracle_steps(cfg, k_steps, budget_s=None):
     ops, (u, v, p), o = oracle_start(cfg)
     t0 = time.perf_counter()
     done, first = 0, None
+    p_prev = None
     for _ in range(k_steps):
-        u, v, p, _ = S.step(ops, u, v, p, o)
+        u, v, pn, _ = S.step(ops, u, v, p, o, p_prev=p_prev)
+        p_prev, p = p, pn
         done += 1
         if first is None:
             first = (u, v, p)
@@ -164,7 +166,7 @@ def run_reference(args, cfg):
     line = {"impl": "reference", "metric": METRIC, "value": sps, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * dt / done, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering")}
+            "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering", "poisson_warm")}
             | {"mom_solve": list(cfg["mom"]), "poisson_solve": list(cfg["poi"]), "fit_sweeps": cfg["fit_sweeps"]},
             "cpu_baseline": {"value": sps, "unit": "steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{done} full fractional steps of the workload (numpy FP64 oracle)"},
@@ -189,7 +191,7 @@ def run_ours(args, cfg):
         ctx.set_precision(args.precision)
     ne, nx, chi = cfg["n_eta"], cfg["n_xi"], cfg["chi"]
     case = qtt.Case(ctx, ne, nx, cfg["R"], cfg["Re"], cfg["dt"], chi, cfg["ordering"], fit_sweeps=cfg["fit_sweeps"],
-                    mom=cfg["mom"], poi=cfg["poi"])
+                    mom=cfg["mom"], poi=cfg["poi"], poisson_warm=args.poisson_warm)
     u0, v0, pad = initial_fields(cfg)
     gu = qtt.qtt_encode(ctx, qtt.qtt_field_to_vector(ctx, u0, cfg["ordering"]), ne + nx, chi)
     gv = qtt.qtt_encode(ctx, qtt.qtt_field_to_vector(ctx, v0, cfg["ordering"]), ne + nx, chi)
@@ -357,7 +359,7 @@ def run_ours(args, cfg):
         line = {"metric": METRIC, "value": job_throughput(world, step_ms * 1e-3), "unit": "steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else f"f64+{args.precision}-contractions", "data": "synthetic",
-                "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering")}
+                "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering", "poisson_warm")}
                 | {"mom_solve": list(cfg["mom"]), "poisson_solve": list(cfg["poi"]), "fit_sweeps": cfg["fit_sweeps"],
                    "state": f"wake_field seed {cfg['seed']}", "l2": "256 MB buffer written between timed steps",
                    "replicas": world,
@@ -699,6 +701,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=("fp64", "fp32", "tf32", "bf16"),
                     help="contraction precision of the step (reduced: digit-split products keeping 3/2/1 digits; "
                          "the Poisson solve, divergence, decompositions and local CG stay FP64)")
+    ap.add_argument("--poisson-warm", default="previous", choices=("previous", "extrapolated"),
+                    help="Poisson warm start of the timed step: the previous pressure (default) or the fitted "
+                         "extrapolation 2 p^m - p^(m-1)")
     ap.add_argument("--warm-start", action="store_true",
                     help="learned Poisson warm start study (one JSON line; no bench line)")
     ap.add_argument("--ws-spinup", type=int, default=10)
@@ -722,6 +727,7 @@ def main():
         cfg.update(n_eta=args.n, n_xi=args.n, workload=f"cylinder_qtt_step_2^{2 * args.n}_chi{args.chi or cfg['chi']}")
     if args.chi is not None:
         cfg.update(chi=args.chi, workload=f"cylinder_qtt_step_2^{cfg['n_eta'] + cfg['n_xi']}_chi{args.chi}")
+    cfg["poisson_warm"] = args.poisson_warm
     if args.kernel_sweep:
         kernel_sweep(args)
         return

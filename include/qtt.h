@@ -338,6 +338,10 @@ typedef struct {
   int chi;                 /* bond cap of u, v, p and of every rounding in the step */
   int fit_sweeps;          /* sweeps of each variational fit in the step */
   qtt_solve_opts mom, poi; /* ALS options of the momentum and Poisson solves */
+  int poisson_warm;        /* warm start of the Poisson solve: 0 the previous pressure p^m; 1 the
+                              extrapolation 2 p^m - p^(m-1), fitted at the pressure's bonds from
+                              p^m with fit_sweeps sweeps (the first step after set_state, which
+                              has no p^(m-1), starts from p^m and runs outside the step graph) */
 } qtt_case_params;
 
 typedef struct {

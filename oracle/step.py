@@ -42,13 +42,18 @@ class StepOpts:
     fit_sweeps: int = 1
     mom: SolveOpts = field(default_factory=lambda: SolveOpts(6, 1e-8, 100))
     poi: SolveOpts = field(default_factory=lambda: SolveOpts(12, 1e-10, 500))
+    # Poisson warm start: "previous" (p^m, the reading of Sec. III.C) or "extrapolated"
+    # (2 p^m - p^(m-1), fitted at the bonds of p^m from p^m with fit_sweeps sweeps)
+    poisson_warm: str = "previous"
 
 
 def _nz(terms):
     return [t for t in terms if all(x is not None for x in t[2:])]
 
 
-def step(ops: Ops, u, v, p, o: StepOpts):
+def step(ops: Ops, u, v, p, o: StepOpts, p_prev=None):
+    """One fractional step; p_prev (the pressure of the step before; None right after the state
+    was set, when the Poisson solve starts from p) feeds the extrapolated warm start."""
     dt, Re = ops.dt, ops.Re
     chi = o.chi
     dxu = tt.round_tt(tt.mpo_mps(ops.Dx, u), chi)
@@ -65,8 +70,11 @@ def step(ops: Ops, u, v, p, o: StepOpts):
                     m.max_sweeps, m.cg_max_iter, m.cg_tol, m.rel_tol, m.stall)
     vs, iv = tt.als(ops.H, _nz([("mpo", 1.0, ops.Jdiag, rhs_v), ("vec", k, ops.JbcLap_v)]), v,
                     m.max_sweeps, m.cg_max_iter, m.cg_tol, m.rel_tol, m.stall)
+    p0 = p
+    if o.poisson_warm == "extrapolated" and p_prev is not None:
+        p0 = tt.fit([("vec", 2.0, p), ("vec", -1.0, p_prev)], p, o.fit_sweeps)
     pn, ip = tt.als(ops.Ap, _nz([("mpo", 1.0, ops.Px, us), ("mpo", 1.0, ops.Pz, vs),
-                                 ("vec", 1.0, ops.bcdiv_w)]), p, q.max_sweeps, q.cg_max_iter, q.cg_tol,
+                                 ("vec", 1.0, ops.bcdiv_w)]), p0, q.max_sweeps, q.cg_max_iter, q.cg_tol,
                     q.rel_tol, q.stall)
     un = tt.fit([("vec", 1.0, us), ("mpo", -dt, ops.Dxp, pn)], us, o.fit_sweeps)
     vn = tt.fit([("vec", 1.0, vs), ("mpo", -dt, ops.Dzp, pn)], vs, o.fit_sweeps)

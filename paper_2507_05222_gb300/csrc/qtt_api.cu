@@ -725,6 +725,7 @@ int poisson_solve(qtt_ctx* ctx, const qtt_mpo* A, const qtt_mps* b, qtt_mps* x_i
 int qtt_case_create(qtt_ctx* ctx, const qtt_case_params* p, qtt_case** out) {
   API_BEGIN
   QTT_CHECK_ARG(ctx && p && out, "case_create: null argument");
+  QTT_CHECK_ARG(p->poisson_warm == 0 || p->poisson_warm == 1, "case_create: poisson_warm must be 0 or 1");
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   std::unique_ptr<qtt_case> h(new qtt_case);
   h->ctx = &c;
@@ -779,10 +780,13 @@ int qtt_case_set_state(qtt_case* h, const qtt_mps* u, const qtt_mps* v, const qt
     if (cs.u) free_mps(cs.u);
     if (cs.v) free_mps(cs.v);
     if (cs.p) free_mps(cs.p);
+    if (cs.p_prev) free_mps(cs.p_prev);
     cs.u = nu;
     cs.v = nv;
     cs.p = np;
+    cs.p_prev = mps_copy(c, np);
   }
+  cs.prev_valid = false;   // no previous pressure: the next step starts its Poisson solve from p
   API_END
 }
 
@@ -839,7 +843,8 @@ static int read_step_records(Ctx& c, Case& cs, const double* hrec, int nsteps, b
       per_step[s].cd = forces ? r[kStepRecForces] : 0.0;
       per_step[s].cl = forces ? r[kStepRecForces + 1] : 0.0;
     }
-    if (cs.use_graph) c.root->launches += cs.graph_launches + int64_t(h[0].sweeps) * cs.body_launches[0] +
+    if (cs.use_graph && !(s == 0 && cs.last_first_eager))
+      c.root->launches += cs.graph_launches + int64_t(h[0].sweeps) * cs.body_launches[0] +
                                           int64_t(h[1].sweeps) * cs.body_launches[1] +
                                           int64_t(h[2].sweeps) * cs.body_launches[2];
     for (int i = 0; i < 3; ++i) {

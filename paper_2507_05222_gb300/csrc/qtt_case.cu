@@ -349,7 +349,7 @@ Case::~Case() {
     if (t) cudaFree(t);
   for (qtt_mpo* m : {Dx, Dz, Dxp, Dzp, H, Ap, Px, Pz, Jdiag})
     if (m) free_mpo(m);
-  for (qtt_mps* x : {bcx_u, bcz_u, bcx_v, bcz_v, JbcLap_u, JbcLap_v, bcdiv_w, absJ, u, v, p})
+  for (qtt_mps* x : {bcx_u, bcz_u, bcx_v, bcz_v, JbcLap_u, JbcLap_v, bcdiv_w, absJ, u, v, p, p_prev})
     if (x) free_mps(x);
 }
 
@@ -584,7 +584,7 @@ void case_forces(Ctx& c, Case& cs, double* out_dev) {
 // right-hand side and momentum solve of each velocity component (2 workers), the two
 // projection fits (2 workers).  The Poisson solve couples u* and v* and runs on the caller's
 // stream.  Results that cross streams are allocated before the fork.
-void step(Ctx& c, Case& cs, double* rec, bool with_forces) {
+void step(Ctx& c, Case& cs, double* rec, bool with_forces, bool extrapolate) {
   AlsCtl* ctl = reinterpret_cast<AlsCtl*>(rec);
   const qtt_case_params& P = cs.P;
   const int chi = P.chi;
@@ -622,12 +622,23 @@ void step(Ctx& c, Case& cs, double* rec, bool with_forces) {
   if (cs.JbcLap_u) mu.push_back(Term::vec(kk, cs.JbcLap_u));
   std::vector<Term> mv = {Term::mpo(1.0, cs.Jdiag, rhs_v.get())};
   if (cs.JbcLap_v) mv.push_back(Term::vec(kk, cs.JbcLap_v));
-  fork(c, 2);
+  // Poisson warm start: p^m, or (poisson_warm = 1, once a previous pressure exists) the
+  // extrapolation 2 p^m - p^(m-1) fitted at the pressure's bonds from p^m, on a third worker
+  // while the momentum solves run; p^m is kept as the next step's p^(m-1)
+  const int nw = P.poisson_warm == 1 ? 3 : 2;
+  MpsP pw = extrapolate ? mk(mps_copy(c, cs.p)) : MpsP(nullptr, free_mps);
+  fork(c, nw);
   fit(worker(c, 0), tu, rhs_u.get(), P.fit_sweeps, true);
   fit(worker(c, 1), tv_, rhs_v.get(), P.fit_sweeps, true);
   als(worker(c, 0), cs.H, mu, us.get(), P.mom, true, ctl + 0, &cs.body_launches[0]);
   als(worker(c, 1), cs.H, mv, vs.get(), P.mom, true, ctl + 1, &cs.body_launches[1]);
-  join(c, 2);
+  if (P.poisson_warm == 1) {
+    Ctx& w2 = worker(c, 2);
+    if (extrapolate) fit(w2, {Term::vec(2.0, cs.p), Term::vec(-1.0, cs.p_prev)}, pw.get(), P.fit_sweeps, true);
+    copy(w2, cs.p_prev->buf.p, cs.p->buf.p, cs.p->off[n]);
+    if (extrapolate) copy(w2, cs.p->buf.p, pw->buf.p, cs.p->off[n]);
+  }
+  join(c, nw);
   cs.mark(c, 2);
   // (iii) pressure Poisson, J-weighted (Sec. III.C): (-|J| Lap_h^p) p = -|J| (.) div(v*) / dt
   ph.reset(new ProfScope(c, KC_PH_POI));
@@ -700,7 +711,7 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
   cudaError_t err = cudaStreamBeginCapture(cs.gstream, cudaStreamCaptureModeRelaxed);
   try {
     if (err != cudaSuccess) throw Error(QTT_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(err));
-    step(c, cs, cs.rec, with_forces);
+    step(c, cs, cs.rec, with_forces, cs.P.poisson_warm == 1);
   } catch (...) {
     cs.capturing = false;
     cudaGraph_t g = nullptr;
@@ -728,13 +739,28 @@ static void capture(Ctx& c, Case& cs, bool with_forces) {
   cs.graph_forces = with_forces;
 }
 
+// The first step after the state was set has no previous pressure: with the extrapolated warm
+// start it runs eagerly from p^m (the captured graph always extrapolates).
+static bool first_step_eager(const Case& cs) { return cs.P.poisson_warm == 1 && !cs.prev_valid; }
+
 void run_steps(Ctx& c, Case& cs, int nsteps, bool with_forces, double* rec_all) {
   if (!cs.use_graph) {
-    for (int s = 0; s < nsteps; ++s) step(c, cs, rec_all + int64_t(kStepRecDoubles) * s, with_forces);
+    for (int s = 0; s < nsteps; ++s) {
+      step(c, cs, rec_all + int64_t(kStepRecDoubles) * s, with_forces, cs.P.poisson_warm == 1 && cs.prev_valid);
+      cs.prev_valid = true;
+    }
     return;
   }
-  if (!cs.gexec || cs.graph_forces != with_forces) capture(c, cs, with_forces);
-  for (int s = 0; s < nsteps; ++s) {
+  int s0 = 0;
+  cs.last_first_eager = false;
+  if (nsteps > 0 && first_step_eager(cs)) {
+    step(c, cs, rec_all, with_forces, false);
+    cs.prev_valid = true;
+    cs.last_first_eager = true;
+    s0 = 1;
+  }
+  if (s0 < nsteps && (!cs.gexec || cs.graph_forces != with_forces)) capture(c, cs, with_forces);
+  for (int s = s0; s < nsteps; ++s) {
     QTT_CUDA(cudaEventRecord(cs.ev_in, c.stream));
     QTT_CUDA(cudaStreamWaitEvent(cs.gstream, cs.ev_in, 0));
     QTT_CUDA(cudaGraphLaunch(cs.gexec, cs.gstream));
@@ -748,6 +774,18 @@ void run_steps_batch(Ctx& c, const std::vector<Case*>& cases, int nsteps, bool w
   // every graph first (captures are host work on the context's streams), then the replays:
   // one stream per case, ordered after the context stream, step s of every case enqueued
   // before step s + 1 of any
+  // cases whose first step has no previous pressure take it eagerly, on the context stream,
+  // before the replays start
+  std::vector<char> eager0(cases.size(), 0);
+  for (size_t i = 0; i < cases.size(); ++i) {
+    cases[i]->last_first_eager = false;
+    if (nsteps > 0 && first_step_eager(*cases[i])) {
+      step(c, *cases[i], rec_all + int64_t(i) * nsteps * kStepRecDoubles, with_forces, false);
+      cases[i]->prev_valid = true;
+      cases[i]->last_first_eager = true;
+      eager0[i] = 1;
+    }
+  }
   for (Case* cs : cases)
     if (!cs->gexec || cs->graph_forces != with_forces) capture(c, *cs, with_forces);
   QTT_CUDA(cudaEventRecord(cases[0]->ev_in, c.stream));
@@ -755,6 +793,7 @@ void run_steps_batch(Ctx& c, const std::vector<Case*>& cases, int nsteps, bool w
   for (int s = 0; s < nsteps; ++s)
     for (size_t i = 0; i < cases.size(); ++i) {
       Case& cs = *cases[i];
+      if (s == 0 && eager0[i]) continue;
       QTT_CUDA(cudaGraphLaunch(cs.gexec, cs.gstream));
       double* dst = rec_all + (int64_t(i) * nsteps + s) * kStepRecDoubles;
       QTT_CUDA(cudaMemcpyAsync(dst, cs.rec, kStepRecDoubles * sizeof(double), cudaMemcpyDeviceToDevice, cs.gstream));

@@ -20,6 +20,9 @@ struct Case {
           *JbcLap_v = nullptr, *bcdiv_w = nullptr, *absJ = nullptr;
   // state
   qtt_mps *u = nullptr, *v = nullptr, *p = nullptr;
+  qtt_mps* p_prev = nullptr;        // the pressure of the previous step (warm start extrapolation)
+  bool prev_valid = false;          // p_prev holds a previous step's pressure (false after set_state)
+  bool last_first_eager = false;    // the last run's first step ran eagerly (launches already counted)
   // CUDA graph of one step (captured on first use, replayed afterwards; invalidated when the
   // state buffers change).  The graph writes its per-step record (kStepRecDoubles) to rec.
   bool use_graph = true;
@@ -51,7 +54,8 @@ constexpr int kStepRecDoubles = kStepRecForces + 2;
 
 Case* build_case(Ctx& c, const qtt_case_params& P);
 // One step; writes its record to rec (device, kStepRecDoubles) and the forces when asked.
-void step(Ctx& c, Case& cs, double* rec, bool with_forces);
+// extrapolate: warm-start the Poisson solve from 2 p^m - p^(m-1) (needs poisson_warm = 1).
+void step(Ctx& c, Case& cs, double* rec, bool with_forces, bool extrapolate);
 // nsteps steps, replaying the captured graph when cs.use_graph; records into rec_all (device,
 // kStepRecDoubles per step).
 void run_steps(Ctx& c, Case& cs, int nsteps, bool with_forces, double* rec_all);

@@ -59,7 +59,7 @@ class qtt_case_params(C.Structure):
     _fields_ = [("n_eta", C.c_int), ("n_xi", C.c_int), ("ordering", C.c_int), ("D", C.c_double),
                 ("R", C.c_double), ("Re", C.c_double), ("dt", C.c_double), ("rot", C.c_double),
                 ("u_inf", C.c_double), ("chi", C.c_int), ("fit_sweeps", C.c_int),
-                ("mom", qtt_solve_opts), ("poi", qtt_solve_opts)]
+                ("mom", qtt_solve_opts), ("poi", qtt_solve_opts), ("poisson_warm", C.c_int)]
 
 
 class qtt_step_info(C.Structure):
@@ -597,11 +597,13 @@ def poisson_solve(ctx: Context, A: MPO, b: MPS, x: MPS, max_sweeps: int, rel_tol
 class Case:
     def __init__(self, ctx: Context, n_eta: int, n_xi: int, R: float, Re: float, dt: float, chi: int,
                  ordering: str = "interleaved", D: float = 1.0, rot: float = 0.0, u_inf: float = 1.0,
-                 fit_sweeps: int = 1, mom=MOM_DEFAULT, poi=POI_DEFAULT):
-        """mom, poi: ALS options (max_sweeps, rel_tol, cg_max_iter[, cg_tol[, stall]])."""
+                 fit_sweeps: int = 1, mom=MOM_DEFAULT, poi=POI_DEFAULT, poisson_warm: str = "previous"):
+        """mom, poi: ALS options (max_sweeps, rel_tol, cg_max_iter[, cg_tol[, stall]]); poisson_warm:
+        "previous" (p^m) or "extrapolated" (2 p^m - p^(m-1), fitted)."""
         self.ctx = ctx
         self.params = qtt_case_params(n_eta, n_xi, ORDERING[ordering], D, R, Re, dt, rot, u_inf, chi, fit_sweeps,
-                                      solve_opts(*mom), solve_opts(*poi))
+                                      solve_opts(*mom), solve_opts(*poi),
+                                      {"previous": 0, "extrapolated": 1}[poisson_warm])
         h = P()
         _check(lib().qtt_case_create(ctx.h, C.byref(self.params), C.byref(h)))
         self.h = h

@@ -369,3 +369,34 @@ def test_headline_step_matches_oracle(ctx):
         assert d_ <= max(10.0 * s_, 1e-10)
     assert max(diffs) < 2e-6
     assert info[0]["finite"] == 1 and np.isfinite(info[0]["cd"]) and np.isfinite(info[0]["cl"])
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_extrapolated_warm_start_steps_match_oracle(ctx, seed):
+    """Three truncated steps (12 bits, chi = 16) with the extrapolated Poisson warm start
+    (2 p^m - p^(m-1) fitted from p^m): every solve takes the oracle's sweeps and stop decision
+    and each field equals the oracle's to 1e-10 or ten times the oracle's own spread under a
+    2^-50 change of its initial pressure."""
+    from paper_2507_05222_gb300 import qtt
+    ne = nx = 6
+    R, Re, dt, chi = 40.0, 100.0, 2e-3, 16
+    ops = Q.Ops(ne, nx, R, Re, dt, "interleaved")
+    u, v, p = wake_state(ops, ne, nx, chi, seed)
+    q = (u, v, [c * (1.0 + 2.0 ** -50) for c in p])
+    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "interleaved", mom=TIGHT_MOM, poi=TIGHT_POI,
+                    poisson_warm="extrapolated")
+    case.set_state(*(qtt.MPS.from_cores(ctx, x) for x in (u, v, p)))
+    o = step_opts(chi, qtt)
+    o.poisson_warm = "extrapolated"
+    pp, qp = None, None          # no previous pressure right after set_state
+    for s in range(3):
+        info = case.fractional_step(1, check=False)
+        un, vn, pn, oi = S.step(ops, u, v, p, o, p_prev=pp)
+        qn = S.step(ops, *q, o, p_prev=qp)[:3]
+        pp, qp = p, q[2]
+        u, v, p, q = un, vn, pn, qn
+        same_solves(info[0], oi)
+        for k, g, r, r2 in zip("uvp", case.get_state(), (u, v, p), q):
+            spread = rel(tt.full(r2), tt.full(r))
+            d = rel(qtt.qtt_decode(ctx, g), tt.full(r))
+            assert d < max(TOL, 10.0 * spread), (s, seed, k, d, spread)

@@ -549,3 +549,23 @@ def test_l1_step_equals_l0_at_full_rank(ordering):
     for a, b in ((un, uf), (vn, vf), (pn, pf)):
         b = b.reshape(2 ** ne, 2 ** nx)
         assert np.abs(ops.decode(a) - b).max() <= 1e-10 * np.abs(b).max()
+
+
+def test_extrapolated_warm_start_fit_and_step():
+    """The extrapolated Poisson warm start: at full rank the fit reproduces 2 p^m - p^(m-1)
+    exactly, and the step's answer does not depend on the warm start (solves converged)."""
+    ne = nx = 3
+    ops = Q.Ops(ne, nx, 40.0, 100.0, 2e-3, "interleaved")
+    g = inputs.rng(31)
+    p = ops.encode(g.standard_normal((2 ** ne, 2 ** nx)), 8)
+    q = ops.encode(g.standard_normal((2 ** ne, 2 ** nx)), 8)
+    f = tt.fit([("vec", 2.0, p), ("vec", -1.0, q)], p, 1)
+    assert np.allclose(tt.full(f), 2 * tt.full(p) - tt.full(q), rtol=1e-12, atol=1e-12)
+    u = ops.encode(1.0 + inputs.gaussian_field(ne, nx, 1, 1e-2), 8)
+    v = ops.encode(inputs.gaussian_field(ne, nx, 2, 1e-2), 8)
+    tight = dict(chi=8, fit_sweeps=2, mom=S.SolveOpts(20, 1e-13, 300, 1e-6, 0.0),
+                 poi=S.SolveOpts(30, 1e-13, 500, 1e-6, 0.0))
+    a = S.step(ops, u, v, p, S.StepOpts(**tight))
+    b = S.step(ops, u, v, p, S.StepOpts(**tight, poisson_warm="extrapolated"), p_prev=q)
+    for x, y in zip(a[:3], b[:3]):
+        assert np.linalg.norm(tt.full(x) - tt.full(y)) <= 1e-9 * np.linalg.norm(tt.full(x))
