@@ -569,3 +569,20 @@ def test_extrapolated_warm_start_fit_and_step():
     b = S.step(ops, u, v, p, S.StepOpts(**tight, poisson_warm="extrapolated"), p_prev=q)
     for x, y in zip(a[:3], b[:3]):
         assert np.linalg.norm(tt.full(x) - tt.full(y)) <= 1e-9 * np.linalg.norm(tt.full(x))
+
+
+def test_table2_rotating_cylinder_fd_sanity():
+    """Table II (Sec. IV.B), FD row: rotating cylinder at Re = 100, rotation rate 1, grid G1,
+    R = 32, dt = 2e-3 gives a mean lift coefficient 2.4908 and St 0.1663.  The L0 oracle's long
+    run (tests/golden/table2_fd.txt, written by `python -m oracle.table2_run --time 160
+    --window 60`) must reproduce both within 1 %: this pins the force read-out (pressure and
+    viscous wall stress, App. F) and the Strouhal estimate on a developed periodic flow."""
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table2_fd.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    assert abs(vals["mean_cl"] - 2.4908) <= 0.01 * 2.4908
+    assert abs(vals["st"] - 0.1663) <= 0.01 * 0.1663
+    assert vals["mean_cd"] > 0.0
