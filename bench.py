@@ -665,6 +665,66 @@ def warm_start_study(args):
     print(json.dumps(line), flush=True)
 
 
+def steady_sweep(args):
+    """Chi sweep of the steady Re = 20 cylinder flow (Sec. IV.A.1) at a reduced grid: 2^6 x 2^7
+    cells, R = 32, dt = 1e-2, sequential bit order, uniform start, 5000 steps (t = 50); for each
+    chi in --steady-chi the QTT run's velocity magnitude against the FD reference
+    (tests/golden/steady_re20_fd.txt, the L0 oracle's run to the same time): relative L2 and max
+    errors, C_D, C_L, kinetic energy, the fraction of parameters (NVPS: MPS entries of u over grid
+    values) and ms per step.  One JSON line per chi."""
+    import torch
+    from paper_2507_05222_gb300 import inputs, qtt
+    torch.cuda.set_device(0)
+    ref = {}
+    rows = []
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "steady_re20_fd.txt")) as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            w = line.split()
+            if w[0] in ("cd", "cl", "ekin"):
+                ref[w[0]] = float(w[1])
+            elif w[0] == "shape":
+                ref["shape"] = (int(w[1]), int(w[2]))
+            else:
+                rows.append([float(x) for x in w])
+    mag_ref = np.asarray(rows)
+    ne, nx, nsteps = 6, 7, int(round(50.0 / 1e-2))
+    for chi in args.steady_chi:
+        ctx = qtt.Context(0)
+        case = qtt.Case(ctx, ne, nx, 32.0, 20.0, 1e-2, chi, "sequential", mom=(6, 1e-10, 300, 1e-2, 0.1),
+                        poi=(12, 1e-10, 500, 1e-2, 0.1))
+        # u = 1, v = 0 and p = 0 in the chi bond profile: the exact rank-1 (or zero) block plus
+        # N(0, 1e-8^2) padding (the solves keep the bond profile of their warm starts)
+        def padded(value, seed):
+            cores = inputs.random_cores(ne + nx, chi, seed, scale=1e-8)
+            for k, c in enumerate(cores):
+                c[0, :, 0] = value if k == 0 else (1.0 if value != 0.0 else 0.0)
+            return qtt.MPS.from_cores(ctx, cores)
+        case.set_state(padded(1.0, 3), padded(0.0, 4), qtt.MPS.from_cores(ctx, inputs.random_cores(ne + nx, chi, 5,
+                                                                                                 scale=1e-8)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        qtt.fractional_step(ctx, case, 1, info=False, check=False)
+        e0.record(ctx.stream)
+        qtt.fractional_step(ctx, case, nsteps - 1, info=False, check=False)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (nsteps - 1)
+        u, v, p = case.get_state()
+        fu = qtt.qtt_vector_to_field(ctx, qtt.qtt_decode(ctx, u), ne, nx, "sequential")
+        fv = qtt.qtt_vector_to_field(ctx, qtt.qtt_decode(ctx, v), ne, nx, "sequential")
+        mag = np.sqrt(fu * fu + fv * fv)
+        cd, cl = case.forces()
+        nvps = sum(int(np.prod(c.shape)) for c in u.cores()) / float(2 ** (ne + nx))
+        line = {"steady_sweep": "Re 20, 2^6 x 2^7 cells, R 32, dt 1e-2, sequential order, t = 50", "chi": chi,
+                "eps_l2_velocity_magnitude": float(np.linalg.norm(mag - mag_ref) / np.linalg.norm(mag_ref)),
+                "eps_max_velocity_magnitude": float(np.abs(mag - mag_ref).max() / np.abs(mag_ref).max()),
+                "cd": cd, "cd_fd": ref["cd"], "cd_rel_error": abs(cd - ref["cd"]) / ref["cd"], "cl": cl,
+                "ekin_rel_error": abs(0.5 * float(np.mean(mag * mag)) - ref["ekin"]) / ref["ekin"],
+                "nvps": nvps, "ms_per_step": ms, "steps": nsteps}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -704,6 +764,9 @@ def main():
     ap.add_argument("--poisson-warm", default="previous", choices=("previous", "extrapolated"),
                     help="Poisson warm start of the timed step: the previous pressure (default) or the fitted "
                          "extrapolation 2 p^m - p^(m-1)")
+    ap.add_argument("--steady-sweep", action="store_true",
+                    help="steady Re = 20 chi sweep against the FD reference (one JSON line per chi; no bench line)")
+    ap.add_argument("--steady-chi", type=int, nargs="+", default=[8, 16, 24, 32, 64])
     ap.add_argument("--warm-start", action="store_true",
                     help="learned Poisson warm start study (one JSON line; no bench line)")
     ap.add_argument("--ws-spinup", type=int, default=10)
@@ -739,6 +802,9 @@ def main():
         return
     if args.warm_start:
         warm_start_study(args)
+        return
+    if args.steady_sweep:
+        steady_sweep(args)
         return
     if args.impl == "reference":
         run_reference(args, cfg)

@@ -786,6 +786,33 @@ __global__ void k_copy_guarded(double* __restrict__ dst, const double* __restric
     dst[e] = src[e];
 }
 
+// Sc = S 2^-e with e = ilogb(max |S_ij|) (0 for a zero or non-finite matrix): a power-of-two
+// scaling, exact, that brings the largest entry into [1, 2) so that the FP32 Jacobi and the
+// squared norms of the refinement neither underflow nor overflow.  *e_out = e.
+__global__ void k_scale_pow2(int64_t n, const double* __restrict__ S, double* __restrict__ Sc, int* e_out) {
+  __shared__ double red[32];
+  __shared__ int es;
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(S[i]));
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+    es = (t > 0.0 && isfinite(t)) ? ilogb(t) : 0;
+    *e_out = es;
+  }
+  __syncthreads();
+  const int e = es;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Sc[i] = ldexp(S[i], -e);
+}
+
+// w[i] *= 2^e
+__global__ void k_unscale_pow2(int n, double* __restrict__ w, const int* __restrict__ e) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = ldexp(w[i], *e);
+}
+
 __global__ void k_frob(int64_t n, const double* __restrict__ x, double* out) {
   __shared__ double red[32];
   double s = 0;
@@ -983,9 +1010,17 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep) {
   init_kernel_attributes();
   const size_t nn = size_t(n) * n;
   DBuf X(&c, nn), Xs(&c, nn), XtX(&c, nn), AX(&c, nn), SX(&c, nn), E(&c, nn), Y(&c, nn), lam(&c, size_t(n)),
-      an(&c, 1), flags(&c, 2), part(&c, 2 * OA_BLOCKS);
+      an(&c, 1), flags(&c, 2), part(&c, 2 * OA_BLOCKS), Ssc(&c, nn);
   int* t0 = reinterpret_cast<int*>(flags.p);
   int* need = t0 + 1;
+  // work on S 2^-e (largest entry in [1, 2)): Gram matrices of small-norm trains (e.g. a field
+  // held at zero with 1e-8 padding, norms ~1e-96) would otherwise vanish in FP32 and in the
+  // squared norms of the refinement; the eigenvalues are scaled back at the end
+  DBuf escale(&c, 1);
+  int* eexp = reinterpret_cast<int*>(escale.p);
+  k_scale_pow2<<<1, 1024, 0, c.stream>>>(int64_t(nn), S, Ssc.p, eexp);
+  after_launch(c, "scale_pow2");
+  S = Ssc.p;
   {
     ProfScope ps(c, KC_EIG);
     k_jacobi_f32<<<jac_ctas, dim3(32, 32), smf, c.stream>>>(n, S, X.p, 10, nullptr, JAC_TOL2_FULL, nullptr);
@@ -1032,6 +1067,8 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep) {
   // ~eps ||S|| / gap in X^T X - I for close pairs; each step squares it.
   for (int it = 0; it < 2; ++it) newton_schulz(c, n, X.p, XtX.p, AX.p);
   copy(c, V, X.p, int64_t(nn));
+  k_unscale_pow2<<<1, 256, 0, c.stream>>>(n, w, eexp);
+  after_launch(c, "unscale_pow2");
 }
 
 }  // namespace qtt

@@ -87,3 +87,30 @@ def test_sym_eig_many_seeds(ctx, kind):
         assert np.abs(V.T @ V - np.eye(n)).max() < 1e-12, seed
         assert np.abs(w - wr).max() <= 1e-12 * scale, seed
         assert np.abs(S @ V - V * w).max() <= 1e-11 * scale, seed
+
+
+@pytest.mark.parametrize("scale", [1e-200, 1e-100, 1e-40, 1e40, 1e150])
+def test_sym_eig_extreme_scales(ctx, scale):
+    """The solver works on S 2^-e (largest entry in [1, 2)): a matrix of any magnitude has the
+    eigenvectors and the scaled eigenvalues of its unit-scale version.  Without the scaling a
+    Gram matrix of a train with norm ~1e-96 (entries ~1e-192) vanished in the FP32 stage and the
+    refinement diverged."""
+    from paper_2507_05222_gb300 import qtt
+    n = 64
+    g = inputs.rng(77)
+    Qm, _ = np.linalg.qr(g.standard_normal((n, n)))
+    lam = spectrum("geometric8", n, g)
+    S1 = (Qm * lam) @ Qm.T
+    S1 = 0.5 * (S1 + S1.T)
+    w1, V1 = qtt.qtt_sym_eig(ctx, S1)
+    w, V = qtt.qtt_sym_eig(ctx, S1 * scale)
+    assert np.all(np.isfinite(w)) and np.all(np.isfinite(V))
+    assert np.abs(w / scale - w1).max() <= 1e-12 * np.abs(w1).max()
+    assert np.abs(np.abs(V.T @ V1) - np.eye(n)).max() < 1e-6   # same eigenvectors up to sign
+
+
+def test_sym_eig_zero_matrix(ctx):
+    from paper_2507_05222_gb300 import qtt
+    w, V = qtt.qtt_sym_eig(ctx, np.zeros((16, 16)))
+    assert np.all(w == 0.0)
+    assert np.abs(V.T @ V - np.eye(16)).max() < 1e-12

@@ -313,3 +313,21 @@ def test_argument_errors(ctx):
     assert e.value.code == -1
     with pytest.raises(qtt.QttError):
         qtt.qtt_round(ctx, x, 0)
+
+
+def test_apply_round_of_a_near_zero_train(ctx):
+    """MPO-MPS product of a field held at zero inside the chi bond profile by 1e-8 padding (norm
+    ~1e-80, the start of a flow at rest): the Gram matrices are ~1e-160 and must still give the
+    oracle's product to 1e-10 (they vanished in the FP32 stage before the eigensolver scaled
+    its input)."""
+    from paper_2507_05222_gb300 import qtt
+    ne, nx, chi = 5, 5, 16
+    ops = Q.Ops(ne, nx, 32.0, 20.0, 1e-2, "sequential")
+    cores = inputs.random_cores(ne + nx, chi, 4, scale=1e-8)
+    for c in cores:
+        c[0, :, 0] = 0.0
+    ref = tt.full(tt.round_tt(tt.mpo_mps(ops.Dx, cores), chi))
+    assert 0.0 < np.linalg.norm(ref) < 1e-60
+    y = qtt.mpo_apply_round(ctx, qtt.MPO.from_cores(ctx, ops.Dx), qtt.MPS.from_cores(ctx, cores), chi)
+    d = qtt.qtt_decode(ctx, y)
+    assert np.linalg.norm(d - ref) <= 1e-10 * np.linalg.norm(ref)
