@@ -400,3 +400,39 @@ def test_extrapolated_warm_start_steps_match_oracle(ctx, seed):
             spread = rel(tt.full(r2), tt.full(r))
             d = rel(qtt.qtt_decode(ctx, g), tt.full(r))
             assert d < max(TOL, 10.0 * spread), (s, seed, k, d, spread)
+
+
+def rest_state(ne, nx, chi):
+    """A flow at rest-like start: u = 1, v = 0, p = 0 held in the chi bond profile by N(0, 1e-8^2)
+    padding (the exact rank-1 or zero block plus noise)."""
+    def padded(value, seed):
+        cores = inputs.random_cores(ne + nx, chi, seed, scale=1e-8)
+        for k, c in enumerate(cores):
+            c[0, :, 0] = value if k == 0 else (1.0 if value != 0.0 else 0.0)
+        return cores
+    return padded(1.0, 3), padded(0.0, 4), inputs.random_cores(ne + nx, chi, 5, scale=1e-8)
+
+
+def test_truncated_steps_from_rest_match_oracle(ctx):
+    """Ten truncated steps (5 + 6 bits, sequential order, chi = 8, Re = 20, dt = 1e-2) from the
+    padded uniform start: the zero fields' trains have norms ~1e-80, so their products' Gram
+    matrices test the eigensolver's scaling; each field equals the oracle's to 1e-10 or ten times
+    the oracle's own spread under a 2^-50 change of its initial pressure."""
+    from paper_2507_05222_gb300 import qtt
+    ne, nx, chi = 5, 6, 8
+    R, Re, dt = 32.0, 20.0, 1e-2
+    ops = Q.Ops(ne, nx, R, Re, dt, "sequential")
+    u, v, p = rest_state(ne, nx, chi)
+    q = (u, v, [c * (1.0 + 2.0 ** -50) for c in p])
+    case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, "sequential", mom=TIGHT_MOM, poi=TIGHT_POI)
+    case.set_state(*(qtt.MPS.from_cores(ctx, x) for x in (u, v, p)))
+    o = step_opts(chi, qtt)
+    for s in range(10):
+        info = case.fractional_step(1, check=False)
+        u, v, p, oi = S.step(ops, u, v, p, o)
+        q = S.step(ops, *q, o)[:3]
+        assert info[0]["finite"] == 1
+        for k, g, r, r2 in zip("uvp", case.get_state(), (u, v, p), q):
+            spread = rel(tt.full(r2), tt.full(r))
+            d = rel(qtt.qtt_decode(ctx, g), tt.full(r))
+            assert d < max(TOL, 10.0 * spread), (s, k, d, spread)
