@@ -811,41 +811,6 @@ void dot_dev(Ctx& c, const qtt_mps* a, const qtt_mps* b, double* out_dev) {
   copy(c, out_dev, E.p, 1);
 }
 
-// ||y|| by a left-to-right Householder QR sweep (the norm of the last core after
-// orthogonalisation): no cancellation, unlike the transfer-matrix <y, y> whose absolute
-// error is eps <|y|, |y|>.  Used when every unfolding fits the one-CTA QR; otherwise the
-// transfer-matrix value is returned (relative accuracy of the norm ~ sqrt(eps) when y is
-// a small difference of large terms).
-void norm_dev(Ctx& c, const qtt_mps* y, double* out_dev) {
-  const int n = y->n, d = y->d;
-  bool fits = true;
-  for (int k = 0; k < n; ++k)
-    if (int64_t(y->bonds[k]) * d * y->bonds[k + 1] + int64_t(y->bonds[k]) * d + y->bonds[k + 1] > 26000) fits = false;
-  if (!fits) {
-    DBuf t(&c, 1);
-    dot_dev(c, y, y, t.p);
-    sqrt_dev(c, t.p, out_dev);
-    return;
-  }
-  int r0 = 1;
-  DBuf cur(&c, size_t(y->core_size(0)));
-  copy(c, cur.p, y->core(0), int64_t(d) * y->bonds[1]);
-  for (int k = 0; k + 1 < n; ++k) {
-    int rows = r0 * d, cols = y->bonds[k + 1];
-    int kk = std::min(rows, cols);
-    DBuf Q(&c, size_t(rows) * kk), R(&c, size_t(kk) * cols);
-    qr(c, 1, rows, cols, 0, cur.p, 0, Q.p, 0, R.p, 0);
-    int r2 = y->bonds[k + 2];
-    DBuf nxt(&c, size_t(kk) * d * r2);
-    einsum(c, "ab,bsc->asc", 1.0, tv(R.p, {kk, cols}), tv(y->core(k + 1), {cols, d, r2}), 0.0, tv(nxt.p, {kk, d, r2}));
-    cur = std::move(nxt);
-    r0 = kk;
-  }
-  DBuf t(&c, 1);
-  dot(c, int64_t(r0) * d, cur.p, cur.p, t.p);
-  sqrt_dev(c, t.p, out_dev);
-}
-
 // ------------------------------------------------------------------ dense encode / decode
 
 qtt_mps* encode_dense(Ctx& c, const double* dense_dev, int n, int d, int chi, double eps) {

@@ -106,7 +106,6 @@ void cg_tc(Ctx& c, const double* L, const double* W, const double* R, const doub
            int w0, int w1, int d, int iters, const double* tol_dev, int* total_dev, const double* dinv);
 
 void dot_dev(Ctx& c, const qtt_mps* a, const qtt_mps* b, double* out_dev);
-void norm_dev(Ctx& c, const qtt_mps* y, double* out_dev);
 void sqrt_dev(Ctx& c, const double* in, double* out);
 qtt_mps* encode_dense(Ctx& c, const double* dense_dev, int n, int d, int chi, double eps);
 void decode_dense(Ctx& c, const qtt_mps* x, double* dense_dev);
