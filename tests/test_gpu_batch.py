@@ -165,3 +165,35 @@ def test_autotuned_batch_matches_oracle(ctx):
             spread = rel(tt.full(b), tt.full(a))
             d = rel(qtt.qtt_decode(c2, g), tt.full(a))
             assert d < max(1e-10, 10.0 * spread), (spec, k, d, spread)
+
+
+def test_batch_with_extrapolated_warm_start(ctx):
+    """Cases with the extrapolated Poisson warm start in a batch: their first step after
+    set_state (no previous pressure) runs eagerly before the concurrent replays, the later ones
+    from their graphs; every case equals the same case stepped alone, bit for bit."""
+    from paper_2507_05222_gb300 import qtt
+    mix = [MIX[0], MIX[3]]
+    opsl = [Q.Ops(ne, nx, R, Re, dt, o, rot=rot) for (o, ne, nx, chi, Re, dt, rot) in mix]
+    states = [start_state(s[1], s[2], s[3], 40 + i, ops) for i, (s, ops) in enumerate(zip(mix, opsl))]
+
+    def make(spec, st, warm):
+        ordering, ne, nx, chi, Re, dt, rot = spec
+        case = qtt.Case(ctx, ne, nx, R, Re, dt, chi, ordering, rot=rot, mom=TIGHT_MOM, poi=TIGHT_POI,
+                        poisson_warm=warm)
+        case.set_state(*[qtt.MPS.from_cores(ctx, x) for x in st])
+        return case
+
+    alone = []
+    for spec, st in zip(mix, states):
+        case = make(spec, st, "extrapolated")
+        case.fractional_step(3)
+        alone.append([qtt.qtt_decode(ctx, g) for g in case.get_state()])
+    cases = [make(mix[0], states[0], "extrapolated"), make(mix[1], states[1], "extrapolated")]
+    recs, status = qtt.fractional_step_batch(ctx, cases, 3)
+    assert status == [0, 0]
+    for i, case in enumerate(cases):
+        for a, b in zip((qtt.qtt_decode(ctx, g) for g in case.get_state()), alone[i]):
+            assert np.array_equal(a, b), i
+    # a second batch call continues from the graphs (the history is kept)
+    recs2, status2 = qtt.fractional_step_batch(ctx, cases, 1)
+    assert status2 == [0, 0]
