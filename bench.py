@@ -166,7 +166,7 @@ def run_reference(args, cfg):
     line = {"impl": "reference", "metric": METRIC, "value": sps, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * dt / done, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering", "poisson_warm")}
+            "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering", "poisson_warm", "apply")}
             | {"mom_solve": list(cfg["mom"]), "poisson_solve": list(cfg["poi"]), "fit_sweeps": cfg["fit_sweeps"]},
             "cpu_baseline": {"value": sps, "unit": "steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{done} full fractional steps of the workload (numpy FP64 oracle)"},
@@ -191,7 +191,7 @@ def run_ours(args, cfg):
         ctx.set_precision(args.precision)
     ne, nx, chi = cfg["n_eta"], cfg["n_xi"], cfg["chi"]
     case = qtt.Case(ctx, ne, nx, cfg["R"], cfg["Re"], cfg["dt"], chi, cfg["ordering"], fit_sweeps=cfg["fit_sweeps"],
-                    mom=cfg["mom"], poi=cfg["poi"], poisson_warm=args.poisson_warm)
+                    mom=cfg["mom"], poi=cfg["poi"], poisson_warm=args.poisson_warm, apply=cfg["apply"])
     u0, v0, pad = initial_fields(cfg)
     gu = qtt.qtt_encode(ctx, qtt.qtt_field_to_vector(ctx, u0, cfg["ordering"]), ne + nx, chi)
     gv = qtt.qtt_encode(ctx, qtt.qtt_field_to_vector(ctx, v0, cfg["ordering"]), ne + nx, chi)
@@ -200,10 +200,10 @@ def run_ours(args, cfg):
     if args.kernel_probe:
         Dx = case.operator(0)
         u, _, _ = case.get_state()
-        qtt.mpo_apply_round(ctx, Dx, u, chi)
+        qtt.mpo_apply_round(ctx, Dx, u, chi, apply=cfg["apply"])
         ctx.sync()
         qtt.profiler_range(True)
-        qtt.mpo_apply_round(ctx, Dx, u, chi)
+        qtt.mpo_apply_round(ctx, Dx, u, chi, apply=cfg["apply"])
         ctx.sync()
         qtt.profiler_range(False)
         return
@@ -359,7 +359,7 @@ def run_ours(args, cfg):
         line = {"metric": METRIC, "value": job_throughput(world, step_ms * 1e-3), "unit": "steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else f"f64+{args.precision}-contractions", "data": "synthetic",
-                "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering", "poisson_warm")}
+                "config": {k: cfg[k] for k in ("workload", "n_eta", "n_xi", "chi", "Re", "dt", "R", "ordering", "poisson_warm", "apply")}
                 | {"mom_solve": list(cfg["mom"]), "poisson_solve": list(cfg["poi"]), "fit_sweeps": cfg["fit_sweeps"],
                    "state": f"wake_field seed {cfg['seed']}", "l2": "256 MB buffer written between timed steps",
                    "replicas": world,
@@ -782,6 +782,10 @@ def main():
                          "nodes of graphs with conditional nodes)")
     ap.add_argument("--phase-breakdown", action="store_true",
                     help="print kernel-class time by step phase (diagnostic; no bench line)")
+    ap.add_argument("--apply", default="sketch", choices=("gram", "sketch"),
+                    help="rounding of the step's four MPO-MPS products (QTT_APPLY_*); the sketched "
+                         "rounding equals the oracle's TT-SVD to ~1e-12 at this workload, the Gram "
+                         "rounding to ~1e-8")
     ap.add_argument("--kernel-probe", action="store_true",
                     help="set up, then one D_x u product with rounding between cudaProfilerStart/Stop (for ncu)")
     args = ap.parse_args()
@@ -791,6 +795,7 @@ def main():
     if args.chi is not None:
         cfg.update(chi=args.chi, workload=f"cylinder_qtt_step_2^{cfg['n_eta'] + cfg['n_xi']}_chi{args.chi}")
     cfg["poisson_warm"] = args.poisson_warm
+    cfg["apply"] = args.apply
     if args.kernel_sweep:
         kernel_sweep(args)
         return

@@ -82,14 +82,29 @@ typedef void (*qtt_free_fn)(void* ptr, void* user);
 #define QTT_PREC_TF32 2
 #define QTT_PREC_BF16 3
 
+/* Rounding of mpo_apply_round (and of the step's four products, qtt_case_params.apply).
+ * QTT_APPLY_GRAM: right-to-left TT-SVD through left Gram environments of M x; only (d chi)-sized
+ * eigenproblems appear, but the Gram matrices square the singular values, so directions below
+ * ~sqrt(eps) sigma_1 of a cut are not resolved (on smooth fields, whose cut spectra reach
+ * 1e-10 sigma_1 at chi, the result differs from the TT-SVD by ~1e-8).  QTT_APPLY_SKETCH: the left
+ * part of M x is orthogonalised through a random sketch of its right part (bond 2 chi + 32) and
+ * one Householder QR per site, and every cut's matrix is then explicit, its eigenpairs refined
+ * in factored form: equal to the TT-SVD up to the sketch's range error (which falls with the
+ * cut spectra's tail beyond 2 chi + 32: ~1e-13 on smooth fields, large on flat spectra such as
+ * random tensor trains, where the Gram rounding is accurate).  Needs d chi <= 160. */
+#define QTT_APPLY_GRAM 0
+#define QTT_APPLY_SKETCH 1
+
 /* Truncation rule of every rounding (Sec. II: keep the first chi singular values, or those
  * above a threshold): keep k = min(chi_max, structural rank, #{sigma_i > rel_tol sigma_1});
  * rel_tol = 0 keeps the structural count (fixed bond profile min(2^k, 2^(n-k), chi_max)).
- * prec: QTT_PREC_* of the contractions of the call (0: FP64). */
+ * prec: QTT_PREC_* of the contractions of the call (0: FP64).  apply: QTT_APPLY_* (read by
+ * mpo_apply_round with rel_tol = 0; must be 0 or 1 everywhere). */
 typedef struct {
   int chi_max;
   double rel_tol;
   int prec;
+  int apply;
 } qtt_trunc;
 
 typedef struct {
@@ -233,8 +248,9 @@ int qtt_round(qtt_ctx* ctx, const qtt_mps* x, qtt_trunc tr, qtt_mps** out, qtt_r
 int mps_axpby_round(qtt_ctx* ctx, double alpha, const qtt_mps* x, double beta, const qtt_mps* y,
                     qtt_trunc tr, qtt_mps** out, qtt_round_info* info);
 /* y = round(M x): core-wise contraction over the physical index (Sec. II.A.2) then
- * TT-rounding, the rounding done on Gram environments so the bond chi*w product is never
- * orthogonalised explicitly. */
+ * TT-rounding without forming the bond chi*w product: by Gram environments or by the sketched
+ * orthogonalisation (tr.apply, QTT_APPLY_*).  rel_tol > 0 forms the product and rounds it by
+ * QR and SVD where the bonds allow it. */
 int mpo_apply_round(qtt_ctx* ctx, const qtt_mpo* M, const qtt_mps* x, qtt_trunc tr,
                     qtt_mps** out, qtt_round_info* info);
 /* c ~ a (.) b (Sec. II.A.3) at the bond profile of `tr`, by the variational fit of Table I:
@@ -342,6 +358,7 @@ typedef struct {
                               extrapolation 2 p^m - p^(m-1), fitted at the pressure's bonds from
                               p^m with fit_sweeps sweeps (the first step after set_state, which
                               has no p^(m-1), starts from p^m and runs outside the step graph) */
+  int apply;               /* QTT_APPLY_* of the step's four MPO-MPS products */
 } qtt_case_params;
 
 typedef struct {

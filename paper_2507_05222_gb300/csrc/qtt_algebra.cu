@@ -116,6 +116,41 @@ __global__ void k_disc_add(const double* rho, const double* w, int nv, int bk, d
   *acc += fmax(tr - kept, 0.0);
 }
 
+// *acc += the sum of the discarded eigenvalues w[bk..nv) of a cut whose eigenpairs were refined
+// in factored form (each Rayleigh quotient then accurate on its own scale).
+__global__ void k_disc_add_tail(const double* w, int nv, int bk, double* acc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = bk; i < nv; ++i) s += fmax(w[i], 0.0);
+  *acc += s;
+}
+
+// One core (l0, d, l1) of the sketch tensor train.  l0 == d l1 (the sketch as wide as the
+// right space it sketches): the identity map, so that the sketch spans that space exactly.
+// Else i.i.d. N(0, s^2) entries by the Box-Muller transform of two uniforms, each the top 53 bits
+// of SplitMix64 (Steele, Lea and Flood 2014) at counter seed + 2i + 1 and seed + 2i + 2.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_sketch_core(int l0, int d, int l1, uint64_t seed, double s, double* __restrict__ out) {
+  const int64_t n = int64_t(l0) * d * l1;
+  const bool ident = int64_t(l0) == int64_t(d) * l1;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    if (ident) {
+      const int64_t l = i / (int64_t(d) * l1), sm = i % (int64_t(d) * l1);
+      out[i] = (l == sm) ? 1.0 : 0.0;
+    } else {
+      const double u1 = (double(splitmix64(seed + 2 * uint64_t(i) + 1) >> 11) + 1.0) * 0x1.0p-53;  // (0, 1]
+      const double u2 = double(splitmix64(seed + 2 * uint64_t(i) + 2) >> 11) * 0x1.0p-53;          // [0, 1)
+      out[i] = s * sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    }
+  }
+}
+
 __global__ void k_add_value(double* acc, double v) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *acc += v;
 }
@@ -505,6 +540,147 @@ qtt_mps* apply_round_gram(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, d
     top_vectors_as_core(c, V.p, nv, bk, out[k].p);
     DBuf Pn(&c, size_t(w0) * a0 * bk);
     gemm(c, 1, int64_t(w0) * a0, bk, nv, 1.0, Z.p, 0, nv, 1, V.p, 0, nv, 1, 0.0, Pn.p, 0, bk, 1);
+    P = std::move(Pn);
+    ob[k] = bk;
+  }
+  qtt_mps* z = into;
+  if (z) QTT_CHECK_ARG(z->n == n && z->d == d && z->bonds == ob, "apply into: output bonds differ");
+  else z = new_mps(&c, n, d, ob);
+  for (int k = 0; k < n; ++k) copy(c, z->core(k), out[k].p, int64_t(ob[k]) * d * ob[k + 1]);
+  return z;
+}
+
+// ------------------------------------------------------------------ sketched rounding of M x
+// TT-SVD of y = M x (Sec. II.A.2 then the rounding of Sec. II.A) without squaring singular
+// values.  The Gram rounding above resolves nothing below ~sqrt(eps) sigma_1 at a cut; on
+// smooth fields the chi-th singular value of the middle cuts sits at 1e-9..1e-11 sigma_1, so
+// its result there differs from the TT-SVD by ~1e-8.  Here:
+//  1. a tensor train Omega (bonds sb_k = min(ell, d sb_{k+1})) sketches the right part of y at
+//     every cut: W_k = y_{>=k} . Omega_{>=k}, (w_k a_k) x sb_k, contracted core by core; its
+//     cores are identity maps while the sketch is as wide as the right space (which it then
+//     spans exactly) and Gaussian where it compresses;
+//  2. left to right, the next left unfolding T_k = F_{k-1} y[k] ((rho d) x (w a)) is kept as
+//     it is while rho d <= sb_{k+1}, else replaced by its coefficients F_k = Q^T T_k in the
+//     orthonormal basis Q of the sketched range T_k W_{k+1} (Householder QR): y's left part is
+//     then Q_{<=k} F_k with Q_{<=k} orthonormal, up to the sketch's range error, which falls
+//     with the (rank ell) tail of the cut's spectrum (<~1e-13 for the fields of the step);
+//  3. right to left as in the Gram rounding, but each cut's matrix A_k = F_{k-1} Z_k
+//     (rho x d c) is explicit, and its eigenpairs are refined in factored form
+//     ((F X)^T (F X) instead of X^T S X), which resolves the tail to its own scale.
+// The result does not depend on Omega beyond the sketch's range error, which is zero when ell
+// reaches the product's largest bond (sketch_width).  Cost: the sketches and one QR of
+// (rho d) x ell per middle site in place of the left Gram recurrence.
+
+// Sketch width: the largest product bond max_k w_k a_k when the QR of a (d ell) x ell sketch
+// supports it (every sketch then spans its cut's range exactly, for any input), else 2 chi + 32
+// (the range error then falls with the cut spectra beyond that width), at most what the QR
+// supports.
+static int sketch_width(int chi, int d, const std::vector<int>& R) {
+  int rmax = *std::max_element(R.begin(), R.end());
+  int want = rmax;
+  if (!qr_fits(d * want, want)) want = 2 * chi + 32;
+  while (want > 16 && !qr_fits(d * want, want)) want -= 8;
+  return std::max(want, 1);
+}
+
+qtt_mps* apply_round_sketch(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, double eps, qtt_mps* into) {
+  const int n = x->n, d = x->d;
+  QTT_CHECK_ARG(M->n == n && M->d == d, "apply: shape mismatch");
+  if (n == 1) return apply_round_gram(c, M, x, chi, eps, into);
+  if (int64_t(d) * chi > 160)
+    throw Error(QTT_ERR_UNSUPPORTED, "apply (sketched rounding): d * chi must be <= 160 (eigensolver limit)");
+  std::vector<int> R(n + 1);
+  for (int k = 0; k <= n; ++k) R[k] = M->bonds[k] * x->bonds[k];
+  std::vector<int> mstruct = left_struct(R, d);
+  const int ell = sketch_width(chi, d, R);
+  std::vector<int> sb(n + 1, 1);
+  for (int k = n - 1; k >= 1; --k) sb[k] = int(std::min<int64_t>(ell, int64_t(d) * sb[k + 1]));
+  // 1. right sketches W[k] (w_k, a_k, sb_k), k = n .. 1
+  std::vector<DBuf> W(n + 1);
+  W[n].reset(&c, 1);
+  fill(c, W[n].p, 1, 1.0);
+  for (int k = n - 1; k >= 1; --k) {
+    int w0 = M->bonds[k], w1 = M->bonds[k + 1], a0 = x->bonds[k], a1 = x->bonds[k + 1], l0 = sb[k], l1 = sb[k + 1];
+    DBuf Om(&c, size_t(l0) * d * l1);
+    int64_t cnt = int64_t(l0) * d * l1;
+    k_sketch_core<<<unsigned(std::min<int64_t>((cnt + 255) / 256, 1024)), 256, 0, c.stream>>>(
+        l0, d, l1, 0x5EEDC0DEull * uint64_t(k + 1) << 20, 1.0 / std::sqrt(double(d) * l1), Om.p);
+    after_launch(c, "sketch_core");
+    DBuf T1(&c, size_t(a0) * d * w1 * l1), T2(&c, size_t(w0) * a0 * d * l1);
+    einsum(c, "atb,vbl->atvl", 1.0, tv(x->core(k), {a0, d, a1}), tv(W[k + 1].p, {w1, a1, l1}), 0.0,
+           tv(T1.p, {a0, d, w1, l1}));
+    einsum(c, "wstv,atvl->wasl", 1.0, tv(M->core(k), {w0, d, d, w1}), tv(T1.p, {a0, d, w1, l1}), 0.0,
+           tv(T2.p, {w0, a0, d, l1}));
+    W[k].reset(&c, size_t(w0) * a0 * l0);
+    einsum(c, "wasl,msl->wam", 1.0, tv(T2.p, {w0, a0, d, l1}), tv(Om.p, {l0, d, l1}), 0.0, tv(W[k].p, {w0, a0, l0}));
+  }
+  // 2. left-to-right coefficients F[k] (rho_k x w_{k+1} a_{k+1}), k = 0 .. n-2
+  std::vector<DBuf> F(n);
+  std::vector<int> rho(n, 1);
+  {
+    DBuf F0(&c, 1);
+    fill(c, F0.p, 1, 1.0);
+    const double* Fp = F0.p;
+    int r = 1;
+    for (int k = 0; k + 1 < n; ++k) {
+      int w0 = M->bonds[k], w1 = M->bonds[k + 1], a0 = x->bonds[k], a1 = x->bonds[k + 1];
+      DBuf T1(&c, size_t(r) * w0 * d * a1), T(&c, size_t(r) * d * w1 * a1);
+      einsum(c, "rwa,atb->rwtb", 1.0, tv(const_cast<double*>(Fp), {r, w0, a0}), tv(x->core(k), {a0, d, a1}), 0.0,
+             tv(T1.p, {r, w0, d, a1}));
+      einsum(c, "rwtb,wstv->rsvb", 1.0, tv(T1.p, {r, w0, d, a1}), tv(M->core(k), {w0, d, d, w1}), 0.0,
+             tv(T.p, {r, d, w1, a1}));
+      const int rows = r * d, cols = w1 * a1, l = sb[k + 1];
+      if (rows <= l) {
+        F[k] = std::move(T);
+        rho[k] = rows;
+      } else {
+        DBuf Y(&c, size_t(rows) * l), Q(&c, size_t(rows) * l);
+        gemm(c, 1, rows, l, cols, 1.0, T.p, 0, cols, 1, W[k + 1].p, 0, l, 1, 0.0, Y.p, 0, l, 1);
+        qr(c, 1, rows, l, 0, Y.p, 0, Q.p, 0, nullptr, 0);
+        F[k].reset(&c, size_t(l) * cols);
+        gemm(c, 1, l, cols, rows, 1.0, Q.p, 0, 1, l, T.p, 0, cols, 1, 0.0, F[k].p, 0, cols, 1);
+        rho[k] = l;
+      }
+      Fp = F[k].p;
+      r = rho[k];
+      W[k + 1] = DBuf();   // no longer needed
+    }
+  }
+  // 3. right-to-left truncation on the explicit cut matrices
+  std::vector<int> ob(n + 1);
+  ob[0] = 1;
+  ob[n] = 1;
+  std::vector<DBuf> out(n);
+  DBuf P(&c, 1);  // (w_{k+1}, a_{k+1}, c_{k+1})
+  fill(c, P.p, 1, 1.0);
+  for (int k = n - 1; k >= 0; --k) {
+    int w0 = M->bonds[k], w1 = M->bonds[k + 1], a0 = x->bonds[k], a1 = x->bonds[k + 1], c1 = ob[k + 1];
+    TV X = tv(x->core(k), {a0, d, a1});
+    TV Wm = tv(M->core(k), {w0, d, d, w1});
+    DBuf T1(&c, size_t(a0) * d * w1 * c1);
+    einsum(c, "atb,vbc->atvc", 1.0, X, tv(P.p, {w1, a1, c1}), 0.0, tv(T1.p, {a0, d, w1, c1}));
+    DBuf Z(&c, size_t(w0) * a0 * d * c1);
+    einsum(c, "wstv,atvc->wasc", 1.0, Wm, tv(T1.p, {a0, d, w1, c1}), 0.0, tv(Z.p, {w0, a0, d, c1}));
+    if (k == 0) {
+      out[0] = std::move(Z);
+      break;
+    }
+    const int nv = d * c1, r = rho[k - 1], wa = w0 * a0;
+    DBuf A(&c, size_t(r) * nv), S(&c, size_t(nv) * nv), wv(&c, size_t(nv)), V(&c, size_t(nv) * nv);
+    gemm(c, 1, r, nv, wa, 1.0, F[k - 1].p, 0, wa, 1, Z.p, 0, nv, 1, 0.0, A.p, 0, nv, 1);
+    F[k - 1] = DBuf();
+    gemm(c, 1, nv, nv, r, 1.0, A.p, 0, 1, nv, A.p, 0, nv, 1, 0.0, S.p, 0, nv, 1);
+    const int keep = std::min(std::min(chi, mstruct[k]), nv);
+    eigh(c, nv, S.p, wv.p, V.p, keep, A.p, r);
+    int bk = choose_rank(c, wv.p, nv, chi, eps, std::min(mstruct[k], nv));
+    if (c.disc_acc && bk < nv) {
+      k_disc_add_tail<<<1, 1, 0, c.stream>>>(wv.p, nv, bk, c.disc_acc);
+      after_launch(c, "disc_add_tail");
+    }
+    out[k].reset(&c, size_t(bk) * nv);
+    top_vectors_as_core(c, V.p, nv, bk, out[k].p);
+    DBuf Pn(&c, size_t(wa) * bk);
+    gemm(c, 1, wa, bk, nv, 1.0, Z.p, 0, nv, 1, V.p, 0, nv, 1, 0.0, Pn.p, 0, bk, 1);
     P = std::move(Pn);
     ob[k] = bk;
   }

@@ -49,6 +49,7 @@ void check_trunc(const qtt_trunc& t) {
   if (t.chi_max < 1) throw Error(QTT_ERR_ARG, "trunc: chi_max must be >= 1");
   if (!(t.rel_tol >= 0.0) || !std::isfinite(t.rel_tol)) throw Error(QTT_ERR_ARG, "trunc: rel_tol must be >= 0");
   prec_digits(t.prec);
+  if (t.apply != QTT_APPLY_GRAM && t.apply != QTT_APPLY_SKETCH) throw Error(QTT_ERR_ARG, "trunc: apply must be 0 or 1");
 }
 
 void check_solve_opts(const qtt_solve_opts& o, const char* what) {
@@ -522,6 +523,8 @@ int mpo_apply_round(qtt_ctx* ctx, const qtt_mpo* M, const qtt_mps* x, qtt_trunc 
   if (tr.rel_tol > 0.0) {
     std::unique_ptr<qtt_mps, void (*)(qtt_mps*)> e(mpo_mps_exact(c, M, x), free_mps);
     y = round_any(c, e.get(), tr.chi_max, tr.rel_tol);
+  } else if (tr.apply == QTT_APPLY_SKETCH) {
+    y = apply_round_sketch(c, M, x, tr.chi_max, 0.0);
   } else {
     y = apply_round_gram(c, M, x, tr.chi_max, 0.0);
   }
@@ -726,6 +729,8 @@ int qtt_case_create(qtt_ctx* ctx, const qtt_case_params* p, qtt_case** out) {
   API_BEGIN
   QTT_CHECK_ARG(ctx && p && out, "case_create: null argument");
   QTT_CHECK_ARG(p->poisson_warm == 0 || p->poisson_warm == 1, "case_create: poisson_warm must be 0 or 1");
+  QTT_CHECK_ARG(p->apply == QTT_APPLY_GRAM || p->apply == QTT_APPLY_SKETCH, "case_create: apply must be 0 or 1");
+  QTT_CHECK_ARG(p->apply != QTT_APPLY_SKETCH || 2 * p->chi <= 160, "case_create: the sketched products need chi <= 80");
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   std::unique_ptr<qtt_case> h(new qtt_case);
   h->ctx = &c;

@@ -598,10 +598,11 @@ void step(Ctx& c, Case& cs, double* rec, bool with_forces, bool extrapolate) {
   MpsP dxv = mk(new_mps(&c, n, 2, apply_bonds(cs.Dx, cs.v, chi)));
   MpsP dzv = mk(new_mps(&c, n, 2, apply_bonds(cs.Dz, cs.v, chi)));
   fork(c, 4);
-  apply_round_gram(worker(c, 0), cs.Dx, cs.u, chi, 0.0, dxu.get());
-  apply_round_gram(worker(c, 1), cs.Dz, cs.u, chi, 0.0, dzu.get());
-  apply_round_gram(worker(c, 2), cs.Dx, cs.v, chi, 0.0, dxv.get());
-  apply_round_gram(worker(c, 3), cs.Dz, cs.v, chi, 0.0, dzv.get());
+  auto apply = P.apply == QTT_APPLY_SKETCH ? apply_round_sketch : apply_round_gram;
+  apply(worker(c, 0), cs.Dx, cs.u, chi, 0.0, dxu.get());
+  apply(worker(c, 1), cs.Dz, cs.u, chi, 0.0, dzu.get());
+  apply(worker(c, 2), cs.Dx, cs.v, chi, 0.0, dxv.get());
+  apply(worker(c, 3), cs.Dz, cs.v, chi, 0.0, dzv.get());
   join(c, 4);
   cs.mark(c, 1);
   // explicit right-hand sides (eq:intermediate_vel_eq), one fit each, warm start u (v), then

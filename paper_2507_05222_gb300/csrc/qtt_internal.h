@@ -319,6 +319,8 @@ void check_recip(Ctx& c, int n, const double* x_dev, double* err_dev);
 // path: 0 = cluster QR when the shape allows it, else one CTA; 1 = one CTA; 2 = cluster only.
 void qr(Ctx& c, int count, int m, int n, int trans, const double* A, int64_t in_stride, double* Q, int64_t q_stride,
         double* R, int64_t r_stride, int path = 0);
+// Whether qr() supports an m x n matrix (cluster kernel or one CTA).
+bool qr_fits(int m, int n);
 // Accurate (one-sided Jacobi, FP64) SVD of a small m x n matrix, m >= n: U (m x n), s, V (n x n).
 void svd_small(Ctx& c, int m, int n, const double* G, double* U, double* s, double* V);
 
@@ -327,7 +329,10 @@ void svd_small(Ctx& c, int m, int n, const double* G, double* U, double* s, doub
 // Ogita-Aishima refinement levels.  keep (0: n) bounds how many leading eigenvectors the
 // caller uses: refinement levels whose tail starts at or after keep are skipped, so the
 // trailing (discarded) vectors span the right subspace but are not resolved among themselves.
-void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep = 0);
+// F (optional, m x n row-major, S = F^T F): every refinement product X^T S X is then formed as
+// (F X)^T (F X), which keeps eigenvalues far below ||S|| (squared singular values of F down to
+// ~eps^2 ||S||) resolved to their own scale.
+void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep = 0, const double* F = nullptr, int m = 0);
 void init_kernel_attributes();
 
 }  // namespace qtt

@@ -789,7 +789,7 @@ __global__ void k_copy_guarded(double* __restrict__ dst, const double* __restric
 // Sc = S 2^-e with e = ilogb(max |S_ij|) (0 for a zero or non-finite matrix): a power-of-two
 // scaling, exact, that brings the largest entry into [1, 2) so that the FP32 Jacobi and the
 // squared norms of the refinement neither underflow nor overflow.  *e_out = e.
-__global__ void k_scale_pow2(int64_t n, const double* __restrict__ S, double* __restrict__ Sc, int* e_out) {
+__global__ void k_scale_pow2(int64_t n, const double* __restrict__ S, double* __restrict__ Sc, int* e_out, int even) {
   __shared__ double red[32];
   __shared__ int es;
   double m = 0.0;
@@ -801,11 +801,20 @@ __global__ void k_scale_pow2(int64_t n, const double* __restrict__ S, double* __
     double t = 0.0;
     for (int w = 0; w < int(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
     es = (t > 0.0 && isfinite(t)) ? ilogb(t) : 0;
+    if (even && (es & 1)) es -= 1;   // largest entry then in [1, 4)
     *e_out = es;
   }
   __syncthreads();
   const int e = es;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Sc[i] = ldexp(S[i], -e);
+}
+
+// Fc = F 2^(-e/2) for the even exponent e of k_scale_pow2.
+__global__ void k_scale_pow2_half(int64_t n, const double* __restrict__ F, double* __restrict__ Fc,
+                                  const int* __restrict__ e) {
+  const int h = *e / 2;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    Fc[i] = ldexp(F[i], -h);
 }
 
 // w[i] *= 2^e
@@ -885,6 +894,13 @@ static void qr_cluster_shape(int m, int n, int& nb, int& cs) {
   cs = k;
 }
 
+bool qr_fits(int m, int n) {
+  init_kernel_attributes();
+  int nb = 0, cs = 0;
+  qr_cluster_shape(m, n, nb, cs);
+  return cs > 0 || qr_smem(m, n) <= 220 * 1024;
+}
+
 void qr(Ctx& c, int count, int m, int n, int trans, const double* A, int64_t in_stride, double* Q, int64_t q_stride,
         double* R, int64_t r_stride, int path) {
   DigitsScope fp64(c, kDigitsFP64);   // the decompositions and their refinement products stay FP64
@@ -953,12 +969,26 @@ static void newton_schulz(Ctx& c, int n, double* X, double* XtX, double* AX) {
   axpby(c, int64_t(n) * n, -0.5, AX, 1.5, X);
 }
 
-// One Ogita-Aishima iteration on X (n x n) for the symmetric S.
-static void oa_iteration(Ctx& c, int n, const double* S, double* X, double* XtX, double* AX, double* SX, double* E,
-                         double* lam, const double* an, double* part) {
+// X^T S X into SX (n x n).  With a factor F (m x n row-major, S = F^T F) it is formed as
+// (F X)^T (F X): each entry then carries an error relative to the product of the norms of its
+// two columns of F X, not to ||S||, so pairs far down the spectrum keep their relative
+// accuracy (the squared form resolves nothing below ~eps ||S||).  FX: m x n scratch.
+static void xtsx(Ctx& c, int n, const double* S, const double* F, int m, const double* X, double* AX, double* FX,
+                 double* SX) {
+  if (F) {
+    gemm(c, 1, m, n, n, 1.0, F, 0, n, 1, X, 0, n, 1, 0.0, FX, 0, n, 1);   // F X
+    gemm(c, 1, n, n, m, 1.0, FX, 0, 1, n, FX, 0, n, 1, 0.0, SX, 0, n, 1); // (F X)^T (F X)
+  } else {
+    gemm(c, 1, n, n, n, 1.0, S, 0, n, 1, X, 0, n, 1, 0.0, AX, 0, n, 1);   // S X
+    gemm(c, 1, n, n, n, 1.0, X, 0, 1, n, AX, 0, n, 1, 0.0, SX, 0, n, 1);  // X^T S X
+  }
+}
+
+// One Ogita-Aishima iteration on X (n x n) for the symmetric S (or S = F^T F, see xtsx).
+static void oa_iteration(Ctx& c, int n, const double* S, const double* F, int m, double* X, double* XtX, double* AX,
+                         double* FX, double* SX, double* E, double* lam, const double* an, double* part) {
   gemm(c, 1, n, n, n, 1.0, X, 0, 1, n, X, 0, n, 1, 0.0, XtX, 0, n, 1);   // X^T X
-  gemm(c, 1, n, n, n, 1.0, S, 0, n, 1, X, 0, n, 1, 0.0, AX, 0, n, 1);    // S X
-  gemm(c, 1, n, n, n, 1.0, X, 0, 1, n, AX, 0, n, 1, 0.0, SX, 0, n, 1);   // X^T S X
+  xtsx(c, n, S, F, m, X, AX, FX, SX);
   oa_update(c, n, XtX, SX, an, E, lam, part, c.guard);
   gemm(c, 1, n, n, n, 1.0, X, 0, n, 1, E, 0, n, 1, 0.0, AX, 0, n, 1);    // X E
   axpby(c, int64_t(n) * n, 1.0, AX, 1.0, X);
@@ -996,11 +1026,12 @@ static void oa_iteration(Ctx& c, int n, const double* S, double* X, double* XtX,
 constexpr float JAC_TOL2_FULL = QTT_JAC_TOL2_FULL;
 constexpr float JAC_TOL2_TAIL = QTT_JAC_TOL2_TAIL;
 
-void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep) {
+void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep, const double* F, int m) {
   DigitsScope fp64(c, kDigitsFP64);   // the decompositions and their refinement products stay FP64
   QTT_CHECK_ARG(n >= 1, "eigh: n >= 1");
   if (keep <= 0 || keep > n) keep = n;
   if (n > 160) throw Error(QTT_ERR_UNSUPPORTED, "eigh: n > 160 not supported");
+  QTT_CHECK_ARG(!F || m >= 1, "eigh: factor needs m >= 1 rows");
   // FP32 Jacobi: QTT_JAC_CTAS CTAs share the eigenvector rows for the larger matrices (each
   // keeps all of A; 8: 16 rows each at n = 128)
   const int jac_ctas = n >= 64 ? QTT_JAC_CTAS : 1;
@@ -1010,7 +1041,8 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep) {
   init_kernel_attributes();
   const size_t nn = size_t(n) * n;
   DBuf X(&c, nn), Xs(&c, nn), XtX(&c, nn), AX(&c, nn), SX(&c, nn), E(&c, nn), Y(&c, nn), lam(&c, size_t(n)),
-      an(&c, 1), flags(&c, 2), part(&c, 2 * OA_BLOCKS), Ssc(&c, nn);
+      an(&c, 1), flags(&c, 2), part(&c, 2 * OA_BLOCKS), Ssc(&c, nn), FX(&c, F ? size_t(m) * n : 1),
+      Fsc(&c, F ? size_t(m) * n : 1);
   int* t0 = reinterpret_cast<int*>(flags.p);
   int* need = t0 + 1;
   // work on S 2^-e (largest entry in [1, 2)): Gram matrices of small-norm trains (e.g. a field
@@ -1018,9 +1050,14 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep) {
   // squared norms of the refinement; the eigenvalues are scaled back at the end
   DBuf escale(&c, 1);
   int* eexp = reinterpret_cast<int*>(escale.p);
-  k_scale_pow2<<<1, 1024, 0, c.stream>>>(int64_t(nn), S, Ssc.p, eexp);
+  k_scale_pow2<<<1, 1024, 0, c.stream>>>(int64_t(nn), S, Ssc.p, eexp, F ? 1 : 0);
   after_launch(c, "scale_pow2");
   S = Ssc.p;
+  if (F) {   // F 2^(-e/2) with e even, so that (F X)^T (F X) is on the scale of S 2^-e
+    k_scale_pow2_half<<<unsigned(std::min<int64_t>((int64_t(m) * n + 255) / 256, 1024)), 256, 0, c.stream>>>(int64_t(m) * n, F, Fsc.p, eexp);
+    after_launch(c, "scale_pow2_half");
+    F = Fsc.p;
+  }
   {
     ProfScope ps(c, KC_EIG);
     k_jacobi_f32<<<jac_ctas, dim3(32, 32), smf, c.stream>>>(n, S, X.p, 10, nullptr, JAC_TOL2_FULL, nullptr);
@@ -1029,16 +1066,18 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep) {
 
   k_frob<<<1, 1024, 0, c.stream>>>(int64_t(n) * n, S, an.p);
   after_launch(c, "frob");
-  constexpr int kLevels = 5;
-  const double taus[kLevels] = {0.0, 1e-3, 1e-6, 1e-9, 1e-12};
+  // levels three decades apart in the eigenvalue; with a factor F the products resolve the
+  // tail to its own scale, and levels continue down to 1e-27 of the largest (singular values of
+  // F down to ~3e-14 of the largest), where the cut of a weakly truncated rounding can fall
+  const double taus[10] = {0.0, 1e-3, 1e-6, 1e-9, 1e-12, 1e-15, 1e-18, 1e-21, 1e-24, 1e-27};
+  const int kLevels = F ? 10 : 5;
   for (int level = 0; level < kLevels; ++level) {
     if (level > 0) {
       k_tail_start<<<1, 1, 0, c.stream>>>(n, lam.p, taus[level], keep, t0, need);
       after_launch(c, "tail_start");
       c.guard = need;
       newton_schulz(c, n, X.p, XtX.p, AX.p);
-      gemm(c, 1, n, n, n, 1.0, S, 0, n, 1, X.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
-      gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, AX.p, 0, n, 1, 0.0, SX.p, 0, n, 1);
+      xtsx(c, n, S, F, m, X.p, AX.p, FX.p, SX.p);
       c.guard = nullptr;
       {
         ProfScope ps(c, KC_EIG);
@@ -1050,12 +1089,11 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep) {
       copy_guarded(c, X.p, AX.p, int64_t(nn), need);
     }
     for (int it = 0; it < (level == 0 ? 3 : 2); ++it)
-      oa_iteration(c, n, S, X.p, XtX.p, AX.p, SX.p, E.p, lam.p, an.p, part.p);
+      oa_iteration(c, n, S, F, m, X.p, XtX.p, AX.p, FX.p, SX.p, E.p, lam.p, an.p, part.p);
     // eigenvalue estimates of the refined vectors, then sort (descending); a skipped level
     // leaves X and lam as they were, and the sort is then the identity
     gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, X.p, 0, n, 1, 0.0, XtX.p, 0, n, 1);
-    gemm(c, 1, n, n, n, 1.0, S, 0, n, 1, X.p, 0, n, 1, 0.0, AX.p, 0, n, 1);
-    gemm(c, 1, n, n, n, 1.0, X.p, 0, 1, n, AX.p, 0, n, 1, 0.0, SX.p, 0, n, 1);
+    xtsx(c, n, S, F, m, X.p, AX.p, FX.p, SX.p);
     oa_update(c, n, XtX.p, SX.p, an.p, E.p, lam.p, part.p, c.guard);
     c.guard = nullptr;
     k_sort_eig<<<1, 1024, n * sizeof(int), c.stream>>>(n, lam.p, X.p, w, Xs.p);

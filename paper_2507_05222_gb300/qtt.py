@@ -33,10 +33,11 @@ class QttError(RuntimeError):
 
 
 class qtt_trunc(C.Structure):
-    _fields_ = [("chi_max", C.c_int), ("rel_tol", C.c_double), ("prec", C.c_int)]
+    _fields_ = [("chi_max", C.c_int), ("rel_tol", C.c_double), ("prec", C.c_int), ("apply", C.c_int)]
 
 
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+APPLY = {"gram": 0, "sketch": 1}
 
 
 class qtt_round_info(C.Structure):
@@ -59,7 +60,7 @@ class qtt_case_params(C.Structure):
     _fields_ = [("n_eta", C.c_int), ("n_xi", C.c_int), ("ordering", C.c_int), ("D", C.c_double),
                 ("R", C.c_double), ("Re", C.c_double), ("dt", C.c_double), ("rot", C.c_double),
                 ("u_inf", C.c_double), ("chi", C.c_int), ("fit_sweeps", C.c_int),
-                ("mom", qtt_solve_opts), ("poi", qtt_solve_opts), ("poisson_warm", C.c_int)]
+                ("mom", qtt_solve_opts), ("poi", qtt_solve_opts), ("poisson_warm", C.c_int), ("apply", C.c_int)]
 
 
 class qtt_step_info(C.Structure):
@@ -422,8 +423,8 @@ class MPO:
 
 # ------------------------------------------------------------------ operations (C-ABI names)
 
-def _trunc(chi, rel_tol, prec="fp64"):
-    return qtt_trunc(int(chi), float(rel_tol), PREC[prec])
+def _trunc(chi, rel_tol, prec="fp64", apply="gram"):
+    return qtt_trunc(int(chi), float(rel_tol), PREC[prec], APPLY[apply])
 
 
 def _info_ptr(out_info):
@@ -493,10 +494,12 @@ def mps_axpby_round(ctx: Context, alpha: float, x: MPS, beta: float, y: MPS, chi
 
 
 def mpo_apply_round(ctx: Context, M: MPO, x: MPS, chi: int, rel_tol: float = 0.0, out_info=None,
-                    prec: str = "fp64") -> MPS:
+                    prec: str = "fp64", apply: str = "gram") -> MPS:
+    """apply: "gram" (Gram-environment rounding) or "sketch" (sketched orthogonalisation with
+    factored eigenpair refinement), QTT_APPLY_* of include/qtt.h."""
     h = P()
     ri = _round_info(out_info)
-    _check(lib().mpo_apply_round(ctx.h, M.h, x.h, _trunc(chi, rel_tol, prec), C.byref(h), _info_ptr(ri)))
+    _check(lib().mpo_apply_round(ctx.h, M.h, x.h, _trunc(chi, rel_tol, prec, apply), C.byref(h), _info_ptr(ri)))
     _fill_round(ri)
     return MPS(ctx, h)
 
@@ -597,13 +600,15 @@ def poisson_solve(ctx: Context, A: MPO, b: MPS, x: MPS, max_sweeps: int, rel_tol
 class Case:
     def __init__(self, ctx: Context, n_eta: int, n_xi: int, R: float, Re: float, dt: float, chi: int,
                  ordering: str = "interleaved", D: float = 1.0, rot: float = 0.0, u_inf: float = 1.0,
-                 fit_sweeps: int = 1, mom=MOM_DEFAULT, poi=POI_DEFAULT, poisson_warm: str = "previous"):
+                 fit_sweeps: int = 1, mom=MOM_DEFAULT, poi=POI_DEFAULT, poisson_warm: str = "previous",
+                 apply: str = "gram"):
         """mom, poi: ALS options (max_sweeps, rel_tol, cg_max_iter[, cg_tol[, stall]]); poisson_warm:
-        "previous" (p^m) or "extrapolated" (2 p^m - p^(m-1), fitted)."""
+        "previous" (p^m) or "extrapolated" (2 p^m - p^(m-1), fitted); apply: rounding of the
+        step's MPO-MPS products, "gram" or "sketch"."""
         self.ctx = ctx
         self.params = qtt_case_params(n_eta, n_xi, ORDERING[ordering], D, R, Re, dt, rot, u_inf, chi, fit_sweeps,
                                       solve_opts(*mom), solve_opts(*poi),
-                                      {"previous": 0, "extrapolated": 1}[poisson_warm])
+                                      {"previous": 0, "extrapolated": 1}[poisson_warm], APPLY[apply])
         h = P()
         _check(lib().qtt_case_create(ctx.h, C.byref(self.params), C.byref(h)))
         self.h = h

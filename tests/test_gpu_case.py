@@ -316,7 +316,8 @@ def test_headline_operations_match_oracle(ctx):
     momentum-operator ALS solve under the stop rule.  The products are held to the Gram-rounding
     limit: this state keeps singular values down to ~1e-14 sigma_1 in its bonds, and directions
     with sigma below sqrt(eps) sigma_1 are not resolved by a Gram eigenproblem, which leaves ~1e-8
-    of the product (measured 5e-8 with tensor-core contractions, 1e-8 on the FP64 pipe)."""
+    of the product (measured 5e-8 with tensor-core contractions, 1e-8 on the FP64 pipe).  The
+    sketched rounding of the same products is held to 1e-10 in both product modes."""
     from paper_2507_05222_gb300 import qtt
     ops, (u, v, p) = headline_state(ctx)
     gu, gv = qtt.MPS.from_cores(ctx, u), qtt.MPS.from_cores(ctx, v)
@@ -324,6 +325,17 @@ def test_headline_operations_match_oracle(ctx):
         ref = tt.full(tt.round_tt(tt.mpo_mps(M, x), 64))
         g = qtt.mpo_apply_round(ctx, qtt.MPO.from_cores(ctx, M), gx, 64)
         assert rel(qtt.qtt_decode(ctx, g), ref) < 1e-6
+        # the sketched rounding (no squared singular values) at the 1e-10 bar, with the
+        # contractions on the tensor cores (digit split) and on the FP64 pipe
+        try:
+            for mode in (0, 1):
+                ctx.set_gemm_mode(mode)
+                g = qtt.mpo_apply_round(ctx, qtt.MPO.from_cores(ctx, M), gx, 64, apply="sketch")
+                err = rel(qtt.qtt_decode(ctx, g), ref)
+                print(f"sketched product, gemm mode {mode}: {err:.2e}")
+                assert err < 1e-10
+        finally:
+            ctx.set_gemm_mode(0)
     ref = tt.full(tt.hadamard_round(u, v, 64, sweeps=2))
     g = qtt.mps_hadamard_round(ctx, gu, gv, 64, sweeps=2)
     assert rel(qtt.qtt_decode(ctx, g), ref) < 1e-11
@@ -351,24 +363,25 @@ def test_headline_step_matches_oracle(ctx):
     chi = 64
     ops = Q.Ops(ne, nx, 40.0, 200.0, 8e-4, "interleaved")
     u, v, p = wake_state(ops, ne, nx, chi, 7)
-    case = qtt.Case(ctx, ne, nx, 40.0, 200.0, 8e-4, chi, "interleaved")
-    case.use_graph(True)
-    case.set_state(*(qtt.MPS.from_cores(ctx, x) for x in (u, v, p)))
-    info = case.fractional_step(1, with_forces=True, check=False)
     o = step_opts(chi, qtt, tight=False)
     ref = S.step(ops, u, v, p, o)
     pert = S.step(ops, u, v, [c * (1.0 + 2.0 ** -50) for c in p], o)
-    same_solves(info[0], ref[3], rtol=3e-2)
-    spreads, diffs = [], []
-    for g, r, q in zip(case.get_state(), ref[:3], pert[:3]):
-        full_r = tt.full(r)
-        spreads.append(rel(tt.full(q), full_r))
-        diffs.append(rel(qtt.qtt_decode(ctx, g), full_r))
-    print("GPU - oracle:", diffs, "oracle spread:", spreads)
-    for d_, s_ in zip(diffs, spreads):
-        assert d_ <= max(10.0 * s_, 1e-10)
-    assert max(diffs) < 2e-6
-    assert info[0]["finite"] == 1 and np.isfinite(info[0]["cd"]) and np.isfinite(info[0]["cl"])
+    for apply in ("gram", "sketch"):
+        case = qtt.Case(ctx, ne, nx, 40.0, 200.0, 8e-4, chi, "interleaved", apply=apply)
+        case.use_graph(True)
+        case.set_state(*(qtt.MPS.from_cores(ctx, x) for x in (u, v, p)))
+        info = case.fractional_step(1, with_forces=True, check=False)
+        same_solves(info[0], ref[3], rtol=3e-2)
+        spreads, diffs = [], []
+        for g, r, q in zip(case.get_state(), ref[:3], pert[:3]):
+            full_r = tt.full(r)
+            spreads.append(rel(tt.full(q), full_r))
+            diffs.append(rel(qtt.qtt_decode(ctx, g), full_r))
+        print(apply, "GPU - oracle:", diffs, "oracle spread:", spreads)
+        for d_, s_ in zip(diffs, spreads):
+            assert d_ <= max(10.0 * s_, 1e-10)
+        assert max(diffs) < 2e-6
+        assert info[0]["finite"] == 1 and np.isfinite(info[0]["cd"]) and np.isfinite(info[0]["cl"])
 
 
 @pytest.mark.parametrize("seed", [0, 1])
