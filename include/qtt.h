@@ -50,7 +50,7 @@ extern "C" {
 #define QTT_ERR_NOT_CONVERGED (-4)/* a solver stopped at its sweep limit above tolerance */
 #define QTT_ERR_TIMEOUT (-5)      /* a bounded device wait ran out */
 #define QTT_ERR_NONFINITE (-6)    /* a NaN or Inf appeared in a result */
-#define QTT_ERR_UNSUPPORTED (-7)  /* size outside what the kernels support (e.g. bond > 160) */
+#define QTT_ERR_UNSUPPORTED (-7)  /* size outside what the kernels support (e.g. bond > 128) */
 
 #define QTT_HOST 0                /* pointer is host memory */
 #define QTT_DEVICE 1              /* pointer is device memory of the context's device */
@@ -91,7 +91,7 @@ typedef void (*qtt_free_fn)(void* ptr, void* user);
  * one Householder QR per site, and every cut's matrix is then explicit, its eigenpairs refined
  * in factored form: equal to the TT-SVD up to the sketch's range error (which falls with the
  * cut spectra's tail beyond 2 chi + 32: ~1e-13 on smooth fields, large on flat spectra such as
- * random tensor trains, where the Gram rounding is accurate).  Needs d chi <= 160. */
+ * random tensor trains, where the Gram rounding is accurate).  Needs d chi <= 256. */
 #define QTT_APPLY_GRAM 0
 #define QTT_APPLY_SKETCH 1
 
@@ -278,7 +278,7 @@ int mps_hadamard_round(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, qtt_tru
  * nothing is allocated: not by cudaMalloc, not by the context pool, not by any library. */
 int mps_dot_noalloc(int n, int d, const int* a_bonds, const double* a_cores, const int* b_bonds,
                     const double* b_cores, double* out_dev, void* cuda_stream);
-/* Symmetric eigendecomposition of a small dense matrix (n <= 160), the building block of every
+/* Symmetric eigendecomposition of a small dense matrix (n <= 256), the building block of every
  * Gram-based rounding: FP32 Jacobi sweeps refined to FP64 accuracy.  S (n x n row-major,
  * symmetric), w (n, descending) and V (n x n row-major, eigenvectors as columns) are host
  * buffers owned by the caller; synchronous. */

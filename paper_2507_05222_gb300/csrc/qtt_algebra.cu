@@ -587,8 +587,8 @@ qtt_mps* apply_round_sketch(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi,
   const int n = x->n, d = x->d;
   QTT_CHECK_ARG(M->n == n && M->d == d, "apply: shape mismatch");
   if (n == 1) return apply_round_gram(c, M, x, chi, eps, into);
-  if (int64_t(d) * chi > 160)
-    throw Error(QTT_ERR_UNSUPPORTED, "apply (sketched rounding): d * chi must be <= 160 (eigensolver limit)");
+  if (int64_t(d) * chi > 256)
+    throw Error(QTT_ERR_UNSUPPORTED, "apply (sketched rounding): d * chi must be <= 256 (eigensolver limit)");
   std::vector<int> R(n + 1);
   for (int k = 0; k <= n; ++k) R[k] = M->bonds[k] * x->bonds[k];
   std::vector<int> mstruct = left_struct(R, d);

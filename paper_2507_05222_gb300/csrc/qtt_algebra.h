@@ -45,7 +45,7 @@ qtt_mps* round_any(Ctx& c, const qtt_mps* y, int chi, double eps);
 // y = round(M x) by Gram rounding; written into `into` (bonds apply_bonds(M, x, chi)) if given.
 qtt_mps* apply_round_gram(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, double eps, qtt_mps* into = nullptr);
 // The same product rounded through a sketched left orthogonalisation and factored eigenpair
-// refinement (no squared singular values; d * chi <= 160).
+// refinement (no squared singular values; d * chi <= 256).
 qtt_mps* apply_round_sketch(Ctx& c, const qtt_mpo* M, const qtt_mps* x, int chi, double eps, qtt_mps* into = nullptr);
 std::vector<int> apply_bonds(const qtt_mpo* M, const qtt_mps* x, int chi);
 

@@ -564,7 +564,7 @@ int mps_hadamard_round(qtt_ctx* ctx, const qtt_mps* a, const qtt_mps* b, qtt_tru
 int qtt_sym_eig(qtt_ctx* ctx, int n, const double* S, double* w, double* V) {
   API_BEGIN
   QTT_CHECK_ARG(ctx && S && w && V, "sym_eig: null argument");
-  QTT_CHECK_ARG(n >= 1 && n <= 160, "sym_eig: n in [1, 160]");
+  QTT_CHECK_ARG(n >= 1 && n <= 256, "sym_eig: n in [1, 256]");
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   size_t nn = size_t(n) * n;
   DBuf dS(&c, nn), dw(&c, size_t(n)), dV(&c, nn);
@@ -730,7 +730,7 @@ int qtt_case_create(qtt_ctx* ctx, const qtt_case_params* p, qtt_case** out) {
   QTT_CHECK_ARG(ctx && p && out, "case_create: null argument");
   QTT_CHECK_ARG(p->poisson_warm == 0 || p->poisson_warm == 1, "case_create: poisson_warm must be 0 or 1");
   QTT_CHECK_ARG(p->apply == QTT_APPLY_GRAM || p->apply == QTT_APPLY_SKETCH, "case_create: apply must be 0 or 1");
-  QTT_CHECK_ARG(p->apply != QTT_APPLY_SKETCH || 2 * p->chi <= 160, "case_create: the sketched products need chi <= 80");
+  QTT_CHECK_ARG(p->apply != QTT_APPLY_SKETCH || 2 * p->chi <= 256, "case_create: the sketched products need chi <= 128");
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   std::unique_ptr<qtt_case> h(new qtt_case);
   h->ctx = &c;

@@ -546,7 +546,17 @@ __global__ void __launch_bounds__(256) k_svd_jacobi(int m, int n, const double* 
 // rotates only its own slab, with no communication between CTAs.  Sweeps stop when the
 // off-diagonal mass falls below off_tol2 of the total (squared Frobenius norms) -- the FP64
 // refinement that follows only needs a start it converges from quadratically.
-constexpr int JAC_MAX_BLOCKS_PER_THREAD = 4;   // n <= 160: 80 pairs, 3240 blocks <= 4 x 1024
+// Up to n = 160 A is stored as padded rows (n x (n + 1), upper triangle used); above, up to
+// n = 256, as the packed upper triangle (n (n + 1) / 2 floats), which fits a CTA's shared memory.
+constexpr int JAC_MAX_N_PADDED = 160, JAC_MAX_N = 256;
+__device__ __forceinline__ int jac_aidx(bool packed, int i, int j, int n, int ld) {   // i <= j
+  return packed ? (i * (2 * n - i - 1)) / 2 + j : i * ld + j;
+}
+__host__ __device__ constexpr size_t jac_a_floats(bool packed, int n) {
+  return packed ? size_t(n) * (n + 1) / 2 : size_t(n) * (n + 1);
+}
+// blocks per thread: n <= 160: 80 pairs, 3240 blocks <= 4 x 1024; n <= 256: 8256 <= 9 x 1024
+template <bool PACKED, int MAXB>
 __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __restrict__ S, double* __restrict__ Vout,
                                                      int max_sweeps, const int* __restrict__ t0_dev, float off_tol2,
                                                      const int* __restrict__ guard) {
@@ -570,20 +580,20 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
   const int npairs = np / 2;
   const int nblocks = npairs * (npairs + 1) / 2;
   const int r0 = (g * n) / G, r1 = ((g + 1) * n) / G;   // this CTA's rows of V
-  float* A = smf;                       // n x ld, upper triangle used
-  float* V = A + size_t(n) * ld;        // (r1 - r0) x ld: row i = component r0 + i
-  const size_t poff = (size_t(n) * ld + size_t(n / G + 1) * ld + 1) & ~size_t(1);   // 8-byte aligned
+  float* A = smf;                       // upper triangle (padded rows or packed)
+  float* V = A + jac_a_floats(PACKED, n);   // (r1 - r0) x ld: row i = component r0 + i
+  const size_t poff = (jac_a_floats(PACKED, n) + size_t(n / G + 1) * ld + 1) & ~size_t(1);   // 8-byte aligned
   float2* cs = reinterpret_cast<float2*>(smf + poff);
   int2* pq = reinterpret_cast<int2*>(cs + npairs);
   __shared__ float red[2][32];
   for (int i = ty; i < n; i += 32)
-    for (int j = i + tx; j < n; j += 32) A[i * ld + j] = float(S[size_t(i + t0) * nfull + (j + t0)]);
+    for (int j = i + tx; j < n; j += 32) A[jac_aidx(PACKED, i, j, n, ld)] = float(S[size_t(i + t0) * nfull + (j + t0)]);
   for (int i = ty; i < r1 - r0; i += 32)
     for (int j = tx; j < n; j += 32) V[i * ld + j] = (r0 + i == j) ? 1.0f : 0.0f;
   // this thread's blocks (k, l), k <= l, for blocks e = tid + 1024 b
-  int bk[JAC_MAX_BLOCKS_PER_THREAD], bl[JAC_MAX_BLOCKS_PER_THREAD];
+  int bk[MAXB], bl[MAXB];
 #pragma unroll
-  for (int b = 0; b < JAC_MAX_BLOCKS_PER_THREAD; ++b) {
+  for (int b = 0; b < MAXB; ++b) {
     int e = tid + 1024 * b, k = 0;
     bk[b] = -1; bl[b] = -1;
     if (e < nblocks) {
@@ -597,7 +607,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
     float off = 0.f, dia = 0.f;
     for (int i = ty; i < n; i += 32) {
       for (int j = i + tx; j < n; j += 32) {
-        float a = A[i * ld + j];
+        float a = A[jac_aidx(PACKED, i, j, n, ld)];
         if (j == i) dia += a * a; else off += a * a;
       }
     }
@@ -622,9 +632,9 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
         if (p > q) { int t2 = p; p = q; q = t2; }
         float c = 1.f, s = 0.f;
         if (q < n) {
-          float apq = A[p * ld + q];
+          float apq = A[jac_aidx(PACKED, p, q, n, ld)];
           if (apq != 0.f) {
-            float tau = (A[q * ld + q] - A[p * ld + p]) / (2.f * apq);
+            float tau = (A[jac_aidx(PACKED, q, q, n, ld)] - A[jac_aidx(PACKED, p, p, n, ld)]) / (2.f * apq);
             float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             // correctly rounded sqrt and division: c^2 + s^2 - 1 stays at the rounding level
             // with no bias, so V drifts from orthonormality like a random walk over the
@@ -639,7 +649,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
       __syncthreads();
       // A <- J^T A J: block (k, l) = R_k B R_l^T with R = [c -s; s c] acting on (p, q)
 #pragma unroll
-      for (int b = 0; b < JAC_MAX_BLOCKS_PER_THREAD; ++b) {
+      for (int b = 0; b < MAXB; ++b) {
         if (bk[b] < 0) break;
         const int k = bk[b], l = bl[b];
         const int2 pq1 = pq[k], pq2 = pq[l];
@@ -649,10 +659,10 @@ __global__ void __launch_bounds__(1024) k_jacobi_f32(int nfull, const double* __
         const bool h1 = q1 < n, h2 = q2 < n;   // a pair with q >= n is a lone index (odd n)
         // upper-triangle addresses of (p1, p2), (p1, q2), (q1, p2), (q1, q2); for k == l the
         // two off-diagonal entries are the same element
-        const int a00 = p1 <= p2 ? p1 * ld + p2 : p2 * ld + p1;
-        const int a01 = p1 <= q2 ? p1 * ld + q2 : q2 * ld + p1;
-        const int a10 = q1 <= p2 ? q1 * ld + p2 : p2 * ld + q1;
-        const int a11 = q1 <= q2 ? q1 * ld + q2 : q2 * ld + q1;
+        const int a00 = p1 <= p2 ? jac_aidx(PACKED, p1, p2, n, ld) : jac_aidx(PACKED, p2, p1, n, ld);
+        const int a01 = p1 <= q2 ? jac_aidx(PACKED, p1, q2, n, ld) : jac_aidx(PACKED, q2, p1, n, ld);
+        const int a10 = q1 <= p2 ? jac_aidx(PACKED, q1, p2, n, ld) : jac_aidx(PACKED, p2, q1, n, ld);
+        const int a11 = q1 <= q2 ? jac_aidx(PACKED, q1, q2, n, ld) : jac_aidx(PACKED, q2, q1, n, ld);
         const float b00 = A[a00];
         const float b01 = h2 ? A[a01] : 0.f;
         const float b10 = h1 ? A[a10] : 0.f;
@@ -868,7 +878,8 @@ void init_kernel_attributes() {
     g_attr_svd = true;
   }
   if (!g_attr_jac) {
-    QTT_CUDA(cudaFuncSetAttribute(k_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    QTT_CUDA(cudaFuncSetAttribute(k_jacobi_f32<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    QTT_CUDA(cudaFuncSetAttribute(k_jacobi_f32<true, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     g_attr_jac = true;
   }
 }
@@ -1030,14 +1041,16 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep, const 
   DigitsScope fp64(c, kDigitsFP64);   // the decompositions and their refinement products stay FP64
   QTT_CHECK_ARG(n >= 1, "eigh: n >= 1");
   if (keep <= 0 || keep > n) keep = n;
-  if (n > 160) throw Error(QTT_ERR_UNSUPPORTED, "eigh: n > 160 not supported");
+  if (n > JAC_MAX_N) throw Error(QTT_ERR_UNSUPPORTED, "eigh: n > 256 not supported");
+  const bool packed = n > JAC_MAX_N_PADDED;
   QTT_CHECK_ARG(!F || m >= 1, "eigh: factor needs m >= 1 rows");
   // FP32 Jacobi: QTT_JAC_CTAS CTAs share the eigenvector rows for the larger matrices (each
   // keeps all of A; 8: 16 rows each at n = 128)
   const int jac_ctas = n >= 64 ? QTT_JAC_CTAS : 1;
   const size_t npairs = size_t((n + 1) & ~1) / 2;
-  const size_t smf = ((size_t(n) * (n + 1) + size_t(n / jac_ctas + 1) * (n + 1) + 1) & ~size_t(1)) * sizeof(float) +
+  const size_t smf = ((jac_a_floats(packed, n) + size_t(n / jac_ctas + 1) * (n + 1) + 1) & ~size_t(1)) * sizeof(float) +
                      npairs * (sizeof(float2) + sizeof(int2));
+  auto jacobi = packed ? k_jacobi_f32<true, 9> : k_jacobi_f32<false, 4>;
   init_kernel_attributes();
   const size_t nn = size_t(n) * n;
   DBuf X(&c, nn), Xs(&c, nn), XtX(&c, nn), AX(&c, nn), SX(&c, nn), E(&c, nn), Y(&c, nn), lam(&c, size_t(n)),
@@ -1060,7 +1073,7 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep, const 
   }
   {
     ProfScope ps(c, KC_EIG);
-    k_jacobi_f32<<<jac_ctas, dim3(32, 32), smf, c.stream>>>(n, S, X.p, 10, nullptr, JAC_TOL2_FULL, nullptr);
+    jacobi<<<jac_ctas, dim3(32, 32), smf, c.stream>>>(n, S, X.p, packed ? 14 : 10, nullptr, JAC_TOL2_FULL, nullptr);
     after_launch(c, "jacobi_f32");
   }
 
@@ -1081,7 +1094,7 @@ void eigh(Ctx& c, int n, const double* S, double* w, double* V, int keep, const 
       c.guard = nullptr;
       {
         ProfScope ps(c, KC_EIG);
-        k_jacobi_f32<<<jac_ctas, dim3(32, 32), smf, c.stream>>>(n, SX.p, Y.p, 8, t0, JAC_TOL2_TAIL, need);
+        jacobi<<<jac_ctas, dim3(32, 32), smf, c.stream>>>(n, SX.p, Y.p, packed ? 10 : 8, t0, JAC_TOL2_TAIL, need);
         after_launch(c, "jacobi_f32_tail");
       }
       c.guard = need;

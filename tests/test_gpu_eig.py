@@ -1,6 +1,7 @@
 """The small symmetric eigensolver (FP32 Jacobi + FP64 refinement) against numpy on the
 spectra the Gram roundings meet: one dominant value over a flat tail, exact zeros from
-rank-deficient Gram matrices, clusters, and wide geometric decay."""
+rank-deficient Gram matrices, clusters, and wide geometric decay; orders up to 160 (padded
+shared-memory rows) and above (packed upper triangle, up to 256)."""
 import numpy as np
 import pytest
 
@@ -38,7 +39,7 @@ def spectrum(kind, n, g):
 
 @pytest.mark.parametrize("kind", ["dominant_flat_tail", "zeros", "geometric", "geometric4", "geometric8",
                                   "geometric12", "cluster", "random"])
-@pytest.mark.parametrize("n", [16, 64, 128])
+@pytest.mark.parametrize("n", [16, 64, 128, 161, 256])
 def test_sym_eig(ctx, kind, n):
     from paper_2507_05222_gb300 import qtt
     g = inputs.rng(n + len(kind))

@@ -124,14 +124,14 @@ def test_sketch_step_matches_oracle(ctx):
 
 
 def test_sketch_rejects_wide_cuts(ctx):
-    """d chi > 160 exceeds the eigensolver of the cut matrices: QTT_ERR_UNSUPPORTED, and the
-    case rejects the sketched products above chi = 80."""
+    """d chi > 256 exceeds the eigensolver of the cut matrices: QTT_ERR_UNSUPPORTED, and the
+    case rejects the sketched products above chi = 128."""
     from paper_2507_05222_gb300 import qtt
     x = inputs.random_cores(8, 4, seed=1)
     M = inputs.random_mpo_cores(8, 2, seed=2)
     with pytest.raises(qtt.QttError) as e:
-        qtt.mpo_apply_round(ctx, qtt.MPO.from_cores(ctx, M), qtt.MPS.from_cores(ctx, x), 96, apply="sketch")
+        qtt.mpo_apply_round(ctx, qtt.MPO.from_cores(ctx, M), qtt.MPS.from_cores(ctx, x), 160, apply="sketch")
     assert e.value.code == -7
     with pytest.raises(qtt.QttError) as e:
-        qtt.Case(ctx, 4, 4, 40.0, 100.0, 2e-3, 96, "interleaved", apply="sketch")
+        qtt.Case(ctx, 4, 4, 40.0, 100.0, 2e-3, 160, "interleaved", apply="sketch")
     assert e.value.code == -1
