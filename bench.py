@@ -554,7 +554,7 @@ def precision_drift(args, cfg):
 def warm_start_study(args):
     """Learned Poisson warm start (the growth direction standing in for the paper's unspecified
     preconditioner of the Poisson sweeps): a rotating-cylinder case (rate 1, Re = 100, 2^10 x
-    2^10 cells, chi = 64, dt = 1e-3) is spun up from the synthetic wake state, then --ws-train
+    2^10 cells, chi = --ws-chi (96), dt = 1e-3) is spun up from the synthetic wake state, then --ws-train
     steps record (u, v, p, the last pressure change) before each step and the change of the
     pressure change over it, restricted to the 2^7 x 2^7 coarse grid on the device; a 4-layer,
     32-channel network is trained on them (Adam, on the device).  Over --ws-test further steps
@@ -569,7 +569,7 @@ def warm_start_study(args):
     torch.cuda.set_device(0)
     ctx = qtt.Context(0)
     ne = nx = 10
-    chi, lv, Hc = 64, 3, 2 ** 7
+    chi, lv, Hc = args.ws_chi, 3, 2 ** 7
     case = qtt.Case(ctx, ne, nx, WORKLOAD["R"], 100.0, 1e-3, chi, "interleaved", rot=1.0,
                     fit_sweeps=WORKLOAD["fit_sweeps"], mom=WORKLOAD["mom"], poi=WORKLOAD["poi"])
     u0, v0 = inputs.wake_field(ne, nx, 11)
@@ -654,7 +654,7 @@ def warm_start_study(args):
                    "poisson_cg_mean": float(np.mean([a[1] for a in v])) if v else None,
                    "step_ms_median": float(np.median([a[2] for a in v])) if v else None,
                    "steps": len(v)} for k, v in rec.items()}
-    line = {"warm_start_study": "rotating cylinder rate 1, Re 100, 2^10 x 2^10, chi 64, dt 1e-3",
+    line = {"warm_start_study": f"rotating cylinder rate 1, Re 100, 2^10 x 2^10, chi {chi}, dt 1e-3",
             "train_pairs": len(X), "train_iters": args.ws_iters, "coarse_grid": [Hc, Hc],
             "network": {"layers": depth, "channels": width, "inputs": "u, v, p, last p change (coarse)",
                         "output": "next p change minus the last (correction to the extrapolation)"},
@@ -773,6 +773,7 @@ def main():
     ap.add_argument("--ws-train", type=int, default=60)
     ap.add_argument("--ws-iters", type=int, default=600)
     ap.add_argument("--ws-test", type=int, default=12)
+    ap.add_argument("--ws-chi", type=int, default=96, help="bond cap of the warm-start study's case")
     ap.add_argument("--drift-steps", type=int, default=0,
                     help="precision study: this many steps at FP64 and at --precision from the same state, C_D/C_L "
                          "drift and final field difference (one JSON line; no bench line)")
