@@ -155,6 +155,38 @@ def oracle_steps(cfg, k_steps, budget_s=None):
     return done / dt, done, dt, len(os.sched_getaffinity(0)), first
 
 
+def l0_errors(cfg, gpu_first, l1_first, gpu_after, steps_after):
+    """Relative weighted L2 error of the velocity magnitude (Sec. IV's norm, weight |J|) against
+    the full-grid FD step L0 (exact Fourier-in-xi, tridiagonal-in-eta solves), started from the
+    same encoded initial state: after the first step for the GPU and for the FP64 QTT oracle L1
+    (the fixed-error condition: the GPU's error at most the oracle's times 1 + 1e-3), and for the
+    GPU after `steps_after` steps (the state the timed window left)."""
+    from oracle import fd, tt, qtt_ops as Q
+    ne, nx, order = cfg["n_eta"], cfg["n_xi"], cfg["ordering"]
+    _, (u, v, _), _ = oracle_start(cfg)
+    grid = fd.Grid(ne, nx, cfg["R"])
+    solver = fd.FDSolver(fd.Case(grid, cfg["Re"], cfg["dt"]), "fft")
+    field = lambda vec: np.ravel(Q.vec_to_field(np.asarray(vec), ne, nx, order))
+    u0, v0 = field(tt.full(u)), field(tt.full(v))
+
+    def eps(uq, vq, ur, vr):
+        mr = np.sqrt(ur ** 2 + vr ** 2)
+        return fd.weighted_l2(grid, np.sqrt(uq ** 2 + vq ** 2) - mr) / fd.weighted_l2(grid, mr)
+
+    ul, vl = u0, v0
+    t0 = time.perf_counter()
+    l0 = []
+    for _ in range(max(1, steps_after)):
+        ul, vl = solver.step(ul, vl)[:2]
+        l0.append((ul, vl))
+    e_gpu = eps(field(gpu_first[0]), field(gpu_first[1]), *l0[0])
+    e_l1 = eps(field(tt.full(l1_first[0])), field(tt.full(l1_first[1])), *l0[0])
+    e_after = eps(field(gpu_after[0]), field(gpu_after[1]), *l0[steps_after - 1])
+    return {"first_step": {"gpu": e_gpu, "oracle_L1": e_l1, "ok": bool(e_gpu <= e_l1 * (1.0 + 1e-3))},
+            "after_timed_window": {"gpu": e_after, "steps": steps_after},
+            "norm": "weighted L2 of |v| (weight |J|), relative to L0's", "L0_s": time.perf_counter() - t0}
+
+
 def run_reference(args, cfg):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -344,7 +376,7 @@ def run_ours(args, cfg):
     step_ms, e2e_s = max_over_ranks([step_ms, e2e_s], world, "cuda")   # the slowest rank
     # ---- CPU baseline: the FP64 oracle on the host cores, one step of the workload from its
     # initial state; that step is also the parity reference of the GPU's first warm-up step
-    cpu, parity = None, None
+    cpu, parity, eps_l0 = None, None, None
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import tt
         sps, done, dt, cores, ofirst = oracle_steps(cfg, 1)
@@ -355,6 +387,7 @@ def run_ours(args, cfg):
             diffs = [float(np.linalg.norm(g - tt.full(o)) / np.linalg.norm(tt.full(o))) for g, o in zip(first, ofirst)]
             parity = {"gpu_vs_oracle_first_step": dict(zip("uvp", diffs)), "bound": STEP_PARITY_BOUND,
                       "ok": bool(max(diffs) <= STEP_PARITY_BOUND)}
+            eps_l0 = l0_errors(cfg, first, ofirst, [qtt.qtt_decode(ctx, x) for x in snap], args.warmup + args.steps)
     if rank == 0:
         line = {"metric": METRIC, "value": job_throughput(world, step_ms * 1e-3), "unit": "steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
@@ -383,7 +416,8 @@ def run_ours(args, cfg):
                 "kernel_classes_ms_by_phase": by_phase,
                 "phase_ms_last_timed_step": phases, "phase_ms_eager_step": eager_phases,
                 "solves": solves,
-                "fixed_error": {"solves_ok": solves_ok, "parity": parity, "drift_vs_fp64_pipe": drift},
+                "fixed_error": {"solves_ok": solves_ok, "parity": parity, "drift_vs_fp64_pipe": drift,
+                                "eps_l2_vs_L0": eps_l0},
                 "clocks": clk, "cpu_baseline": cpu,
                 "last_step": {"cd": info[0]["cd"], "cl": info[0]["cl"]}}
         print(json.dumps(line))

@@ -250,10 +250,56 @@ class Case:
         return np.full(Nx, self.u_inf), np.zeros(Nx)
 
 
-class FDSolver:
-    """Full-grid fractional step (Sec. III.C) with cached sparse LU factorisations."""
+class PeriodicXiSolver:
+    """Direct solve of M x = b for a grid operator M that is invariant under shifts along the
+    periodic xi direction (the coefficients of the momentum operator and of the pressure
+    Laplacian depend on eta only: J, g11/J, g22/J of App. A's analytic metric, g12 = 0), with
+    couplings to xi neighbours s in {-1, 0, +1} only.  M is block-circulant: with
+    B_s[i, i'] = M[(i, j), (i', j + s)], the discrete Fourier transform along xi turns it into
+    one tridiagonal eta system per mode m, sum_s B_s exp(2 pi i s m / N_xi), solved by a banded
+    LU; this is the same linear system as the sparse solve, in O(N log N)."""
 
-    def __init__(self, case: Case):
+    def __init__(self, M: sp.spmatrix, g: Grid):
+        Ne, Nx = g.N_eta, g.N_xi
+        M = M.tocsr()
+        self.Ne, self.Nx = Ne, Nx
+        B = {s: np.zeros((Ne, Ne)) for s in (-1, 0, 1)}
+        rows = np.arange(Ne) * Nx                      # (i, j = 0)
+        sub = M[rows]
+        coo = sub.tocoo()
+        for r, c, v in zip(coo.row, coo.col, coo.data):
+            ip, jp = divmod(int(c), Nx)
+            s = jp if jp <= Nx // 2 else jp - Nx
+            if s not in B:
+                raise ValueError("operator couples xi neighbours beyond +-1")
+            B[s][r, ip] += v
+        for s_, Bs in B.items():
+            off = Bs - np.diag(np.diag(Bs)) - np.diag(np.diag(Bs, 1), 1) - np.diag(np.diag(Bs, -1), -1)
+            if np.abs(off).max() > 0:
+                raise ValueError("eta coupling beyond the tridiagonal band")
+        w = np.exp(2j * np.pi * np.arange(Nx) / Nx)      # mode m: shift s contributes w_m^s
+        self.ab = np.zeros((Nx, 3, Ne), dtype=complex)   # solve_banded layout per mode
+        for s_, Bs in B.items():
+            f = (w ** s_)[:, None]
+            self.ab[:, 0, 1:] += f * np.diag(Bs, 1)
+            self.ab[:, 1, :] += f * np.diag(Bs)
+            self.ab[:, 2, :-1] += f * np.diag(Bs, -1)
+
+    def solve(self, b):
+        from scipy.linalg import solve_banded
+        bh = np.fft.fft(np.reshape(b, (self.Ne, self.Nx)), axis=1)
+        xh = np.empty_like(bh)
+        for k in range(self.Nx):
+            xh[:, k] = solve_banded((1, 1), self.ab[k], bh[:, k])
+        return np.real(np.fft.ifft(xh, axis=1)).ravel()
+
+
+class FDSolver:
+    """Full-grid fractional step (Sec. III.C) with cached direct solvers of the momentum and
+    pressure systems: sparse LU (direct="lu") or the exact Fourier-in-xi, tridiagonal-in-eta
+    solve of the same matrices (direct="fft", for grids where a sparse LU would not fit)."""
+
+    def __init__(self, case: Case, direct: str = "lu"):
         self.case = case
         g = case.grid
         self.vel = operators(g, "velocity")
@@ -262,8 +308,14 @@ class FDSolver:
         I = sp.identity(n, format="csc")
         self.H = (I - (case.dt / case.Re) * self.vel["Lap"][0]).tocsc()
         self.Lp = self.pre["Lap"][0].tocsc()
-        self._Hlu = spla.splu(self.H)
-        self._Plu = spla.splu(self.Lp)
+        if direct == "lu":
+            self._Hlu = spla.splu(self.H)
+            self._Plu = spla.splu(self.Lp)
+        elif direct == "fft":
+            self._Hlu = PeriodicXiSolver(self.H, g)
+            self._Plu = PeriodicXiSolver(self.Lp, g)
+        else:
+            raise ValueError(direct)
 
     def grad_div(self, u, v):
         c = self.case

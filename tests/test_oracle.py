@@ -586,3 +586,33 @@ def test_table2_rotating_cylinder_fd_sanity():
     assert abs(vals["mean_cl"] - 2.4908) <= 0.01 * 2.4908
     assert abs(vals["st"] - 0.1663) <= 0.01 * 0.1663
     assert vals["mean_cd"] > 0.0
+
+
+@pytest.mark.parametrize("ne,nx,rot", [(3, 4, 0.0), (4, 5, 0.7), (5, 3, 1.3)])
+def test_fft_direct_solver_equals_sparse_lu(ne, nx, rot):
+    """The Fourier-in-xi, tridiagonal-in-eta solve of L0 (for grids too large for a sparse LU)
+    is the same linear algebra as the sparse LU: the momentum and pressure systems on random
+    right-hand sides, and a whole L0 step, agree to rounding (the block-circulant structure
+    holds because the analytic metric depends on eta only)."""
+    case = fd.Case(fd.Grid(ne, nx, 40.0), Re=100.0, dt=2e-3, rot=rot)
+    lu, ff = fd.FDSolver(case, "lu"), fd.FDSolver(case, "fft")
+    g = inputs.rng(ne * 10 + nx)
+    n = case.grid.N_eta * case.grid.N_xi
+    for M, a, b in ((lu.H, lu._Hlu, ff._Hlu), (lu.Lp, lu._Plu, ff._Plu)):
+        rhs = g.standard_normal(n)
+        x1, x2 = a.solve(rhs), b.solve(rhs)
+        assert np.linalg.norm(x1 - x2) <= 1e-12 * np.linalg.norm(x1)
+        assert np.linalg.norm(M @ x2 - rhs) <= 1e-11 * np.linalg.norm(rhs)
+    u = 1.0 + 1e-2 * g.standard_normal(n)
+    v = 1e-2 * g.standard_normal(n)
+    for r1, r2 in zip(lu.step(u, v), ff.step(u, v)):
+        assert np.linalg.norm(r1 - r2) <= 1e-12 * np.linalg.norm(r1)
+
+
+def test_fft_direct_solver_rejects_coupling_beyond_neighbours():
+    """A matrix coupling xi nodes two apart is not of the solver's form and is refused."""
+    gr = fd.Grid(2, 3, 40.0)
+    n = gr.N_eta * gr.N_xi
+    M = sp.identity(n, format="csr") + sp.csr_matrix((np.ones(1), ([0], [2])), shape=(n, n))
+    with pytest.raises(ValueError):
+        fd.PeriodicXiSolver(M, gr)
