@@ -765,6 +765,72 @@ def steady_sweep(args):
         print(json.dumps(line), flush=True)
 
 
+def periodogram_peak(sig, dt):
+    """Frequency of the largest peak of the Hann-windowed periodogram of `sig` (sampled every dt),
+    refined by a parabola through the log-power of the peak bin and its neighbours."""
+    x = np.asarray(sig) - np.mean(sig)
+    pw = np.abs(np.fft.rfft(x * np.hanning(len(x)))) ** 2
+    k = int(np.argmax(pw[1:]) + 1)
+    off = 0.0
+    if 1 <= k < len(pw) - 1 and min(pw[k - 1], pw[k], pw[k + 1]) > 0:
+        a, b, c = np.log(pw[k - 1]), np.log(pw[k]), np.log(pw[k + 1])
+        off = 0.5 * (a - c) / (a - 2 * b + c)
+    return float((k + off) / (len(x) * dt))
+
+
+def transient_sweep(args):
+    """Strouhal number versus chi for vortex shedding behind the non-rotating cylinder (Sec.
+    IV.A.2) at a reduced grid: Re = 100, 2^6 x 2^7 cells, R = 32, dt = 1e-2, sequential bit order,
+    started from the seeded wake state (seed 7) encoded at chi, 6000 steps (t = 60); St of the lift
+    from its zero crossings over t >= 30 (eq:st), mean C_D and the lift amplitude over that window,
+    against the FD oracle's run from the same state (tests/golden/transient_re100_fd.txt);
+    ms per step and the parameter fraction.  One JSON line per chi."""
+    import torch
+    from paper_2507_05222_gb300 import inputs, qtt
+    torch.cuda.set_device(0)
+    ref = {}
+    with open(os.path.join(ROOT, "tests", "golden", "transient_re100_fd.txt")) as f:
+        for line in f:
+            if not line.startswith("#"):
+                k, v = line.split()
+                ref[k] = float(v)
+    ne, nx, dt, t_end, t_win = 6, 7, 1e-2, 60.0, 30.0
+    nsteps = int(round(t_end / dt))
+    u0, v0 = inputs.wake_field(ne, nx, 7)
+    for chi in args.transient_chi:
+        ctx = qtt.Context(0)
+        case = qtt.Case(ctx, ne, nx, 32.0, 100.0, dt, chi, "sequential", mom=(6, 1e-10, 300, 1e-2, 0.1),
+                        poi=(12, 1e-10, 500, 1e-2, 0.1), apply=args.apply)
+        enc = lambda f: qtt.qtt_encode(ctx, qtt.qtt_field_to_vector(ctx, f, "sequential"), ne + nx, chi)
+        case.set_state(enc(u0), enc(v0), qtt.MPS.from_cores(ctx, inputs.random_cores(ne + nx, chi, 5, scale=1e-8)))
+        cd, cl = [], []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        chunk = 500
+        e0.record(ctx.stream)
+        for s0 in range(0, nsteps, chunk):
+            recs = qtt.fractional_step(ctx, case, min(chunk, nsteps - s0), with_forces=True, check=False)
+            cd += [r["cd"] for r in recs]
+            cl += [r["cl"] for r in recs]
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nsteps
+        t = dt * np.arange(1, nsteps + 1)
+        w = t >= t_win
+        cdm, clm = np.asarray(cd)[w], np.asarray(cl)[w]
+        st = qtt.qtt_strouhal(t[w], clm)          # eq:st, the library's zero-crossing count
+        st_spec = periodogram_peak(clm, dt)       # not moved by high-frequency noise in C_L
+        u, _, _ = case.get_state()
+        nvps = sum(int(np.prod(c.shape)) for c in u.cores()) / float(2 ** (ne + nx))
+        line = {"transient_sweep": "Re 100, 2^6 x 2^7 cells, R 32, dt 1e-2, sequential order, wake_field seed 7, "
+                                   "t = 60, statistics over t >= 30", "chi": chi, "apply": args.apply,
+                "st": st, "st_fd": ref["st"], "st_abs_error": abs(st - ref["st"]), "st_spectral": st_spec, "st_spectral_fd": ref["st_spectral"],
+                "cd_mean": float(np.mean(cdm)), "cd_mean_fd": ref["cd_mean"],
+                "cl_amplitude": float(np.ptp(clm)), "cl_amplitude_fd": ref["cl_amp"],
+                "finite": bool(np.all(np.isfinite(cd)) and np.all(np.isfinite(cl))),
+                "nvps": nvps, "ms_per_step": ms, "steps": nsteps}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -807,6 +873,9 @@ def main():
     ap.add_argument("--steady-sweep", action="store_true",
                     help="steady Re = 20 chi sweep against the FD reference (one JSON line per chi; no bench line)")
     ap.add_argument("--steady-chi", type=int, nargs="+", default=[8, 16, 24, 32, 64])
+    ap.add_argument("--transient-sweep", action="store_true",
+                    help="Strouhal number versus chi, vortex shedding at Re 100 on 2^6 x 2^7 cells (Sec. IV.A.2)")
+    ap.add_argument("--transient-chi", type=int, nargs="+", default=[16, 32, 48])
     ap.add_argument("--warm-start", action="store_true",
                     help="learned Poisson warm start study (one JSON line; no bench line)")
     ap.add_argument("--ws-spinup", type=int, default=10)
@@ -851,6 +920,9 @@ def main():
         return
     if args.steady_sweep:
         steady_sweep(args)
+        return
+    if args.transient_sweep:
+        transient_sweep(args)
         return
     if args.impl == "reference":
         run_reference(args, cfg)
