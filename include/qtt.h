@@ -301,8 +301,10 @@ int qtt_qr(qtt_ctx* ctx, int m, int n, int trans, const double* A, double* Q, do
  * TMA-staged tiles and tensor-memory accumulators (3); both give bit-identical results. */
 int qtt_dgemm(qtt_ctx* ctx, int m, int n, int k, const double* A, const double* B, double* C, int path);
 /* Matrix products of the whole library: mode 0 (default) sends products of at least 2^23
- * multiply-adds to the tensor cores (digit-split FP64), mode 1 keeps every product on the FP64
- * pipe, modes 2 and 3 are mode 0 with the digit products on mma.sync (2) or tcgen05 (3).
+ * multiply-adds to the tensor cores (digit-split FP64, the digit products by tcgen05.mma on
+ * TMA-staged tiles), mode 1 keeps every product on the FP64 pipe, modes 2 and 3 are mode 0 with
+ * the digit products forced onto warp-level mma.sync (2) or tcgen05 (3); 0, 2 and 3 give
+ * bit-identical results.
  * Takes effect for work enqueued afterwards (a captured step keeps its kernels). */
 int qtt_ctx_set_gemm_mode(qtt_ctx* ctx, int mode);
 /* Self-check of the QR's Householder scalars: the maximum relative errors of its Newton-Raphson

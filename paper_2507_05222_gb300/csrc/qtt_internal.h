@@ -293,8 +293,9 @@ void gemm_ozaki(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t K, double a
                 double* C, int64_t sCb, int64_t sCm, int64_t sCn);
 void init_ozaki_attributes();   // kernel attributes, once (before any stream capture)
 // The digit products of gemm_ozaki on the fifth-generation tensor cores (qtt_tc05.cu): the
-// engine of gemm mode 0 when true (mode 3 forces it, mode 2 forces the mma.sync kernel).
-constexpr bool kDigitProductsOnTc05 = false;
+// engine of gemm mode 0 when true, for every FP64 product whose padded k is a multiple of 16
+// (mode 3 forces it, mode 2 forces the mma.sync kernel; the two give bit-identical results).
+constexpr bool kDigitProductsOnTc05 = true;
 void init_tc05_attributes();     // kernel attributes and the tensor-map encoder, once
 bool tc05_fits(int64_t Kp);
 void oz_gemm_tc05(Ctx& c, int64_t batch, int64_t M, int64_t N, int64_t Kp, int splits, int64_t ksplit,
