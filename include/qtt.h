@@ -112,8 +112,11 @@ typedef struct {
   double norm;             /* ||result||_2 */
   double discarded_norm;   /* sqrt(sum over cuts of the discarded sigma^2): the TT-SVD error bound
                               (Sec. II, rounding), equal to ||exact - result|| for a canonical
-                              sweep.  From Gram eigenvalues it resolves only values above
-                              ~1e-8 ||exact|| (they square the singular values).  -1 for
+                              sweep.  From Gram eigenvalues (QTT_APPLY_GRAM and the other
+                              Gram roundings) it resolves only values above ~1e-8 ||exact||
+                              (they square the singular values); the sketched rounding of
+                              mpo_apply_round sums Rayleigh quotients formed from explicit cut
+                              matrices, resolved down to the FP64 floor.  -1 for
                               mps_hadamard_round, whose result is a variational fit. */
 } qtt_round_info;
 
