@@ -51,3 +51,51 @@ def test_missing_library_fails_loudly(lib, monkeypatch, tmp_path):
     monkeypatch.setattr(lib, "_lib", None)
     with pytest.raises(RuntimeError):
         lib.lib()
+
+
+def test_binding_structs_match_the_header_layout(lib, tmp_path):
+    """Every struct the binding passes by value or pointer has the header's field names, offsets
+    and size: a C program compiled against include/qtt.h prints sizeof and offsetof of each field
+    the ctypes mirror names (a name the header lacks fails to compile; a field the binding lacks
+    changes the size)."""
+    import ctypes
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = [lib.qtt_trunc, lib.qtt_round_info, lib.qtt_solve_opts, lib.qtt_solve_info, lib.qtt_case_params,
+               lib.qtt_step_info]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "qtt.h"', "int main(void) {"]
+    expect = []
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        expect.append(ctypes.sizeof(st))
+        for fname, _ in st._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {fname}));')
+            expect.append(getattr(st, fname).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
+    # and the same member names in the same order (padding can hide a missing trailing field)
+    import re
+    header = open(os.path.join(root, "include", "qtt.h")).read()
+    header = re.sub(r"/\*.*?\*/", "", header, flags=re.S)
+    for st in structs:
+        m = re.search(r"typedef struct\s*\{([^{}]*)\}\s*" + st.__name__ + r"\s*;", header)
+        assert m, st.__name__
+        names = []
+        for decl in m.group(1).split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            ty_and_first, *rest = [x.strip() for x in decl.split(",")]
+            names.append(ty_and_first.split()[-1].lstrip("*"))
+            names += [x.lstrip("*") for x in rest]
+        assert names == [f for f, _ in st._fields_], st.__name__
